@@ -1,0 +1,471 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT demagnetization-tensor (DM) stray field on GB300.
+
+One step = one pass of the field pipeline with the fused energy, i.e.
+H = -N * M and E = -(mu0/2) V sum M.H on a 256^3 grid (2 nm cubic cells,
+seeded random unit m, Ms = 8e5 A/m) in FP32 (FFTs and spectral product in
+FP32, tensor set up in FP64). The tensor setup runs once per geometry before
+the timed region (the method's setup/apply split) and is reported as
+setup_ms. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (numpy FFT convolution) on a
+bounded sample grid of the same workload, on the host cores.
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(independent magnetization states, no data-path collective); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stray-field cells/s at 256^3 FP32 (field + energy step), vs plain FP64 on 1 GB300"
+N_GRID = (256, 256, 256)
+CELL = (2e-9, 2e-9, 2e-9)
+MS = 8e5
+SEED = 1
+MU0 = 4e-7 * math.pi
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+PASS_NAMES = ["x_fwd", "y_fwd", "z_conv", "y_inv", "x_inv", "energy"]
+
+
+def pass_bytes(n, P, elem=4):
+    """Algorithmic HBM bytes of each kernel per launch (the data each pass must
+    read and write once): spectra are complex (2 elem), the tensor spectrum is
+    6 real octant arrays."""
+    nx, ny, nz = n
+    Px, Py, Pz = P
+    Kx = Px // 2 + 1
+    c = 2 * elem
+    cells = nx * ny * nz
+    s1 = 3 * nz * ny * Kx * c
+    s2 = 3 * nz * Py * Kx * c
+    nh = 6 * (Pz // 2 + 1) * (Py // 2 + 1) * Kx * elem
+    return {
+        "x_fwd": 3 * cells * elem + s1,
+        "y_fwd": s1 + s2,
+        "z_conv": 2 * s2 + nh,
+        "y_inv": s2 + s1,
+        "x_inv": s1 + 3 * cells * elem + 3 * cells * elem,  # reads S1 and M, writes H
+    }
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1204_4302_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1204_4302_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def load_traffic(kernel: str, n, src_hash: str):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, scaled to
+    this workload, or None if absent or taken on an older kernel source."""
+    try:
+        with open(TRAFFIC) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = t.get(kernel)
+    if not ent or ent.get("source_hash") != src_hash:
+        return None
+    cells = n[0] * n[1] * n[2]
+    return ent["bytes_per_cell"] * cells
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1204_4302_gb300 import inputs
+    from paper_1204_4302_gb300.plan import Plan
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = N_GRID
+    cells = n[0] * n[1] * n[2]
+    # independent state per rank (replicas of the method, distinct inputs)
+    m_np = inputs.random_unit(n, seed=SEED + rank)
+    M = torch.tensor(MS * m_np, dtype=torch.float32, device=dev)
+
+    t0 = time.perf_counter()
+    plan = Plan(n, CELL, prec="f32", device=dev)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    info = plan.info()
+    P = (info["px"], info["py"], info["pz"])
+    H = torch.empty_like(M)
+    E = torch.empty((), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    from paper_1204_4302_gb300 import binding as B
+
+    def step():
+        B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    plan.set_timing(True)
+    launches0 = plan.launch_count()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    for _ in range(args.steps):
+        step()
+    ev1.record(st)
+    ev1.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = plan.launch_count() - launches0
+    pass_ms, pass_n = plan.get_timing(6)
+    plan.set_timing(False)
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * cells * args.steps / (ms / 1e3)
+
+    # energy sanity (device value, read after timing)
+    E_val = float(E.item())
+
+    # ---------------------------------------------------------------- roofline
+    peak, peak_kind = load_peaks()
+    pb = pass_bytes(n, P, 4)
+    avg = {nm: (pass_ms[i] / pass_n[i] if pass_n[i] else None) for i, nm in enumerate(PASS_NAMES[:5])}
+    per_pass = {}
+    for nm in PASS_NAMES[:5]:
+        if avg[nm]:
+            gbs = pb[nm] / (avg[nm] * 1e-3) / 1e9
+            per_pass[nm] = {"ms": round(avg[nm], 4), "bytes": pb[nm], "gbs": round(gbs, 1),
+                            "frac": round(gbs / peak, 3)}
+    dominant = max(per_pass, key=lambda k: per_pass[k]["ms"]) if per_pass else "z_conv"
+    src_hash = source_hash()
+    traffic = load_traffic(dominant, n, src_hash)
+    roof = {
+        "bound": "hbm",
+        "kernel": dominant,
+        "achieved": per_pass.get(dominant, {}).get("gbs"),
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": per_pass.get(dominant, {}).get("frac"),
+        "traffic": traffic,
+        "peak_source": peak_kind,
+        "algorithmic_bytes": pb[dominant],
+    }
+
+    # ------------------------------------------------ FP64 form and FP32 error
+    f64 = None
+    if not args.skip_f64:
+        plan64 = Plan(n, CELL, prec="f64", device=dev)
+        M64 = M.double()
+        H64 = torch.empty_like(M64)
+        E64 = torch.empty((), dtype=torch.float64, device=dev)
+        from paper_1204_4302_gb300 import binding as B
+        for _ in range(2):
+            B.demag_field_energy(plan64.handle, M64.data_ptr(), H64.data_ptr(), E64.data_ptr(), st.cuda_stream)
+        torch.cuda.synchronize()
+        k64 = max(3, args.steps // 4)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(k64):
+            B.demag_field_energy(plan64.handle, M64.data_ptr(), H64.data_ptr(), E64.data_ptr(), st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        diff = (H.double() - H64)
+        rel_max = float(diff.abs().max() / H64.abs().max())
+        rel_rms = float(diff.norm() / H64.norm())
+        f64 = {"ms_per_step": round(ms64, 4), "cells_per_s": cells / (ms64 / 1e3),
+               "speedup_f32_over_f64": round(ms64 / ms_per_step, 2),
+               "f32_rel_max_err_vs_f64": rel_max, "f32_rel_rms_err_vs_f64": rel_rms,
+               "energy_rel_diff": abs(E_val - float(E64.item())) / abs(float(E64.item()))}
+        plan64.close()
+        del M64, H64
+
+    # ------------------------------------------------ gradient (adjoint) timing
+    grad = None
+    if not args.skip_grad:
+        m32 = torch.tensor(m_np, dtype=torch.float32, device=dev)
+        G = torch.empty_like(m32)
+        from paper_1204_4302_gb300 import binding as B
+        for _ in range(2):
+            B.demag_energy_grad(plan.handle, m32.data_ptr(), None, MS, E.data_ptr(), G.data_ptr(), None,
+                                st.cuda_stream)
+        torch.cuda.synchronize()
+        kg = max(3, args.steps // 2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(kg):
+            B.demag_energy_grad(plan.handle, m32.data_ptr(), None, MS, E.data_ptr(), G.data_ptr(), None,
+                                st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        grad = {"ms_per_step": round(e0.elapsed_time(e1) / kg, 4)}
+        del m32, G
+
+    # ------------------------------------------------ end to end (host buffers)
+    e2e = None
+    if not args.skip_e2e:
+        from paper_1204_4302_gb300 import binding as B
+        Mh = M.cpu().pin_memory()
+        Hh = torch.empty_like(Mh).pin_memory()
+        for _ in range(2):
+            B.demag_field_host(plan.handle, Mh.data_ptr(), Hh.data_ptr(), st.cuda_stream)
+        barrier()
+        ke = max(3, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            B.demag_field_host(plan.handle, Mh.data_ptr(), Hh.data_ptr(), st.cuda_stream)
+        barrier()
+        te = (time.perf_counter() - t0) / ke
+        tmax = te
+        if dist is not None:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tmax = float(t.item())
+        nbytes = 3 * cells * 4
+        e2e = {"value": world * cells / tmax, "unit": "cells/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": round(tmax * 1e3, 4)}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cpu = cpu_baseline(args.cpu_sample)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "cells/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded random unit magnetization)",
+            "config": {"workload": "DM stray field + energy, 256x256x256 cells of 2 nm, padded 512^3, FP32 "
+                                   "FFT/product, FP64 tensor setup",
+                       "grid": list(n), "padded": list(P), "cell_m": list(CELL), "Ms": MS,
+                       "parallelism": f"replicas x{world} (independent states)",
+                       "l2": "inputs and spectra (~2 GB) larger than L2, no flush needed"},
+            "gpu_launches": launches,
+            "setup_ms": round(setup_ms, 1),
+            "energy_J": E_val,
+            "passes": per_pass,
+            "roofline": roof,
+            "clocks": clocks,
+            "e2e": e2e,
+            "plain_f64": f64,
+            "gradient": grad,
+            "cpu_baseline": cpu,
+            "source_hash": src_hash,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    plan.close()
+
+
+# ------------------------------------------------------------------- oracle side
+def _oracle_sample(k: int):
+    """The oracle's field on a k^3 grid of the same workload (same cell, same
+    state recipe); returns a callable that runs one field evaluation."""
+    import numpy as np
+
+    import oracle
+    from paper_1204_4302_gb300 import inputs
+    n = (k, k, k)
+    M = MS * inputs.random_unit(n, seed=SEED)
+    P = tuple(oracle.padded_size(v) for v in n)
+    spec = oracle.tensor_spectrum(oracle.tensor_octant(n, CELL), P)   # setup, untimed
+
+    def run():
+        H = oracle.field_fft(M, CELL, P=P, spectrum=spec)
+        return oracle.energy(M, H, CELL)
+    return run, k ** 3
+
+
+def cpu_baseline(k: int):
+    run, cells = _oracle_sample(k)
+    run()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        run()
+        reps += 1
+        if time.perf_counter() - t0 > 8.0 or reps >= 5:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": cells / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy-FFT oracle field + energy on a {k}^3 grid of the same workload "
+                      f"(2 nm cells, random unit m), tensor spectrum precomputed; {reps} runs, "
+                      f"{dt:.2f} s each"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    k = args.ref_sample
+    run, cells = _oracle_sample(k)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = cells / dt
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "cells/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded random unit magnetization)",
+        "config": {"workload": "DM stray field + energy, 256x256x256 cells of 2 nm (bounded sample, see cpu_baseline)",
+                   "grid": list(N_GRID), "sample_grid": [k, k, k]},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 numpy-FFT oracle field + energy per step on a {k}^3 grid of the "
+                                   f"same workload, tensor spectrum precomputed"},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--ref-sample", type=int, default=64)
+    ap.add_argument("--skip-f64", action="store_true")
+    ap.add_argument("--skip-grad", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * demag.h - C ABI of the GB300 (sm_103a) FFT demagnetization-tensor library.
+ *
+ * The library computes the micromagnetic stray field of the demagnetization-
+ * tensor method (DM) of Abert et al., "Numerical Methods for the Stray-Field
+ * Calculation" (arXiv 1204.4302):
+ *
+ *   H(r) = -sum_r' N(r - r') M(r')                         (Sec. 3.1, Eq. "demag")
+ *
+ * on a regular nx x ny x nz grid of cells of edges dx, dy, dz, evaluated as a
+ * zero-padded 3-D FFT convolution (Sec. 3.1, Eq. "convolution": an element-
+ * wise 3x3 matrix-vector product in Fourier space). N is the cell-averaged
+ * demagnetization tensor (homogeneously magnetized cells, field averaged over
+ * each cell, Sec. 5.1), positive definite at the origin with trace 1. The
+ * paper writes H = N * M with the opposite sign convention for N; both
+ * describe the same field.
+ *
+ * Conventions shared by all entry points
+ *  - Layout: M, H and every other field are structure-of-arrays
+ *    [3][nz][ny][nx], C order, x fastest, components (x, y, z).
+ *  - Element type: float for DEMAG_F32 plans, double for DEMAG_F64 plans.
+ *    DEMAG_F32 runs the FFTs and the spectral product in FP32 with an FP64
+ *    tensor setup; DEMAG_F64 runs everything in FP64.
+ *  - Units: M and H in A/m, energies in J, cell edges in m (any consistent
+ *    length unit works for the field: N is dimensionless). mu0 = 4 pi 1e-7.
+ *  - Pointers named "device" must be device memory of the plan's GPU, at
+ *    least 16-byte aligned, not overlapping each other. The caller keeps
+ *    ownership of every pointer it passes; the plan owns its own buffers.
+ *  - Streams: a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. Calls are asynchronous on that stream unless stated otherwise.
+ *  - Errors: every call returns a status and never aborts. On failure a
+ *    message is kept per thread, readable with demag_last_error(). A plan is
+ *    not thread safe: use one plan per host thread or serialise calls.
+ */
+#ifndef DEMAG_H
+#define DEMAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct demag_plan *demag_plan_t;
+
+typedef enum {
+    DEMAG_OK = 0,
+    DEMAG_ERR_INVALID_ARG = 1, /* bad size, null or misaligned pointer, aliasing */
+    DEMAG_ERR_NOT_SETUP = 2,   /* demag_tensor_setup() has not run on this plan */
+    DEMAG_ERR_OOM = 3,         /* device or pinned host allocation failed */
+    DEMAG_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has it) */
+    DEMAG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    DEMAG_ERR_UNSUPPORTED = 6  /* size or option outside what is built */
+} demag_status;
+
+typedef enum { DEMAG_F32 = 0, DEMAG_F64 = 1 } demag_prec;
+
+/* Optional plan settings; zero-initialise and set what you need. */
+typedef struct {
+    /* Padded FFT lengths per axis. 0 selects the smallest power of two
+     * >= 2n - 1 (1 when n == 1). Any power of two >= 2n - 1 gives the same
+     * field up to rounding (the convolution is exact for every such period). */
+    int px, py, pz;
+} demag_options;
+
+/* Sizes of a plan, as chosen at creation. */
+typedef struct {
+    int nx, ny, nz;          /* physical grid */
+    int px, py, pz;          /* padded FFT lengths */
+    int kx;                  /* px/2 + 1 stored x frequencies */
+    int prec;                /* demag_prec */
+    size_t device_bytes;     /* device memory held by the plan */
+    int launches_per_field;  /* kernels one demag_field call launches */
+    double tensor_imag_max;  /* largest |imaginary part| of the tensor spectrum
+                                after setup (exactly 0 in exact arithmetic: the
+                                wrapped tensor is even or odd per axis) */
+} demag_info;
+
+/* Create a plan for an nx x ny x nz grid with cell edges dx, dy, dz.
+ * Allocates the plan's device buffers on the current CUDA device (two
+ * spectra, the tensor spectrum, twiddle tables); launches nothing.
+ * Sizes: 1 <= n <= 512 per axis (padded length <= 1024).
+ * Returns DEMAG_ERR_INVALID_ARG for non-positive sizes or edges,
+ * DEMAG_ERR_UNSUPPORTED for sizes beyond the limit, DEMAG_ERR_OOM if the
+ * device allocation fails. *out is NULL on failure. */
+demag_status demag_plan_create(int nx, int ny, int nz, double dx, double dy, double dz,
+                               demag_prec prec, demag_plan_t *out);
+
+/* Same, with options (may be NULL). */
+demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, double dz,
+                                  demag_prec prec, const demag_options *opt,
+                                  demag_plan_t *out);
+
+/* Tensor setup, once per geometry (paper Sec. 4: the convolution kernel
+ * depends only on geometry and discretisation). Evaluates the six tensor
+ * components N_xx..N_yz in FP64 on the device for every offset of the grid
+ * (closed form for touching cells, Gauss-Legendre quadrature of the point
+ * kernel at intermediate range, a multipole expansion of the cell average
+ * far away), places them at wrapped offsets of the padded grid and stores
+ * the (real) 3-D spectrum. Allocates and frees temporary device memory;
+ * blocks until done. Idempotent. */
+demag_status demag_tensor_setup(demag_plan_t plan, void *stream);
+
+/* H = -N * M (paper Sec. 3.1, Eq. "demag"). M, H: device, [3][nz][ny][nx] of
+ * the plan's element type; H must not alias M. Needs demag_tensor_setup().
+ * Asynchronous: launches demag_info.launches_per_field kernels on stream. */
+demag_status demag_field(demag_plan_t plan, const void *M, void *H, void *stream);
+
+/* Adjoint of M -> H applied to G (same layout). The tensor is symmetric
+ * (N_ij = N_ji) and even (N(-r) = N(r)), so the operator is self-adjoint and
+ * this equals demag_field(G). Used for gradients: d/dM of sum(G . H(M)). */
+demag_status demag_field_adjoint(demag_plan_t plan, const void *G, void *out, void *stream);
+
+/* Field and energy E = -(mu0/2) V sum_cells M.H (paper Sec. 2, the stray-
+ * field energy, in SI units; V = dx dy dz). H: device output as above.
+ * E_dev: device pointer to one double receiving E. The per-block partial sums
+ * are formed in the field's last pass and summed in FP64 with compensation.
+ * Asynchronous. */
+demag_status demag_field_energy(demag_plan_t plan, const void *M, void *H, double *E_dev,
+                                void *stream);
+
+/* Energy only: computes E for M without storing H (the last pass keeps only
+ * the energy sums), synchronises the stream and writes E to *E_out (host). */
+demag_status demag_energy(demag_plan_t plan, const void *M, double *E_out, void *stream);
+
+/* Energy and its gradient for a magnetization given as M = Ms * w * m, with m
+ * the reduced magnetization [3][nz][ny][nx] (device), w an optional per-cell
+ * weight [nz][ny][nx] (device, e.g. a 0/1 mask of the body; NULL = 1) and Ms
+ * the saturation magnetization (A/m). All in the same kernels as the field:
+ *   E    = -(mu0/2) V sum M.H                       (paper Sec. 2)
+ *   grad = g * dE/dm = -g mu0 V Ms w H               (the operator is
+ *          self-adjoint, so the adjoint of the field map is the field map)
+ * E_dev (device double) and grad (device, layout of m, not aliasing m or w)
+ * are each optional but not both NULL. gscale_dev: optional device double g
+ * (the upstream gradient of E); NULL means g = 1. Asynchronous. */
+demag_status demag_energy_grad(demag_plan_t plan, const void *m, const void *w, double Ms,
+                               double *E_dev, void *grad, const double *gscale_dev, void *stream);
+
+/* End-to-end call with host buffers: copies M (host, [3][nz][ny][nx]) to the
+ * device, computes H and copies it back to H_host, then synchronises the
+ * stream. Page-locked host memory gives full copy bandwidth; pageable memory
+ * works too. Uses plan-owned device buffers allocated at the first call. */
+demag_status demag_field_host(demag_plan_t plan, const void *M_host, void *H_host, void *stream);
+
+/* Plan sizes and memory. */
+demag_status demag_plan_info(demag_plan_t plan, demag_info *info);
+
+/* Per-kernel timing of the field pipeline with CUDA events recorded on the
+ * launch stream around each kernel (off by default). demag_get_timing fills
+ * ms[i] with the summed milliseconds of pass i and counts[i] with its number
+ * of launches since the last reset, for i < n (n <= 8; pass order: x forward,
+ * y forward, z convolution, y inverse, x inverse, energy finalise). Reading
+ * synchronises on the recorded events. */
+demag_status demag_set_timing(demag_plan_t plan, int enable);
+demag_status demag_get_timing(demag_plan_t plan, double *ms, long *counts, int n);
+
+/* Number of kernels this plan has launched since creation. */
+long demag_launch_count(demag_plan_t plan);
+
+/* Destroy a plan and free its device memory (NULL is ignored). */
+void demag_plan_destroy(demag_plan_t plan);
+
+/* Last error message of the calling thread ("" if none). */
+const char *demag_last_error(void);
+
+/* Name of a status code. */
+const char *demag_status_string(demag_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEMAG_H */

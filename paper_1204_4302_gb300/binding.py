@@ -1,0 +1,195 @@
+"""ctypes binding of libdemag.so: the C entry points under the same names.
+
+Argument marshalling only. Every computation runs in the library's CUDA
+kernels; when the library is missing this module raises instead of falling
+back to anything else. Pointers are passed as integers (device addresses,
+e.g. ``tensor.data_ptr()``), streams as integer handles (``cudaStream_t``).
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_double, c_int, c_long, c_size_t, c_void_p
+from pathlib import Path
+
+LIB_PATH = Path(__file__).resolve().parent / "_build" / "libdemag.so"
+
+DEMAG_F32 = 0
+DEMAG_F64 = 1
+
+STATUS = {
+    0: "DEMAG_OK",
+    1: "DEMAG_ERR_INVALID_ARG",
+    2: "DEMAG_ERR_NOT_SETUP",
+    3: "DEMAG_ERR_OOM",
+    4: "DEMAG_ERR_CUDA",
+    5: "DEMAG_ERR_TIMEOUT",
+    6: "DEMAG_ERR_UNSUPPORTED",
+}
+
+# Every symbol include/demag.h declares (the CPU tests check the export list).
+EXPORTS = [
+    "demag_plan_create", "demag_plan_create_ex", "demag_tensor_setup", "demag_field",
+    "demag_field_adjoint", "demag_field_energy", "demag_energy", "demag_energy_grad",
+    "demag_field_host", "demag_plan_info", "demag_set_timing", "demag_get_timing",
+    "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
+]
+
+
+class DemagError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.name = STATUS.get(status, f"status {status}")
+        super().__init__(f"{where}: {self.name}: {message}")
+
+
+class demag_options(ctypes.Structure):
+    _fields_ = [("px", c_int), ("py", c_int), ("pz", c_int)]
+
+
+class demag_info(ctypes.Structure):
+    _fields_ = [
+        ("nx", c_int), ("ny", c_int), ("nz", c_int),
+        ("px", c_int), ("py", c_int), ("pz", c_int),
+        ("kx", c_int), ("prec", c_int),
+        ("device_bytes", c_size_t),
+        ("launches_per_field", c_int),
+        ("tensor_imag_max", c_double),
+    ]
+
+
+_lib = None
+
+
+def load(path: str | Path | None = None):
+    """Load libdemag.so (built in-tree by ``paper_1204_4302_gb300.build``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise ImportError(
+            f"{p} is missing: build the CUDA library first "
+            "(python -m paper_1204_4302_gb300.build, or __graft_entry__.build())")
+    lib = ctypes.CDLL(str(p))
+    S = c_int
+    P = c_void_p
+    D = c_double
+    I = c_int
+    sig = {
+        "demag_plan_create": (S, [I, I, I, D, D, D, I, POINTER(c_void_p)]),
+        "demag_plan_create_ex": (S, [I, I, I, D, D, D, I, POINTER(demag_options), POINTER(c_void_p)]),
+        "demag_tensor_setup": (S, [P, P]),
+        "demag_field": (S, [P, P, P, P]),
+        "demag_field_adjoint": (S, [P, P, P, P]),
+        "demag_field_energy": (S, [P, P, P, P, P]),
+        "demag_energy": (S, [P, P, POINTER(c_double), P]),
+        "demag_energy_grad": (S, [P, P, P, D, P, P, P, P]),
+        "demag_field_host": (S, [P, P, P, P]),
+        "demag_plan_info": (S, [P, POINTER(demag_info)]),
+        "demag_set_timing": (S, [P, I]),
+        "demag_get_timing": (S, [P, POINTER(c_double), POINTER(c_long), I]),
+        "demag_launch_count": (c_long, [P]),
+        "demag_plan_destroy": (None, [P]),
+        "demag_last_error": (ctypes.c_char_p, []),
+        "demag_status_string": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        msg = load().demag_last_error()
+        raise DemagError(status, where, msg.decode() if msg else "")
+
+
+def _p(v):
+    return None if v is None or v == 0 else c_void_p(int(v))
+
+
+# ------------------------------------------------------------------ entry points
+def demag_plan_create(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32):
+    h = c_void_p()
+    _check(load().demag_plan_create(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                    int(prec), ctypes.byref(h)), "demag_plan_create")
+    return h.value
+
+
+def demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=0):
+    h = c_void_p()
+    opt = demag_options(int(px), int(py), int(pz))
+    _check(load().demag_plan_create_ex(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                       int(prec), ctypes.byref(opt), ctypes.byref(h)),
+           "demag_plan_create_ex")
+    return h.value
+
+
+def demag_tensor_setup(plan, stream=0):
+    _check(load().demag_tensor_setup(_p(plan), _p(stream)), "demag_tensor_setup")
+
+
+def demag_field(plan, M, H, stream=0):
+    _check(load().demag_field(_p(plan), _p(M), _p(H), _p(stream)), "demag_field")
+
+
+def demag_field_adjoint(plan, G, out, stream=0):
+    _check(load().demag_field_adjoint(_p(plan), _p(G), _p(out), _p(stream)), "demag_field_adjoint")
+
+
+def demag_field_energy(plan, M, H, E_dev, stream=0):
+    _check(load().demag_field_energy(_p(plan), _p(M), _p(H), _p(E_dev), _p(stream)), "demag_field_energy")
+
+
+def demag_energy(plan, M, stream=0) -> float:
+    e = c_double()
+    _check(load().demag_energy(_p(plan), _p(M), ctypes.byref(e), _p(stream)), "demag_energy")
+    return e.value
+
+
+def demag_energy_grad(plan, m, w, Ms, E_dev, grad, gscale_dev=None, stream=0):
+    _check(load().demag_energy_grad(_p(plan), _p(m), _p(w), float(Ms), _p(E_dev), _p(grad),
+                                    _p(gscale_dev), _p(stream)), "demag_energy_grad")
+
+
+def demag_field_host(plan, M_host, H_host, stream=0):
+    _check(load().demag_field_host(_p(plan), _p(M_host), _p(H_host), _p(stream)), "demag_field_host")
+
+
+def demag_plan_info(plan) -> dict:
+    info = demag_info()
+    _check(load().demag_plan_info(_p(plan), ctypes.byref(info)), "demag_plan_info")
+    return {name: getattr(info, name) for name, _ in demag_info._fields_}
+
+
+def demag_set_timing(plan, enable=True):
+    _check(load().demag_set_timing(_p(plan), int(bool(enable))), "demag_set_timing")
+
+
+def demag_get_timing(plan, n=6):
+    ms = (c_double * n)()
+    cnt = (c_long * n)()
+    _check(load().demag_get_timing(_p(plan), ms, cnt, int(n)), "demag_get_timing")
+    return list(ms), list(cnt)
+
+
+def demag_launch_count(plan) -> int:
+    return int(load().demag_launch_count(_p(plan)))
+
+
+def demag_plan_destroy(plan):
+    if plan:
+        load().demag_plan_destroy(_p(plan))
+
+
+def demag_last_error() -> str:
+    m = load().demag_last_error()
+    return m.decode() if m else ""
+
+
+def demag_status_string(s: int) -> str:
+    return load().demag_status_string(int(s)).decode()

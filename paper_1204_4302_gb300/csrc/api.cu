@@ -1,0 +1,617 @@
+// C ABI of the FFT demagnetization-tensor library (declared in
+// include/demag.h). Host-side plan management and the pass sequence:
+//
+//   x R2C (pruned to nx inputs) -> y FFT (ny of Py inputs) ->
+//   z FFT . (H^ = -N^ M^) . z IFFT (nz outputs kept) ->
+//   y IFFT (ny outputs kept) -> x C2R (nx outputs, scaled 1/(Px Py Pz),
+//   optional per-block energy sums) [-> energy finalise]
+//
+// which is the zero-padded convolution H = -N * M of paper Sec. 3.1 (Eq.
+// "demag" evaluated through Eq. "convolution").
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+using demag::Passes;
+
+namespace {
+
+thread_local std::string g_err;
+
+demag_status fail(demag_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define DEMAG_CUDA(call)                                                                      \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,     \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+constexpr int kMaxN = 512;
+constexpr int kMaxP = 1024;
+constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int default_pad(int n)
+{
+    int p = 1;
+    while (p < 2 * n - 1) p *= 2;
+    return p;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_size(const demag_plan *p) { return p->prec == DEMAG_F32 ? sizeof(float) : sizeof(double); }
+
+int64_t ncell(const demag_plan *p) { return (int64_t)p->nx * p->ny * p->nz; }
+
+// The pointer must be device (or managed) memory of the plan's device, 16-byte
+// aligned. Host pointers are rejected before any kernel could touch them.
+demag_status check_dev_ptr(const demag_plan *p, const void *ptr, const char *name)
+{
+    if (!ptr) return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is NULL");
+    if (((uintptr_t)ptr & 15u) != 0) return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not device memory");
+    if (a.type == cudaMemoryTypeDevice && a.device != p->device)
+        return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " lives on another device");
+    return DEMAG_OK;
+}
+
+bool overlap(const void *a, const void *b, size_t bytes)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+// Twiddle table W_P^m = exp(-2 pi i m / P), m < P, from long double sin/cos.
+template <typename C>
+std::vector<C> twiddles(int P)
+{
+    std::vector<C> t(P);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int m = 0; m < P; ++m) {
+        const long double a = 2.0L * pi * (long double)m / (long double)P;
+        t[m].x = (decltype(t[m].x))cosl(a);
+        t[m].y = (decltype(t[m].y))(-sinl(a));
+    }
+    return t;
+}
+
+// --- per-kernel timing: a ring of call slots with one event per pass edge.
+constexpr int kRing = 64;
+constexpr int kEvPerCall = 7;
+
+struct TimingRing {
+    cudaEvent_t ev[kRing][kEvPerCall];
+    int used[kRing];  // number of events recorded in the slot (0 = free)
+    int next;
+};
+
+TimingRing *ring_of(demag_plan *p) { return static_cast<TimingRing *>(p->ring); }
+
+void ring_collect_slot(demag_plan *p, TimingRing *R, int s)
+{
+    if (R->used[s] < 2) { R->used[s] = 0; return; }
+    cudaEventSynchronize(R->ev[s][R->used[s] - 1]);
+    for (int i = 0; i + 1 < R->used[s]; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, R->ev[s][i], R->ev[s][i + 1]) == cudaSuccess) {
+            p->pass_ms[i] += ms;
+            p->pass_n[i] += 1;
+        }
+    }
+    R->used[s] = 0;
+}
+
+struct PassTimer {
+    demag_plan *p;
+    TimingRing *R = nullptr;
+    int slot = -1, k = 0;
+    cudaStream_t st;
+    PassTimer(demag_plan *p_, cudaStream_t s) : p(p_), st(s)
+    {
+        if (!p->timing) return;
+        R = ring_of(p);
+        slot = R->next;
+        R->next = (R->next + 1) % kRing;
+        if (R->used[slot]) ring_collect_slot(p, R, slot);
+        mark();
+    }
+    void mark()
+    {
+        if (R && k < kEvPerCall) { cudaEventRecord(R->ev[slot][k], st); ++k; R->used[slot] = k; }
+    }
+};
+
+// What one pass through the pipeline reads and writes (see XIn / XOut).
+struct FieldJob {
+    const void *in;       // input field [3][nz][ny][nx]
+    const void *wcell;    // optional per-cell weight [nz][ny][nx]
+    double wscalar;       // input = in * wscalar * wcell
+    void *out;            // optional output = H * oscale * wcell * g
+    double oscale;
+    const double *gdev;   // optional device scalar g
+    double *E_dev;        // optional energy -(mu0/2) V sum input . H
+};
+
+template <typename T>
+demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
+{
+    using C = typename demag::CplxOf<T>::type;
+    C *S1 = static_cast<C *>(p->S1);
+    C *S2 = static_cast<C *>(p->S2);
+    const bool f32 = p->prec == DEMAG_F32;
+    const C *twx = f32 ? (const C *)(const void *)p->tw32[0] : (const C *)(const void *)p->tw64[0];
+    const C *twy = f32 ? (const C *)(const void *)p->tw32[1] : (const C *)(const void *)p->tw64[1];
+    const C *twz = f32 ? (const C *)(const void *)p->tw32[2] : (const C *)(const void *)p->tw64[2];
+    const T *nhat = f32 ? (const T *)(const void *)p->nhat32 : (const T *)(const void *)p->nhat64;
+    const int nx = p->nx, ny = p->ny, nz = p->nz, Px = p->Px, Py = p->Py, Pz = p->Pz, Kx = p->Kx, Kxp = p->Kxp;
+    const int rows = 3 * nz * ny;
+    demag::XIn<T> xi;
+    xi.in = static_cast<const T *>(job.in);
+    xi.in_rs = nx;
+    xi.wcell = static_cast<const T *>(job.wcell);
+    xi.wscalar = (T)job.wscalar;
+    xi.rows_per_comp = nz * ny;
+    demag::XOut<T> xo;
+    xo.out = static_cast<T *>(job.out);
+    xo.out_rs = nx;
+    xo.scale = (T)(1.0 / ((double)Px * Py * Pz));
+    xo.oscale = (T)job.oscale;
+    xo.wcell = static_cast<const T *>(job.wcell);
+    xo.gdev = job.gdev;
+    xo.Mref = job.E_dev ? static_cast<const T *>(job.in) : nullptr;
+    xo.mscale = (T)job.wscalar;
+    xo.partials = job.E_dev ? p->partials : nullptr;
+    xo.rows_per_comp = nz * ny;
+    PassTimer tm(p, st);
+    cudaError_t e;
+    // x forward
+    if (Px == 1) e = Passes<T>::x1_fwd(xi, rows, S1, st);
+    else e = Passes<T>::x_fwd(Px / 2, xi, rows, nx, S1, Kxp, twx, st);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x forward: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    // y forward
+    if (Py > 1) {
+        e = Passes<T>::col(Py, false, S1, S2, 3 * nz * Kx, Kx, (int64_t)ny * Kxp, Kxp, ny,
+                           (int64_t)Py * Kxp, Kxp, Py, twy, 1, st);
+        if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y forward: ") + cudaGetErrorString(e));
+        p->launches++;
+    }
+    tm.mark();
+    // z forward . product . z inverse
+    e = Passes<T>::zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat, Py, Kx,
+                         twz, 1, st);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("z convolution: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    // y inverse
+    if (Py > 1) {
+        e = Passes<T>::col(Py, true, S2, S1, 3 * nz * Kx, Kx, (int64_t)Py * Kxp, Kxp, Py, (int64_t)ny * Kxp, Kxp,
+                           ny, twy, 1, st);
+        if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y inverse: ") + cudaGetErrorString(e));
+        p->launches++;
+    }
+    tm.mark();
+    // x inverse (+ epilogue)
+    int nblocks;
+    if (Px == 1) {
+        nblocks = p->npartials;
+        e = Passes<T>::x1_inv(S1, rows, xo, nblocks, st);
+    } else {
+        nblocks = Passes<T>::x_blocks(Px / 2, rows);
+        e = Passes<T>::x_inv(Px / 2, S1, Kxp, rows, nx, xo, twx, st);
+    }
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x inverse: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    if (job.E_dev) {
+        const double V = p->dx * p->dy * p->dz;
+        e = demag::energy_finalize(p->partials, nblocks, -0.5 * kMu0 * V, job.E_dev, st);
+        if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
+        p->launches++;
+        tm.mark();
+    }
+    return DEMAG_OK;
+}
+
+demag_status check_scalar_ptr(const void *ptr, const char *name)
+{
+    if (((uintptr_t)ptr & 7u) != 0) return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not 8-byte aligned");
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not device memory");
+    return DEMAG_OK;
+}
+
+demag_status run_job(demag_plan *p, const FieldJob &job, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    demag_status s;
+    const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
+    if ((s = check_dev_ptr(p, job.in, "input field")) != DEMAG_OK) return s;
+    if (job.out) {
+        if ((s = check_dev_ptr(p, job.out, "output field")) != DEMAG_OK) return s;
+        if (overlap(job.in, job.out, bytes))
+            return fail(DEMAG_ERR_INVALID_ARG, "output overlaps input (in-place is not supported)");
+    }
+    if (job.wcell) {
+        if ((s = check_dev_ptr(p, job.wcell, "cell weight")) != DEMAG_OK) return s;
+        if (job.out && overlap(job.wcell, job.out, bytes))
+            return fail(DEMAG_ERR_INVALID_ARG, "output overlaps the cell weight");
+    }
+    if (job.gdev && (s = check_scalar_ptr(job.gdev, "gradient scale")) != DEMAG_OK) return s;
+    if (job.E_dev && (s = check_scalar_ptr(job.E_dev, "E_dev")) != DEMAG_OK) return s;
+    if (!job.out && !job.E_dev) return fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no output, no energy)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == DEMAG_F32) return run_field<float>(p, job, st);
+    return run_field<double>(p, job, st);
+}
+
+FieldJob plain_job(const void *M, void *H, double *E_dev)
+{
+    FieldJob j;
+    j.in = M; j.wcell = nullptr; j.wscalar = 1.0;
+    j.out = H; j.oscale = 1.0; j.gdev = nullptr;
+    j.E_dev = E_dev;
+    return j;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *demag_last_error(void) { return g_err.c_str(); }
+
+const char *demag_status_string(demag_status s)
+{
+    switch (s) {
+    case DEMAG_OK: return "DEMAG_OK";
+    case DEMAG_ERR_INVALID_ARG: return "DEMAG_ERR_INVALID_ARG";
+    case DEMAG_ERR_NOT_SETUP: return "DEMAG_ERR_NOT_SETUP";
+    case DEMAG_ERR_OOM: return "DEMAG_ERR_OOM";
+    case DEMAG_ERR_CUDA: return "DEMAG_ERR_CUDA";
+    case DEMAG_ERR_TIMEOUT: return "DEMAG_ERR_TIMEOUT";
+    case DEMAG_ERR_UNSUPPORTED: return "DEMAG_ERR_UNSUPPORTED";
+    }
+    return "DEMAG_ERR_UNKNOWN";
+}
+
+void demag_plan_destroy(demag_plan_t p)
+{
+    if (!p) return;
+    DeviceGuard g(p->device);
+    if (p->S2 && p->S2 != p->S1) cudaFree(p->S2);
+    cudaFree(p->S1);
+    cudaFree(p->nhat32);
+    cudaFree(p->nhat64);
+    for (int a = 0; a < 3; ++a) { cudaFree(p->tw64[a]); cudaFree(p->tw32[a]); }
+    cudaFree(p->partials);
+    cudaFree(p->e_dev);
+    cudaFree(p->dM);
+    cudaFree(p->dH);
+    if (p->ring) {
+        TimingRing *R = ring_of(p);
+        for (int s = 0; s < kRing; ++s)
+            for (int i = 0; i < kEvPerCall; ++i) cudaEventDestroy(R->ev[s][i]);
+        delete R;
+    }
+    delete p;
+}
+
+demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
+                                  const demag_options *opt, demag_plan_t *out)
+{
+    if (!out) return fail(DEMAG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DEMAG_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz))
+        return fail(DEMAG_ERR_INVALID_ARG, "cell edges must be positive and finite");
+    if (prec != DEMAG_F32 && prec != DEMAG_F64) return fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
+    if (nx > kMaxN || ny > kMaxN || nz > kMaxN)
+        return fail(DEMAG_ERR_UNSUPPORTED, "grid sizes above 512 per axis are not built");
+    int P[3] = {default_pad(nx), default_pad(ny), default_pad(nz)};
+    const int n[3] = {nx, ny, nz};
+    if (opt) {
+        const int req[3] = {opt->px, opt->py, opt->pz};
+        for (int a = 0; a < 3; ++a) {
+            if (req[a] == 0) continue;
+            if (!is_pow2(req[a]) || req[a] < 2 * n[a] - 1)
+                return fail(DEMAG_ERR_INVALID_ARG, "padded lengths must be powers of two >= 2n - 1");
+            if (req[a] > kMaxP) return fail(DEMAG_ERR_UNSUPPORTED, "padded lengths above 1024 are not built");
+            P[a] = req[a];
+        }
+    }
+    demag_plan *p = new demag_plan;
+    memset(p, 0, sizeof(*p));
+    p->nx = nx; p->ny = ny; p->nz = nz;
+    p->dx = dx; p->dy = dy; p->dz = dz;
+    p->prec = prec;
+    p->Px = P[0]; p->Py = P[1]; p->Pz = P[2];
+    p->Kx = P[0] == 1 ? 1 : P[0] / 2 + 1;
+    p->Kxp = P[0] == 1 ? 1 : (p->Kx + 1) / 2 * 2;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(DEMAG_ERR_CUDA, "no CUDA device");
+    }
+    const size_t cs = prec == DEMAG_F32 ? sizeof(float2) : sizeof(double2);
+    const size_t s1 = (size_t)3 * nz * ny * p->Kxp * cs;
+    const size_t s2 = (size_t)3 * nz * p->Py * p->Kxp * cs;
+    const size_t plane = (size_t)(p->Pz / 2 + 1) * (p->Py / 2 + 1) * p->Kx;
+    const int rows = 3 * nz * ny;
+    p->npartials = p->Px == 1 ? std::max(1, std::min(4096, (rows + 255) / 256))
+                              : (prec == DEMAG_F32 ? Passes<float>::x_blocks(p->Px / 2, rows)
+                                                   : Passes<double>::x_blocks(p->Px / 2, rows));
+    auto cleanup_fail = [&](cudaError_t e, const char *what) {
+        demag_plan_destroy(p);
+        return fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->S1, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S1");
+    if (p->Py > 1) {
+        if ((e = cudaMalloc(&p->S2, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S2");
+    } else {
+        p->S2 = p->S1;
+    }
+    if (prec == DEMAG_F32) {
+        if ((e = cudaMalloc(&p->nhat32, 6 * plane * sizeof(float))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
+    } else {
+        if ((e = cudaMalloc(&p->nhat64, 6 * plane * sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
+    }
+    if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc partials");
+    if ((e = cudaMalloc(&p->e_dev, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc energy");
+    for (int a = 0; a < 3; ++a) {
+        const auto t64 = twiddles<double2>(P[a]);
+        if ((e = cudaMalloc(&p->tw64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
+        if ((e = cudaMemcpy(p->tw64[a], t64.data(), sizeof(double2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cleanup_fail(e, "twiddle upload");
+        if (prec == DEMAG_F32) {
+            const auto t32 = twiddles<float2>(P[a]);
+            if ((e = cudaMalloc(&p->tw32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
+            if ((e = cudaMemcpy(p->tw32[a], t32.data(), sizeof(float2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cleanup_fail(e, "twiddle upload");
+        }
+    }
+    if ((e = cudaMemset(p->S1, 0, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+    if (p->S2 != p->S1 && (e = cudaMemset(p->S2, 0, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+    p->device_bytes = s1 + (p->S2 != p->S1 ? s2 : 0) + 6 * plane * (prec == DEMAG_F32 ? 4 : 8) +
+                      sizeof(double) * (p->npartials + 1) +
+                      (size_t)(P[0] + P[1] + P[2]) * (sizeof(double2) + (prec == DEMAG_F32 ? sizeof(float2) : 0));
+    *out = p;
+    g_err.clear();
+    return DEMAG_OK;
+}
+
+demag_status demag_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
+                               demag_plan_t *out)
+{
+    return demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec, nullptr, out);
+}
+
+demag_status demag_tensor_setup(demag_plan_t p, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (p->setup_done) return DEMAG_OK;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = p->nx, ny = p->ny, nz = p->nz, Px = p->Px, Py = p->Py, Pz = p->Pz, Kx = p->Kx, Kxp = p->Kxp;
+    const size_t plane = (size_t)(Pz / 2 + 1) * (Py / 2 + 1) * Kx;
+    double *oct = nullptr, *W = nullptr, *nh64 = p->nhat64;
+    double2 *St = nullptr;
+    unsigned long long *imag = nullptr;
+    bool own64 = false;
+    demag_status rs = DEMAG_OK;
+    auto done = [&](demag_status s) {
+        cudaFree(oct); cudaFree(W); cudaFree(St); cudaFree(imag);
+        if (own64) cudaFree(nh64);
+        return s;
+    };
+#define SETUP_CUDA(call)                                                                       \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            rs = fail(e_ == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,        \
+                      std::string("tensor setup: ") + #call + ": " + cudaGetErrorString(e_));  \
+            return done(rs);                                                                   \
+        }                                                                                      \
+    } while (0)
+    SETUP_CUDA(cudaMalloc(&oct, sizeof(double) * 6 * (size_t)nx * ny * nz));
+    SETUP_CUDA(cudaMalloc(&W, sizeof(double) * (size_t)Px * Py * Pz));
+    SETUP_CUDA(cudaMalloc(&St, sizeof(double2) * (size_t)Pz * Py * Kxp));
+    SETUP_CUDA(cudaMalloc(&imag, sizeof(unsigned long long)));
+    SETUP_CUDA(cudaMemsetAsync(imag, 0, sizeof(unsigned long long), st));
+    if (!nh64) {
+        SETUP_CUDA(cudaMalloc(&nh64, sizeof(double) * 6 * plane));
+        own64 = true;
+    }
+    SETUP_CUDA(demag::tensor_octant(oct, nx, ny, nz, p->dx, p->dy, p->dz, st));
+    demag::XIn<double> xin;
+    xin.in = W;
+    xin.in_rs = Px;
+    xin.wcell = nullptr;
+    xin.wscalar = 1.0;
+    xin.rows_per_comp = Pz * Py;
+    for (int c = 0; c < 6; ++c) {
+        SETUP_CUDA(demag::tensor_wrap(oct, c, nx, ny, nz, Px, Py, Pz, W, st));
+        if (Px == 1) SETUP_CUDA(Passes<double>::x1_fwd(xin, (int64_t)Pz * Py, St, st));
+        else SETUP_CUDA(Passes<double>::x_fwd(Px / 2, xin, Pz * Py, Px, St, Kxp, p->tw64[0], st));
+        if (Py > 1)
+            SETUP_CUDA(Passes<double>::col(Py, false, St, St, Pz * Kx, Kx, (int64_t)Py * Kxp, Kxp, Py,
+                                           (int64_t)Py * Kxp, Kxp, Py, p->tw64[1], 1, st));
+        if (Pz > 1)
+            SETUP_CUDA(Passes<double>::col(Pz, false, St, St, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, Pz, Kxp,
+                                           (int64_t)Py * Kxp, Pz, p->tw64[2], 1, st));
+        SETUP_CUDA(demag::tensor_extract(St, c, Px, Py, Pz, Kxp, nh64, p->nhat32, imag, st));
+    }
+    unsigned long long bits = 0;
+    SETUP_CUDA(cudaMemcpyAsync(&bits, imag, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    SETUP_CUDA(cudaStreamSynchronize(st));
+    memcpy(&p->imag_max, &bits, sizeof(double));
+    p->launches += 1 + 6 * (2 + (Py > 1) + (Pz > 1));
+    p->setup_done = true;
+    g_err.clear();
+    return done(DEMAG_OK);
+#undef SETUP_CUDA
+}
+
+demag_status demag_field(demag_plan_t p, const void *M, void *H, void *stream)
+{
+    if (!H) return fail(DEMAG_ERR_INVALID_ARG, "H is NULL");
+    return run_job(p, plain_job(M, H, nullptr), stream);
+}
+
+demag_status demag_field_adjoint(demag_plan_t p, const void *G, void *out, void *stream)
+{
+    // N_ij = N_ji and N(-r) = N(r): the operator equals its adjoint.
+    if (!out) return fail(DEMAG_ERR_INVALID_ARG, "out is NULL");
+    return run_job(p, plain_job(G, out, nullptr), stream);
+}
+
+demag_status demag_field_energy(demag_plan_t p, const void *M, void *H, double *E_dev, void *stream)
+{
+    if (!E_dev) return fail(DEMAG_ERR_INVALID_ARG, "E_dev is NULL");
+    if (!H) return fail(DEMAG_ERR_INVALID_ARG, "H is NULL");
+    return run_job(p, plain_job(M, H, E_dev), stream);
+}
+
+demag_status demag_energy(demag_plan_t p, const void *M, double *E_out, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!E_out) return fail(DEMAG_ERR_INVALID_ARG, "E_out is NULL");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    demag_status s = run_job(p, plain_job(M, nullptr, p->e_dev), stream);
+    if (s != DEMAG_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    DEMAG_CUDA(cudaMemcpyAsync(E_out, p->e_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(cudaStreamSynchronize(st));
+    return DEMAG_OK;
+}
+
+demag_status demag_field_host(demag_plan_t p, const void *M_host, void *H_host, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!M_host || !H_host) return fail(DEMAG_ERR_INVALID_ARG, "host buffers must not be NULL");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
+    if (!p->dM) DEMAG_CUDA(cudaMalloc(&p->dM, bytes));
+    if (!p->dH) DEMAG_CUDA(cudaMalloc(&p->dH, bytes));
+    cudaStream_t st = (cudaStream_t)stream;
+    DEMAG_CUDA(cudaMemcpyAsync(p->dM, M_host, bytes, cudaMemcpyHostToDevice, st));
+    demag_status s = run_job(p, plain_job(p->dM, p->dH, nullptr), stream);
+    if (s != DEMAG_OK) return s;
+    DEMAG_CUDA(cudaMemcpyAsync(H_host, p->dH, bytes, cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(cudaStreamSynchronize(st));
+    return DEMAG_OK;
+}
+
+demag_status demag_energy_grad(demag_plan_t p, const void *m, const void *w, double Ms, double *E_dev,
+                               void *grad, const double *gscale_dev, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!isfinite(Ms)) return fail(DEMAG_ERR_INVALID_ARG, "Ms must be finite");
+    FieldJob j;
+    j.in = m; j.wcell = w; j.wscalar = Ms;
+    j.out = grad;
+    // dE/dm = Ms w dE/dM = -mu0 V Ms w H (the operator is self-adjoint)
+    j.oscale = -kMu0 * p->dx * p->dy * p->dz * Ms;
+    j.gdev = gscale_dev;
+    j.E_dev = E_dev;
+    return run_job(p, j, stream);
+}
+
+demag_status demag_plan_info(demag_plan_t p, demag_info *info)
+{
+    if (!p || !info) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
+    info->nx = p->nx; info->ny = p->ny; info->nz = p->nz;
+    info->px = p->Px; info->py = p->Py; info->pz = p->Pz;
+    info->kx = p->Kx;
+    info->prec = p->prec;
+    info->device_bytes = p->device_bytes;
+    info->launches_per_field = 3 + 2 * (p->Py > 1);
+    info->tensor_imag_max = p->imag_max;
+    return DEMAG_OK;
+}
+
+demag_status demag_set_timing(demag_plan_t p, int enable)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    DeviceGuard g(p->device);
+    if (enable && !p->ring) {
+        TimingRing *R = new TimingRing;
+        memset(R, 0, sizeof(*R));
+        for (int s = 0; s < kRing; ++s)
+            for (int i = 0; i < kEvPerCall; ++i) DEMAG_CUDA(cudaEventCreate(&R->ev[s][i]));
+        p->ring = R;
+    }
+    p->timing = enable != 0;
+    for (int i = 0; i < 8; ++i) { p->pass_ms[i] = 0; p->pass_n[i] = 0; }
+    if (p->ring) {
+        TimingRing *R = ring_of(p);
+        for (int s = 0; s < kRing; ++s) R->used[s] = 0;
+        R->next = 0;
+    }
+    return DEMAG_OK;
+}
+
+demag_status demag_get_timing(demag_plan_t p, double *ms, long *counts, int n)
+{
+    if (!p || !ms || !counts || n < 0 || n > 8) return fail(DEMAG_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(p->device);
+    if (p->ring) {
+        TimingRing *R = ring_of(p);
+        for (int s = 0; s < kRing; ++s)
+            if (R->used[s]) ring_collect_slot(p, R, s);
+    }
+    for (int i = 0; i < n; ++i) { ms[i] = p->pass_ms[i]; counts[i] = p->pass_n[i]; }
+    return DEMAG_OK;
+}
+
+long demag_launch_count(demag_plan_t p) { return p ? p->launches : 0; }
+
+}  // extern "C"

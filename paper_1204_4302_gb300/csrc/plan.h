@@ -1,0 +1,111 @@
+// Internal declarations shared by the C-ABI layer and the kernel translation
+// units. Not part of the public interface (see include/demag.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "demag.h"
+
+namespace demag {
+
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+
+// Prologue / epilogue options of the x passes.
+// Input scaling: value = in * wscalar * (wcell ? wcell[cell] : 1), where wcell
+// is a per-cell weight [nz][ny][nx] shared by the three components (a
+// saturation-magnetization mask).
+template <typename T> struct XIn {
+    const T *in;
+    int64_t in_rs;
+    const T *wcell;
+    T wscalar;
+    int rows_per_comp;  // nz * ny rows per component (to index wcell)
+};
+// Output: h = scale * (inverse transform). If out: out = h * oscale * w * g
+// with w = wcell[cell] (or 1) and g = *gdev (or 1). If partials: the block's
+// sum of mscale * w * Mref * h is written to partials[blockIdx.x].
+template <typename T> struct XOut {
+    T *out;
+    int64_t out_rs;
+    T scale;
+    T oscale;
+    const T *wcell;
+    const double *gdev;
+    const T *Mref;
+    T mscale;
+    double *partials;
+    int rows_per_comp;
+};
+
+// Launchers of the field passes for element type T (defined in
+// passes_f32.cu / passes_f64.cu). L is the transform length of the pass.
+template <typename T> struct Passes {
+    using C = typename CplxOf<T>::type;
+    // real-to-complex along x; L = Px/2 (complex length), Px >= 2
+    static cudaError_t x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *out, int64_t out_rs,
+                             const C *twx, cudaStream_t st);
+    // complex-to-real along x with the XOut epilogue
+    static cudaError_t x_inv(int L, const C *in, int64_t in_rs, int nrows, int nvalid, const XOut<T> &o,
+                             const C *twx, cudaStream_t st);
+    static int x_blocks(int L, int nrows);
+    // strided column transforms (y passes, z forward of the setup)
+    static cudaError_t col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss,
+                           int64_t irs, int nin, int64_t oss, int64_t ors, int nout, const C *tw,
+                           int twstride, cudaStream_t st);
+    // fused z forward, spectral product, z inverse (in place)
+    static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+                             int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
+                             cudaStream_t st);
+    // Px == 1: rows of one value; same prologue / epilogue as above
+    static cudaError_t x1_fwd(const XIn<T> &a, int64_t n, C *out, cudaStream_t st);
+    static cudaError_t x1_inv(const C *in, int64_t n, const XOut<T> &o, int nblocks, cudaStream_t st);
+};
+
+// Tensor setup kernels (tensor.cu).
+cudaError_t tensor_octant(double *out, int nx, int ny, int nz, double dx, double dy, double dz,
+                          cudaStream_t st);
+cudaError_t tensor_wrap(const double *oct, int comp, int nx, int ny, int nz, int Px, int Py,
+                        int Pz, double *out, cudaStream_t st);
+cudaError_t tensor_extract(const double2 *S, int comp, int Px, int Py, int Pz, int Kxp,
+                           double *nhat64, float *nhat32, unsigned long long *imag_max,
+                           cudaStream_t st);
+cudaError_t energy_finalize(const double *partials, int n, double factor, double *E,
+                            cudaStream_t st);
+
+}  // namespace demag
+
+// The opaque plan.
+struct demag_plan {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    demag_prec prec;
+    int Px, Py, Pz, Kx, Kxp;
+    int device;
+    size_t device_bytes;
+    // spectra: S1 [3][nz][ny][Kxp], S2 [3][nz][Py][Kxp] (S2 == S1 when Py == 1)
+    void *S1, *S2;
+    // tensor spectrum [6][Pz/2+1][Py/2+1][Kx]
+    double *nhat64;
+    float *nhat32;
+    // forward twiddle tables W_P^m, m < P, per axis
+    double2 *tw64[3];
+    float2 *tw32[3];
+    // energy: per-block partial sums and plan-owned outputs
+    double *partials;
+    int npartials;
+    double *e_dev;
+    // host-buffer entry point buffers
+    void *dM, *dH;
+    bool setup_done;
+    double imag_max;
+    // timing
+    bool timing;
+    void *ring;  // per-kernel timing events (api.cu)
+    double pass_ms[8];
+    long pass_n[8];
+    long launches;
+};

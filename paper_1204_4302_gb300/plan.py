@@ -1,0 +1,144 @@
+"""Torch-facing wrapper of a libdemag plan.
+
+PyTorch only provides device memory and the current stream here; every
+operation is one call into the C ABI (``binding``). Fields are tensors of
+shape (3, nz, ny, nx), float32 for ``prec="f32"`` plans and float64 for
+``prec="f64"``, contiguous, on the plan's CUDA device.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+
+class Plan:
+    """Stray field of an nx x ny x nz grid of cells with edges (dx, dy, dz)."""
+
+    def __init__(self, n, d, prec: str = "f32", pad=None, device=None, setup: bool = True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdemag needs a CUDA device; there is no CPU path")
+        self.n = tuple(int(v) for v in n)
+        self.d = tuple(float(v) for v in d)
+        if prec not in ("f32", "f64"):
+            raise ValueError("prec must be 'f32' or 'f64'")
+        self.prec = prec
+        self.dtype = torch.float32 if prec == "f32" else torch.float64
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        nx, ny, nz = self.n
+        code = B.DEMAG_F32 if prec == "f32" else B.DEMAG_F64
+        self.handle = None
+        with torch.cuda.device(self.device):
+            if pad is None:
+                self.handle = B.demag_plan_create(nx, ny, nz, *self.d, code)
+            else:
+                self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, *pad)
+        self.shape = (3, nz, ny, nx)
+        if setup:
+            self.setup()
+
+    # ------------------------------------------------------------------ basics
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _field_arg(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(t, torch.Tensor) or t.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if t.dtype != self.dtype:
+            raise ValueError(f"{name} must be {self.dtype} for a {self.prec} plan")
+        if tuple(t.shape) != self.shape:
+            raise ValueError(f"{name} must have shape {self.shape}, got {tuple(t.shape)}")
+        return t.contiguous()
+
+    def _cell_arg(self, w):
+        if w is None:
+            return None
+        nx, ny, nz = self.n
+        if not isinstance(w, torch.Tensor) or w.device != self.device or w.dtype != self.dtype:
+            raise ValueError(f"the cell weight must be a {self.dtype} tensor on {self.device}")
+        if tuple(w.shape) != (nz, ny, nx):
+            raise ValueError(f"the cell weight must have shape {(nz, ny, nx)}")
+        return w.contiguous()
+
+    def setup(self):
+        with torch.cuda.device(self.device):
+            B.demag_tensor_setup(self.handle, self._stream())
+
+    def info(self) -> dict:
+        return B.demag_plan_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            B.demag_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ ops
+    def field(self, M: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """H = -N * M (paper Sec. 3.1, Eq. "demag")."""
+        M = self._field_arg(M, "M")
+        H = torch.empty_like(M) if out is None else self._field_arg(out, "out")
+        B.demag_field(self.handle, M.data_ptr(), H.data_ptr(), self._stream())
+        return H
+
+    def field_adjoint(self, G: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        G = self._field_arg(G, "G")
+        R = torch.empty_like(G) if out is None else self._field_arg(out, "out")
+        B.demag_field_adjoint(self.handle, G.data_ptr(), R.data_ptr(), self._stream())
+        return R
+
+    def field_energy(self, M: torch.Tensor, out: torch.Tensor | None = None):
+        """(H, E) with E a float64 device scalar, E = -(mu0/2) V sum M.H."""
+        M = self._field_arg(M, "M")
+        H = torch.empty_like(M) if out is None else self._field_arg(out, "out")
+        E = torch.empty((), dtype=torch.float64, device=self.device)
+        B.demag_field_energy(self.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), self._stream())
+        return H, E
+
+    def energy(self, M: torch.Tensor) -> float:
+        M = self._field_arg(M, "M")
+        return B.demag_energy(self.handle, M.data_ptr(), self._stream())
+
+    def energy_grad(self, m: torch.Tensor, Ms: float, w: torch.Tensor | None = None,
+                    want_energy: bool = True, want_grad: bool = True,
+                    gscale: torch.Tensor | None = None):
+        """E and g * dE/dm for M = Ms * w * m, in one pass of the pipeline."""
+        m = self._field_arg(m, "m")
+        w = self._cell_arg(w)
+        E = torch.empty((), dtype=torch.float64, device=self.device) if want_energy else None
+        G = torch.empty_like(m) if want_grad else None
+        if gscale is not None:
+            if gscale.dtype != torch.float64 or gscale.numel() != 1 or gscale.device != self.device:
+                raise ValueError("gscale must be a float64 device scalar")
+            gscale = gscale.contiguous()
+        B.demag_energy_grad(self.handle, m.data_ptr(), None if w is None else w.data_ptr(), float(Ms),
+                            None if E is None else E.data_ptr(), None if G is None else G.data_ptr(),
+                            None if gscale is None else gscale.data_ptr(), self._stream())
+        return E, G
+
+    def field_host(self, M_host, H_host=None):
+        """End to end from host memory: copies in, computes, copies out, syncs.
+        M_host / H_host: CPU tensors (pinned for full bandwidth)."""
+        if M_host.device.type != "cpu" or M_host.dtype != self.dtype or tuple(M_host.shape) != self.shape:
+            raise ValueError("M_host must be a CPU tensor of the plan's dtype and shape")
+        M_host = M_host.contiguous()
+        if H_host is None:
+            H_host = torch.empty(self.shape, dtype=self.dtype, pin_memory=M_host.is_pinned())
+        B.demag_field_host(self.handle, M_host.data_ptr(), H_host.data_ptr(), self._stream())
+        return H_host
+
+    # ------------------------------------------------------------------ timing
+    def set_timing(self, enable: bool = True):
+        B.demag_set_timing(self.handle, enable)
+
+    def get_timing(self, n: int = 6):
+        return B.demag_get_timing(self.handle, n)
+
+    def launch_count(self) -> int:
+        return B.demag_launch_count(self.handle)

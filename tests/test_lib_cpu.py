@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every entry point include/demag.h declares, and fails cleanly (a
+status, not a crash) when no CUDA device is present."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "demag.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(demag_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1204_4302_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1204_4302_gb300 import binding
+    declared = _declared()
+    assert len(declared) >= 16
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(binding.EXPORTS) == declared
+
+
+def test_status_strings(lib):
+    from paper_1204_4302_gb300 import binding
+    for code, name in binding.STATUS.items():
+        assert binding.demag_status_string(code) == name
+
+
+def test_invalid_arguments_are_rejected_before_any_device_call(lib):
+    from paper_1204_4302_gb300 import binding
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create(0, 4, 4, 1.0, 1.0, 1.0)
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create(4, 4, 4, -1.0, 1.0, 1.0)
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create(513, 4, 4, 1.0, 1.0, 1.0)
+    assert e.value.name == "DEMAG_ERR_UNSUPPORTED"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, 12, 0, 0)  # not a power of two
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, 8, 0, 0)  # below 2n - 1
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_field(None, None, None)
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+    with pytest.raises(binding.DemagError):
+        binding.demag_energy(None, None)
+    binding.demag_plan_destroy(None)
+    assert binding.demag_launch_count(None) == 0
+
+
+def test_no_device_gives_a_cuda_status():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1204_4302_gb300 import binding
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create(4, 4, 4, 1.0, 1.0, 1.0)
+    assert e.value.name in ("DEMAG_ERR_CUDA", "DEMAG_ERR_OOM")
+
+
+def test_plan_refuses_without_cuda():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1204_4302_gb300.plan import Plan
+    with pytest.raises(RuntimeError):
+        Plan((4, 4, 4), (1.0, 1.0, 1.0))
+
+
+def test_inputs_module_is_independent():
+    """The input generators import neither the library nor the oracle."""
+    src = open(os.path.join(ROOT, "paper_1204_4302_gb300", "inputs.py")).read()
+    assert "import oracle" not in src and "binding" not in src and "torch" not in src
