@@ -96,6 +96,13 @@ bool overlap(const void *a, const void *b, size_t bytes)
     return x < y + bytes && y < x + bytes;
 }
 
+// [a, a + abytes) and [b, b + bbytes) intersect
+bool overlap2(const void *a, size_t abytes, const void *b, size_t bbytes)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bbytes && y < x + abytes;
+}
+
 // Twiddle table W_P^m = exp(-2 pi i m / P), m < P, from long double sin/cos.
 template <typename C>
 std::vector<C> twiddles(int P)
@@ -278,7 +285,7 @@ demag_status run_job(demag_plan *p, const FieldJob &job, void *stream)
     }
     if (job.wcell) {
         if ((s = check_dev_ptr(p, job.wcell, "cell weight")) != DEMAG_OK) return s;
-        if (job.out && overlap(job.wcell, job.out, bytes))
+        if (job.out && overlap2(job.wcell, bytes / 3, job.out, bytes))
             return fail(DEMAG_ERR_INVALID_ARG, "output overlaps the cell weight");
     }
     if (job.gdev && (s = check_scalar_ptr(job.gdev, "gradient scale")) != DEMAG_OK) return s;

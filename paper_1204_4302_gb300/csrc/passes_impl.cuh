@@ -9,10 +9,12 @@ namespace demag {
 
 namespace {
 
-template <typename KernelT>
-cudaError_t allow_smem(KernelT kern, size_t bytes)
+// Opt in to more than 48 KB of dynamic shared memory, once per kernel and
+// device (the cache is per template argument, i.e. per kernel).
+template <auto Kern>
+cudaError_t allow_smem(size_t bytes)
 {
-    // Opt in to more than 48 KB of dynamic shared memory once per device.
+    const auto kern = Kern;
     static int done_for = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -63,7 +65,7 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
         if constexpr (LL <= 512) {                                                            \
             using S = TileShape<T, LL>;                                                       \
             const size_t sm = swsize(LL * S::TC) * sizeof(C);                                 \
-            cudaError_t e = allow_smem(k_x_fwd<T, LL>, sm);                                   \
+            cudaError_t e = allow_smem<k_x_fwd<T, LL>>(sm);                                   \
             if (e != cudaSuccess) return e;                                                   \
             const int grid = (nrows + S::TC - 1) / S::TC;                                     \
             k_x_fwd<T, LL><<<grid, S::NT, sm, st>>>(a, nrows, nvalid, out, out_rs, twx); \
@@ -93,7 +95,7 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
         if constexpr (LL <= 512) {                                                            \
             using S = TileShape<T, LL>;                                                       \
             const size_t sm = swsize(LL * S::TC) * sizeof(C);                                 \
-            cudaError_t e = allow_smem(k_x_inv<T, LL>, sm);                                   \
+            cudaError_t e = allow_smem<k_x_inv<T, LL>>(sm);                                   \
             if (e != cudaSuccess) return e;                                                   \
             const int grid = (nrows + S::TC - 1) / S::TC;                                     \
             k_x_inv<T, LL><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx);           \
@@ -118,12 +120,12 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
         const size_t sm = swsize(LL * S::TC) * sizeof(C);                                     \
         const int grid = (ncols + S::TC - 1) / S::TC;                                         \
         if (inv) {                                                                            \
-            cudaError_t e = allow_smem(k_col_fft<T, LL, true>, sm);                           \
+            cudaError_t e = allow_smem<k_col_fft<T, LL, true>>(sm);                           \
             if (e != cudaSuccess) return e;                                                   \
             k_col_fft<T, LL, true><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, \
                                                            oss, ors, nout, tw, twstride);     \
         } else {                                                                              \
-            cudaError_t e = allow_smem(k_col_fft<T, LL, false>, sm);                          \
+            cudaError_t e = allow_smem<k_col_fft<T, LL, false>>(sm);                          \
             if (e != cudaSuccess) return e;                                                   \
             k_col_fft<T, LL, false><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, \
                                                             oss, ors, nout, tw, twstride);    \
@@ -144,7 +146,7 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
     case LL: {                                                                                \
         using Sh = TileShape<T, LL>;                                                          \
         const size_t sm = 3 * swsize(LL * Sh::TC) * sizeof(C);                                \
-        cudaError_t e = allow_smem(k_z_conv<T, LL>, sm);                                      \
+        cudaError_t e = allow_smem<k_z_conv<T, LL>>(sm);                                      \
         if (e != cudaSuccess) return e;                                                       \
         const int grid = (ncols + Sh::TC - 1) / Sh::TC;                                       \
         k_z_conv<T, LL><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, \
