@@ -155,6 +155,37 @@ demag_status demag_plan_info(demag_plan_t plan, demag_info *info);
 demag_status demag_set_timing(demag_plan_t plan, int enable);
 demag_status demag_get_timing(demag_plan_t plan, double *ms, long *counts, int n);
 
+/* Energy E = -(mu0/2) dx dy dz sum M.H of a field pair the caller already
+ * holds, without any memory allocation. The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory where they
+ * need the energy, for example code that runs while a stream is captured
+ * into a CUDA graph in the global capture mode (where cudaMalloc is
+ * illegal), hosts that hand out device memory only through their own pool,
+ * and tight loops in which an allocation, which can synchronise the device,
+ * is not acceptable. No plan is needed.
+ *   nx, ny, nz, dx, dy, dz: grid and cell edges (V = dx dy dz);
+ *   prec: element type of M and H (DEMAG_F32 float, DEMAG_F64 double);
+ *   M, H: device, [3][nz][ny][nx], 16-byte aligned, on the current device;
+ *   E_dev: device double receiving E (8-byte aligned).
+ * The per-block partial sums live in one fixed 512 KB device array owned by
+ * the library (a file-scope __device__ array that every GPU loading the
+ * library holds until the process exits). It fits 3 nx ny nz <= 65536 * 8192
+ * values (178956970 cells); larger grids return DEMAG_ERR_UNSUPPORTED.
+ * Every call on a device shares that array and leaves its last contents
+ * there; each call overwrites every slot it reads, so nothing needs clearing.
+ * Calls that overlap on the GPU (e.g. on two streams at once) race on it:
+ * order them on one stream or with events.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and may load the
+ * library's kernels; make that first call before any stream capture.
+ * Asynchronous; no cudaMalloc, cudaFree or other allocating call.
+ * Returns DEMAG_ERR_INVALID_ARG for bad sizes, precision or pointers and
+ * DEMAG_ERR_CUDA if the set-up or a launch fails. demag_last_error() is not
+ * updated by this call. */
+demag_status demag_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
+                                  demag_prec prec, const void *M, const void *H, double *E_dev,
+                                  void *stream);
+
 /* Number of kernels this plan has launched since creation. */
 long demag_launch_count(demag_plan_t plan);
 

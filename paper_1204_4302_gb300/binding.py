@@ -32,6 +32,7 @@ EXPORTS = [
     "demag_field_adjoint", "demag_field_energy", "demag_energy", "demag_energy_grad",
     "demag_field_host", "demag_plan_info", "demag_set_timing", "demag_get_timing",
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
+    "demag_energy_noalloc",
 ]
 
 
@@ -92,6 +93,7 @@ def load(path: str | Path | None = None):
         "demag_plan_destroy": (None, [P]),
         "demag_last_error": (ctypes.c_char_p, []),
         "demag_status_string": (ctypes.c_char_p, [I]),
+        "demag_energy_noalloc": (S, [I, I, I, D, D, D, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +191,14 @@ def demag_plan_destroy(plan):
 def demag_last_error() -> str:
     m = load().demag_last_error()
     return m.decode() if m else ""
+
+
+def demag_energy_noalloc(nx, ny, nz, dx, dy, dz, prec, M, H, E_dev, stream=0):
+    """Energy of a field pair without any allocation (see include/demag.h)."""
+    status = load().demag_energy_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                         int(prec), _p(M), _p(H), _p(E_dev), _p(stream))
+    if status != 0:
+        raise DemagError(status, "demag_energy_noalloc", "see include/demag.h for the conditions")
 
 
 def demag_status_string(s: int) -> str:
