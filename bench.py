@@ -455,9 +455,13 @@ def main():
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global N_GRID
+    if args.grid:
+        N_GRID = (args.grid,) * 3
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

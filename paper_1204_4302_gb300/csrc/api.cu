@@ -10,6 +10,7 @@
 // "demag" evaluated through Eq. "convolution").
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -222,7 +223,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     tm.mark();
     // z forward . product . z inverse
     e = Passes<T>::zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat, Py, Kx,
-                         twz, 1, st);
+                         twz, 1, st, p->zvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("z convolution: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -378,6 +379,7 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
     p->Px = P[0]; p->Py = P[1]; p->Pz = P[2];
     p->Kx = P[0] == 1 ? 1 : P[0] / 2 + 1;
     p->Kxp = P[0] == 1 ? 1 : (p->Kx + 1) / 2 * 2;
+    if (const char *zv = getenv("DEMAG_ZVARIANT")) p->zvariant = atoi(zv) == 1 ? 1 : 0;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
         delete p;

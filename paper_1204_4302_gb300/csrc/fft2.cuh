@@ -1,0 +1,580 @@
+// Two-stage register FFT kernels for the strided passes (y forward / inverse
+// and the fused z pass). A column of length L = R1 * R2 is transformed by
+// one radix-R1 stage and one radix-R2 stage, each a register DFT, with a
+// single exchange through shared memory in between (Stockham order, the
+// output in natural order). Columns with L <= 16 are transformed whole by one
+// thread, with no exchange.
+//
+// The zero padding of the convolution is used twice: the forward input has
+// at most L/2 non-zero rows, so the upper half of every first-stage input is
+// zero at compile time; the inverse output is needed for at most L/2 rows, so
+// the last stage computes only the lower half.
+#pragma once
+#include "fft_engine.cuh"
+
+namespace demag {
+
+// Radix pair (R1, R2) of a two-stage column transform of length L.
+template <int L> struct ColRadix;
+template <> struct ColRadix<32> { static constexpr int R1 = 8, R2 = 4; };
+template <> struct ColRadix<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct ColRadix<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct ColRadix<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct ColRadix<512> { static constexpr int R1 = 32, R2 = 16; };
+template <> struct ColRadix<1024> { static constexpr int R1 = 32, R2 = 32; };
+
+// Radix pair of the fused z pass: the second stage keeps three components in
+// registers for the tensor product, so R2 = 16.
+template <int L> struct ZRadix { static constexpr int R2 = 16, R1 = L / 16; };
+
+template <typename T> struct Tile2 { static constexpr int NT = 256; };
+template <> struct Tile2<double> { static constexpr int NT = 128; };
+
+// Columns per CTA: the stage with fewer butterflies per column gives one
+// butterfly to every thread, the other stage loops.
+template <typename T, int L> struct ColShape {
+    static constexpr int R1 = ColRadix<L>::R1, R2 = ColRadix<L>::R2;
+    static constexpr int NT = Tile2<T>::NT;
+    static constexpr int TC = NT / (R1 < R2 ? R1 : R2);
+};
+// z pass: every thread owns one stage-2 butterfly (three components); the
+// CTA size NT is a tuning choice (variant 0: Tile2 threads, 1: half).
+// Variant 0: TC = Tile2 threads / R1 columns; when R1 = 2 R2 the CTA has
+// 3 TC R2 threads so both stage-1 passes give each thread one butterfly.
+// Variant 1: half the columns.
+template <typename T, int L, int V = 0> struct ZShape {
+    static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2;
+    static constexpr int TC = (V == 0 ? Tile2<T>::NT : Tile2<T>::NT / 2) / R1;
+    static constexpr int NT = R1 == 2 * R2 ? 3 * TC * R2 : TC * R1;
+};
+
+// v[r] *= W_L^(r * k) (or its conjugate), table W_L^m at tw[m * twstride]
+template <int R, int L, bool INV, typename C>
+__device__ __forceinline__ void twiddle_row(C *v, int k, const C *__restrict__ tw, int twstride)
+{
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const C w = __ldg(&tw[((r * k) % L) * twstride]);
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+}
+
+// 4-byte asynchronous global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------- columns
+// Strided column transform, column f = slab * width + off, element r at
+// slab * ss + r * rs + off. PIN: rows >= L/2 of the input are zero (nin <=
+// L/2). POUT: only rows < L/2 are stored (nout <= L/2).
+template <typename T, int L, bool INV, bool PIN, bool POUT>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
+       const typename Cplx<T>::type *__restrict__ tw, int twstride)
+{
+    using C = typename Cplx<T>::type;
+    using S = ColShape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TC = S::TC;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int f0 = blockIdx.x * TC;
+    // stage 1: radix R1 over rows j1 + r R2, j1 < R2
+#pragma unroll
+    for (int q = 0; q < (TC * R2 + NT - 1) / NT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b < TC * R2) {
+            const int c = b % TC, j1 = b / TC, f = f0 + c;
+            C u[R1];
+            const bool ok = f < ncols;
+            int64_t base = 0;
+            if (ok) {
+                const int slab = f / width;
+                base = (int64_t)slab * iss + (f - slab * width);
+            }
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int row = j1 + r * R2;
+                u[r] = cmk<C>(0, 0);
+                if (!(PIN && r >= R1 / 2) && ok && row < nin) u[r] = in[base + (int64_t)row * irs];
+            }
+            RegDFT<R1, INV, C>::run(u);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
+        }
+    }
+    __syncthreads();
+    // stage 2: radix R2 over rows j2 + r R1, j2 < R1; output rows j2 + r R1
+#pragma unroll
+    for (int q = 0; q < (TC * R1 + NT - 1) / NT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b < TC * R1) {
+            const int c = b % TC, j2 = b / TC, f = f0 + c;
+            C v[R2];
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[r] = sm[sw((j2 + r * R1) * TC + c)];
+            twiddle_row<R2, L, INV>(v, j2, tw, twstride);
+            RegDFT<R2, INV, C>::run(v);
+            if (f < ncols) {
+                const int slab = f / width;
+                const int64_t base = (int64_t)slab * oss + (f - slab * width);
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    const int row = j2 + r * R1;
+                    if (!(POUT && r >= R2 / 2) && row < nout) out[base + (int64_t)row * ors] = v[r];
+                }
+            }
+        }
+    }
+}
+
+// Short columns (L <= 16): one thread per column, no shared memory.
+template <typename T, int L, bool INV>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_col1(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout)
+{
+    using C = typename Cplx<T>::type;
+    const int f = blockIdx.x * Tile2<T>::NT + threadIdx.x;
+    if (f >= ncols) return;
+    const int slab = f / width, off = f - slab * width;
+    const int64_t bi = (int64_t)slab * iss + off, bo = (int64_t)slab * oss + off;
+    C u[L];
+#pragma unroll
+    for (int r = 0; r < L; ++r) u[r] = r < nin ? in[bi + (int64_t)r * irs] : cmk<C>(0, 0);
+    RegDFT<L, INV, C>::run(u);
+#pragma unroll
+    for (int r = 0; r < L; ++r)
+        if (r < nout) out[bo + (int64_t)r * ors] = u[r];
+}
+
+// ---------------------------------------------------------------- z pass
+// Tensor product at one frequency: h = -N^ m with the folded, parity-signed
+// tensor spectrum (see k_z_conv).
+template <typename T, typename C>
+__device__ __forceinline__ void tensor_product(const T *__restrict__ nhat, int64_t plane, int64_t b, T sy,
+                                               T sz, C &x, C &y, C &z)
+{
+    const T nxx = __ldg(&nhat[b]), nyy = __ldg(&nhat[plane + b]), nzz = __ldg(&nhat[2 * plane + b]);
+    const T nxy = sy * __ldg(&nhat[3 * plane + b]);
+    const T nxz = sz * __ldg(&nhat[4 * plane + b]);
+    const T nyz = sy * sz * __ldg(&nhat[5 * plane + b]);
+    const C mx = x, my = y, mz = z;
+    x = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+    y = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+    z = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+}
+
+// Order of the ky rows over the z-pass CTAs: 0, Py/2, 1, Py-1, 2, Py-2, ...
+// so that the two rows sharing a folded tensor row run at about the same
+// time and the second read of that tensor block hits L2.
+__device__ __forceinline__ int ky_pair_order(int i, int Py)
+{
+    if (i == 0) return 0;
+    if (i == 1) return Py / 2;
+    const int m = i >> 1;
+    return (i & 1) ? Py - m : m;
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem)
+{
+    if constexpr (sizeof(T) == 4) cp_async4(smem, gmem);
+    else cp_async8(smem, gmem);
+}
+
+// Fused z pass, two stages (L >= 32): forward stage 1 (radix R1, rows < nrows
+// read, upper half zero) for the three components into shared memory;
+// forward stage 2 (radix R2) into registers, which then hold the three
+// components at the frequencies kz = j2 + r R1; tensor product in
+// registers; inverse stage 1 (radix R2) in registers back to shared memory;
+// inverse stage 2 (radix R1) stores the rows z < nrows. Column f = i * width
+// + kx with ky = ky_pair_order(i). The CTA's block of the tensor spectrum
+// ([6][L/2+1][Py/2+1][Kx], folded in ky and kz) is copied to shared memory
+// asynchronously while the first stage runs.
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(ZShape<T, L, V>::NT, 1)
+k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+          int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
+          int twstride)
+{
+    using C = typename Cplx<T>::type;
+    using Sh = ZShape<T, L, V>;
+    constexpr int R1 = Sh::R1, R2 = Sh::R2, NT = Sh::NT, TC = Sh::TC;
+    constexpr int TS = swsize(L * TC);
+    constexpr int NB1 = TC * R2;  // stage-1 butterflies per component
+    constexpr int HZ = L / 2 + 1;
+    static_assert(NT % TC == 0, "tensor prefetch assumes TC divides the threads");
+    static_assert((R1 * TC) % 32 == 0 && (R2 * TC) % 32 == 0, "shared-memory offsets need 32-aligned rows");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    T *smT = reinterpret_cast<T *>(sm + 3 * TS);  // [kzf][comp][c] tensor block
+    const int f0 = blockIdx.x * TC;
+    const int hy = Py / 2 + 1;
+    const int64_t plane = (int64_t)HZ * hy * Kx;
+
+    {
+        const int c = threadIdx.x % TC, f = f0 + c;
+        if (f < ncols) {
+            const int i = f / width, kx = f - i * width;
+            const int ky = ky_pair_order(i, Py);
+            const int kyf = ky > Py / 2 ? Py - ky : ky;
+            const T *src = nhat + (int64_t)kyf * Kx + kx;
+            for (int idx = threadIdx.x / TC; idx < HZ * 6; idx += NT / TC) {
+                const int kzf = idx / 6, comp = idx - kzf * 6;
+                cp_async_elem(&smT[idx * TC + c], src + comp * plane + (int64_t)kzf * hy * Kx);
+            }
+        }
+    }
+
+    // forward stage 1, three components: rows j1 + r R2 -> rows j1 R1 + r
+#pragma unroll
+    for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b < 3 * NB1) {
+            const int comp = b / NB1, bb = b - comp * NB1;
+            const int c = bb % TC, j1 = bb / TC, f = f0 + c;
+            C u[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+            if (f < ncols) {
+                const int i = f / width;
+                const C *col = S + (int64_t)ky_pair_order(i, Py) * ss + (f - i * width) + comp * cs + j1 * rs;
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r)
+                    if (j1 + r * R2 < nrows) u[r] = col[(int64_t)r * R2 * rs];
+            }
+            RegDFT<R1, false, C>::run(u);
+            C *s = sm + comp * TS + sw(j1 * R1 * TC + c);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // forward stage 2 + product + inverse stage 1
+    const bool act2 = threadIdx.x < TC * R1;
+    const int c2 = threadIdx.x % TC, j2 = threadIdx.x / TC, f2 = f0 + c2;
+    C v0[R2], v1[R2], v2[R2];
+    if (act2) {
+        const C *s = sm + sw(j2 * TC + c2);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            constexpr int step = R1 * TC + (R1 * TC) / 32;
+            v0[r] = s[r * step];
+            v1[r] = s[TS + r * step];
+            v2[r] = s[2 * TS + r * step];
+        }
+#pragma unroll
+        for (int r = 1; r < R2; ++r) {
+            const C w = __ldg(&tw[r * j2 * twstride]);
+            v0[r] = cmul(v0[r], w);
+            v1[r] = cmul(v1[r], w);
+            v2[r] = cmul(v2[r], w);
+        }
+        RegDFT<R2, false, C>::run(v0);
+        RegDFT<R2, false, C>::run(v1);
+        RegDFT<R2, false, C>::run(v2);
+        if (f2 < ncols) {
+            const int ky = ky_pair_order(f2 / width, Py);
+            const T sy = ky > Py / 2 ? (T)-1 : (T)1;
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                // kz = j2 + r R1: below L/2 for r < R2/2, above for r > R2/2
+                int kzf;
+                T sz;
+                if (r < R2 / 2) { kzf = j2 + r * R1; sz = (T)1; }
+                else if (r == R2 / 2) { kzf = L / 2 - j2; sz = j2 == 0 ? (T)1 : (T)-1; }
+                else { kzf = (R2 - r) * R1 - j2; sz = (T)-1; }
+                const T *t = smT + kzf * 6 * TC + c2;
+                const T nxx = t[0], nyy = t[TC], nzz = t[2 * TC];
+                const T nxy = sy * t[3 * TC], nxz = sz * t[4 * TC], nyz = sy * sz * t[5 * TC];
+                const C mx = v0[r], my = v1[r], mz = v2[r];
+                v0[r] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+                v1[r] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+                v2[r] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+            }
+        }
+        RegDFT<R2, true, C>::run(v0);
+        RegDFT<R2, true, C>::run(v1);
+        RegDFT<R2, true, C>::run(v2);
+    }
+    __syncthreads();  // all stage-2 reads done before the buffers are rewritten
+    if (act2) {
+        C *s = sm + sw(j2 * R2 * TC + c2);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            const int o = r * TC + (r * TC) / 32;
+            s[o] = v0[r];
+            s[TS + o] = v1[r];
+            s[2 * TS + o] = v2[r];
+        }
+    }
+    __syncthreads();
+
+    // inverse stage 2: radix R1 over rows j1 + r R2 (NS = R2), rows < nrows kept
+#pragma unroll
+    for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b < 3 * NB1) {
+            const int comp = b / NB1, bb = b - comp * NB1;
+            const int c = bb % TC, j1 = bb / TC, f = f0 + c;
+            const C *s = sm + comp * TS + sw(j1 * TC + c);
+            C u[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                constexpr int step = R2 * TC + (R2 * TC) / 32;
+                u[r] = s[r * step];
+            }
+#pragma unroll
+            for (int r = 1; r < R1; ++r) u[r] = cmulc(u[r], __ldg(&tw[r * j1 * twstride]));
+            RegDFT<R1, true, C>::run(u);
+            if (f < ncols) {
+                const int i = f / width;
+                C *col = S + (int64_t)ky_pair_order(i, Py) * ss + (f - i * width) + comp * cs + j1 * rs;
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r)
+                    if (j1 + r * R2 < nrows) col[(int64_t)r * R2 * rs] = u[r];
+            }
+        }
+    }
+}
+
+// Fused z pass for L <= 16: one thread per column, all in registers.
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile2<T>::NT, (L >= 16 ? 1 : 2))
+k_z_conv1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+          int nrows, const T *__restrict__ nhat, int Py, int Kx)
+{
+    using C = typename Cplx<T>::type;
+    const int f = blockIdx.x * Tile2<T>::NT + threadIdx.x;
+    if (f >= ncols) return;
+    const int ky = f / width, kx = f - ky * width;
+    const int64_t base = (int64_t)ky * ss + kx;
+    C a[L], b[L], c[L];
+#pragma unroll
+    for (int r = 0; r < L; ++r) {
+        const bool ok = r < nrows;
+        a[r] = ok ? S[base + (int64_t)r * rs] : cmk<C>(0, 0);
+        b[r] = ok ? S[base + (int64_t)r * rs + cs] : cmk<C>(0, 0);
+        c[r] = ok ? S[base + (int64_t)r * rs + 2 * cs] : cmk<C>(0, 0);
+    }
+    RegDFT<L, false, C>::run(a);
+    RegDFT<L, false, C>::run(b);
+    RegDFT<L, false, C>::run(c);
+    const bool fy = ky > Py / 2;
+    const int kyf = fy ? Py - ky : ky;
+    const T sy = fy ? (T)-1 : (T)1;
+    const int hy = Py / 2 + 1;
+    const int64_t plane = (int64_t)(L / 2 + 1) * hy * Kx;
+#pragma unroll
+    for (int r = 0; r < L; ++r) {
+        const bool fz = r > L / 2;
+        const int kzf = fz ? L - r : r;
+        tensor_product<T>(nhat, plane, ((int64_t)kzf * hy + kyf) * Kx + kx, sy, fz ? (T)-1 : (T)1, a[r], b[r],
+                          c[r]);
+    }
+    RegDFT<L, true, C>::run(a);
+    RegDFT<L, true, C>::run(b);
+    RegDFT<L, true, C>::run(c);
+#pragma unroll
+    for (int r = 0; r < L; ++r)
+        if (r < nrows) {
+            S[base + (int64_t)r * rs] = a[r];
+            S[base + (int64_t)r * rs + cs] = b[r];
+            S[base + (int64_t)r * rs + 2 * cs] = c[r];
+        }
+}
+
+}  // namespace demag
+
+namespace demag {
+
+// ---------------------------------------------------------------- x passes
+// Rows of 2L reals are packed as L complex values z[n] = x[2n] + i x[2n+1]
+// and transformed with two stages, L = R1 * R2 (stage 1 radix R1 by R2
+// threads per row, stage 2 radix R2 by R1 threads per row; R1 <= 32 so a
+// row's stage-2 threads share a warp). The real-to-complex split needs
+// Z[k] and Z[L-k]: Z[j2 + r R1] sits in thread j2, Z[L - j2 - r R1] in thread
+// R1 - j2 at r' = R2 - 1 - r (thread 0 holds its own partners), exchanged by
+// warp shuffles.
+template <int L> struct XRadix;
+template <> struct XRadix<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct XRadix<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct XRadix<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct XRadix<512> { static constexpr int R1 = 32, R2 = 16; };
+
+template <typename T, int L> struct XShape {
+    static constexpr int R1 = XRadix<L>::R1, R2 = XRadix<L>::R2;
+    static constexpr int NT = Tile2<T>::NT;
+    static constexpr int TR = NT / (R1 > R2 ? R1 : R2);  // rows per CTA
+    static constexpr int RS = swsize(L);                 // padded row in shared memory
+};
+
+template <typename C>
+__device__ __forceinline__ C shfl_c(C v, int lane)
+{
+    C r;
+    r.x = __shfl_sync(0xffffffffu, v.x, lane);
+    r.y = __shfl_sync(0xffffffffu, v.y, lane);
+    return r;
+}
+
+// Real-to-complex along x (see k_x_fwd for the packing), two stages.
+// PIN: the row has at most L reals (the zero-padded field), so the upper half
+// of the packed sequence is zero; otherwise all 2L reals are read (setup).
+template <typename T, int L, bool PIN>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
+         const typename Cplx<T>::type *__restrict__ twx)
+{
+    using C = typename Cplx<T>::type;
+    using S = XShape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, TR = S::TR, RS = S::RS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int row0 = blockIdx.x * TR;
+    // stage 1: thread (row, j1) reads z[j1 + r R2] (r < R1/2 when PIN: the rest is padding)
+    if (threadIdx.x < TR * R2) {
+        const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
+        C u[R1];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+        if (row < nrows) {
+            const T *p = a.in + (int64_t)row * a.in_rs;
+            const T ws = a.wscalar;
+#pragma unroll
+            for (int r = 0; r < (PIN ? R1 / 2 : R1); ++r) {
+                const int x0 = 2 * (j1 + r * R2);
+                if (x0 < nvalid) u[r].x = p[x0] * ws * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
+                if (x0 + 1 < nvalid)
+                    u[r].y = p[x0 + 1] * ws * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0 + 1);
+            }
+        }
+        RegDFT<R1, false, C>::run(u);
+        C *s = sm + rr * RS;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+    }
+    __syncthreads();
+    // stage 2 + split: thread (row, j2) computes X[k], k = j2 + r R1
+    if (threadIdx.x < TR * R1) {
+        const int rr = threadIdx.x / R1, j2 = threadIdx.x % R1, row = row0 + rr;
+        const C *s = sm + rr * RS;
+        C v[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], __ldg(&twx[2 * r * j2]));
+        RegDFT<R2, false, C>::run(v);
+        const int lane = threadIdx.x & 31;
+        const int partner = (lane & ~(R1 - 1)) | ((R1 - j2) & (R1 - 1));
+        C X[R2];
+        const T h = (T)0.5;
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            const C q = shfl_c(v[R2 - 1 - r], partner);
+            const C pz = j2 == 0 ? v[(R2 - r) % R2] : q;  // Z[L - k]
+            const int k = j2 + r * R1;
+            const C E = cmk<C>(h * (v[r].x + pz.x), h * (v[r].y - pz.y));
+            const C O = cmk<C>(h * (v[r].y + pz.y), -h * (v[r].x - pz.x));
+            X[r] = cadd(E, cmul(O, __ldg(&twx[k])));
+        }
+        if (row < nrows) {
+            C *o = out + (int64_t)row * out_rs;
+#pragma unroll
+            for (int r = 0; r < R2; ++r) o[j2 + r * R1] = X[r];
+            if (j2 == 0) {
+                // X[L] = E(0) - O(0) (W_{2L}^L = -1), from Z[0]
+                const C z0 = v[0];
+                o[L] = cmk<C>(z0.x - z0.y, (T)0);
+            }
+        }
+    }
+}
+
+// Complex-to-real along x (see k_x_inv), two stages, XOut epilogue.
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
+         const typename Cplx<T>::type *__restrict__ twx)
+{
+    using C = typename Cplx<T>::type;
+    using S = XShape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TR = S::TR, RS = S::RS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int row0 = blockIdx.x * TR;
+    // stage 1: thread (row, j1) builds Z[k], k = j1 + r R2, from X[k] and X[L-k]
+    if (threadIdx.x < TR * R2) {
+        const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
+        C u[R1];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+        if (row < nrows) {
+            const C *p = in + (int64_t)row * in_rs;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int k = j1 + r * R2;
+                const C a = p[k];
+                const C b = p[L - k];
+                const C E2 = cmk<C>(a.x + b.x, a.y - b.y);
+                const C D = cmk<C>(a.x - b.x, a.y + b.y);
+                const C O2 = cmulc(D, __ldg(&twx[k]));
+                u[r] = cmk<C>(E2.x - O2.y, E2.y + O2.x);
+            }
+        }
+        RegDFT<R1, true, C>::run(u);
+        C *s = sm + rr * RS;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+    }
+    __syncthreads();
+    T acc = 0, cmp = 0;
+    if (threadIdx.x < TR * R1) {
+        const int rr = threadIdx.x / R1, j2 = threadIdx.x % R1, row = row0 + rr;
+        const C *s = sm + rr * RS;
+        C v[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
+        RegDFT<R2, true, C>::run(v);
+        if (row < nrows) {
+            const T g = o.gdev ? (T)(*o.gdev) : (T)1;
+            const T oscale = o.oscale * g;
+#pragma unroll
+            for (int r = 0; r < R2 / 2; ++r) {  // z[n], n = j2 + r R1 < L/2
+                const int n = j2 + r * R1;
+                const T hv[2] = {v[r].x * o.scale, v[r].y * o.scale};
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int x = 2 * n + u;
+                    if (x >= nvalid) continue;
+                    const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
+                    const int64_t idx = (int64_t)row * o.out_rs + x;
+                    if (o.out) o.out[idx] = hv[u] * oscale * w;
+                    if (o.partials) {
+                        const T t = o.mscale * w * o.Mref[idx] * hv[u];
+                        const T y = t - cmp, sum = acc + y;
+                        cmp = (sum - acc) - y;
+                        acc = sum;
+                    }
+                }
+            }
+        }
+    }
+    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials);
+}
+
+}  // namespace demag

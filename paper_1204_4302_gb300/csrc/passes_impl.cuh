@@ -2,6 +2,7 @@
 // compile-time kernel instantiations of fft_engine.cuh. Included once per
 // element type (passes_f32.cu, passes_f64.cu).
 #pragma once
+#include "fft2.cuh"
 #include "fft_engine.cuh"
 #include "plan.h"
 
@@ -60,6 +61,21 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
                              const C *twx, cudaStream_t st)
 {
     if (nrows <= 0) return cudaSuccess;
+    if (L >= 64) {
+#define DEMAG_CASE2(LL)                                                                        \
+    case LL: {                                                                                 \
+        using S = XShape<T, LL>;                                                               \
+        const size_t sm = (size_t)S::TR * S::RS * sizeof(C);                                   \
+        const int grid = (nrows + S::TR - 1) / S::TR;                                          \
+        if (nvalid <= LL)                                                                      \
+            k_x_fwd2<T, LL, true><<<grid, S::NT, sm, st>>>(a, nrows, nvalid, out, out_rs, twx); \
+        else                                                                                   \
+            k_x_fwd2<T, LL, false><<<grid, S::NT, sm, st>>>(a, nrows, nvalid, out, out_rs, twx); \
+        return cudaGetLastError();                                                             \
+    }
+        switch (L) { DEMAG_CASE2(64) DEMAG_CASE2(128) DEMAG_CASE2(256) DEMAG_CASE2(512) default: return cudaErrorInvalidValue; }
+#undef DEMAG_CASE2
+    }
 #define DEMAG_CASE(LL)                                                                        \
     case LL: {                                                                                \
         if constexpr (LL <= 512) {                                                            \
@@ -81,8 +97,15 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
 template <typename T>
 int Passes<T>::x_blocks(int L, int nrows)
 {
-    const int tc = (Tile<T>::NT * Tile<T>::EPT) / L;
-    return (nrows + tc - 1) / tc;
+    int rows_per_cta;
+    switch (L) {
+    case 64: rows_per_cta = XShape<T, 64>::TR; break;
+    case 128: rows_per_cta = XShape<T, 128>::TR; break;
+    case 256: rows_per_cta = XShape<T, 256>::TR; break;
+    case 512: rows_per_cta = XShape<T, 512>::TR; break;
+    default: rows_per_cta = (Tile<T>::NT * Tile<T>::EPT) / L;
+    }
+    return (nrows + rows_per_cta - 1) / rows_per_cta;
 }
 
 template <typename T>
@@ -90,6 +113,18 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
                              const C *twx, cudaStream_t st)
 {
     if (nrows <= 0) return cudaSuccess;
+    if (L >= 64) {
+#define DEMAG_CASE2(LL)                                                                        \
+    case LL: {                                                                                 \
+        using S = XShape<T, LL>;                                                               \
+        const size_t sm = (size_t)S::TR * S::RS * sizeof(C);                                   \
+        const int grid = (nrows + S::TR - 1) / S::TR;                                          \
+        k_x_inv2<T, LL><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx);             \
+        return cudaGetLastError();                                                             \
+    }
+        switch (L) { DEMAG_CASE2(64) DEMAG_CASE2(128) DEMAG_CASE2(256) DEMAG_CASE2(512) default: return cudaErrorInvalidValue; }
+#undef DEMAG_CASE2
+    }
 #define DEMAG_CASE(LL)                                                                        \
     case LL: {                                                                                \
         if constexpr (LL <= 512) {                                                            \
@@ -109,51 +144,97 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
 }
 
 template <typename T>
+template <int L, bool INV, bool PIN, bool POUT>
+cudaError_t Passes<T>::col_launch(const C *in, C *out, int ncols, int width, int64_t iss, int64_t irs, int nin,
+                                  int64_t oss, int64_t ors, int nout, const C *tw, int twstride,
+                                  cudaStream_t st)
+{
+    using S = ColShape<T, L>;
+    const size_t sm = swsize(L * S::TC) * sizeof(C);
+    cudaError_t e = allow_smem<k_col2<T, L, INV, PIN, POUT>>(sm);
+    if (e != cudaSuccess) return e;
+    const int grid = (ncols + S::TC - 1) / S::TC;
+    k_col2<T, L, INV, PIN, POUT><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout,
+                                                         tw, twstride);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss,
                            int64_t irs, int nin, int64_t oss, int64_t ors, int nout, const C *tw,
                            int twstride, cudaStream_t st)
 {
     if (ncols <= 0) return cudaSuccess;
-#define DEMAG_CASE(LL)                                                                        \
-    case LL: {                                                                                \
-        using S = TileShape<T, LL>;                                                           \
-        const size_t sm = swsize(LL * S::TC) * sizeof(C);                                     \
-        const int grid = (ncols + S::TC - 1) / S::TC;                                         \
-        if (inv) {                                                                            \
-            cudaError_t e = allow_smem<k_col_fft<T, LL, true>>(sm);                           \
-            if (e != cudaSuccess) return e;                                                   \
-            k_col_fft<T, LL, true><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, \
-                                                           oss, ors, nout, tw, twstride);     \
-        } else {                                                                              \
-            cudaError_t e = allow_smem<k_col_fft<T, LL, false>>(sm);                          \
-            if (e != cudaSuccess) return e;                                                   \
-            k_col_fft<T, LL, false><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, \
-                                                            oss, ors, nout, tw, twstride);    \
-        }                                                                                     \
-        return cudaGetLastError();                                                            \
-    }
-    switch (L) { DEMAG_FOR_EACH_L(DEMAG_CASE) default: return cudaErrorInvalidValue; }
+    if (L <= 16) {
+        // one thread per column
+        const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
+#define DEMAG_CASE(LL)                                                                         \
+    case LL:                                                                                   \
+        if (inv)                                                                               \
+            k_col1<T, LL, true><<<grid, Tile2<T>::NT, 0, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout); \
+        else                                                                                   \
+            k_col1<T, LL, false><<<grid, Tile2<T>::NT, 0, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout); \
+        return cudaGetLastError();
+        switch (L) { DEMAG_CASE(1) DEMAG_CASE(2) DEMAG_CASE(4) DEMAG_CASE(8) DEMAG_CASE(16) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE
+    }
+    // the zero padding halves the input (forward) or the output (inverse)
+    const bool pin = 2 * nin <= L, pout = 2 * nout <= L;
+#define DEMAG_CASE(LL)                                                                         \
+    case LL:                                                                                   \
+        if (!inv && pin) return col_launch<LL, false, true, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
+        if (inv && pout) return col_launch<LL, true, false, true>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
+        if (inv) return col_launch<LL, true, false, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
+        return col_launch<LL, false, false, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st);
+    switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) DEMAG_CASE(1024) default: return cudaErrorInvalidValue; }
+#undef DEMAG_CASE
+}
+
+template <typename T>
+template <int L, int V>
+cudaError_t Passes<T>::zconv_launch(C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                    const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st)
+{
+    using Sh = ZShape<T, L, V>;
+    const size_t sm = 3 * swsize(L * Sh::TC) * sizeof(C) + (L / 2 + 1) * 6 * Sh::TC * sizeof(T);
+    cudaError_t e = allow_smem<k_z_conv2<T, L, V>>(sm);
+    if (e != cudaSuccess) return e;
+    const int grid = (ncols + Sh::TC - 1) / Sh::TC;
+    k_z_conv2<T, L, V><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride);
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
-                             cudaStream_t st)
+                             cudaStream_t st, int variant)
 {
     if (ncols <= 0) return cudaSuccess;
-#define DEMAG_CASE(LL)                                                                        \
-    case LL: {                                                                                \
-        using Sh = TileShape<T, LL>;                                                          \
-        const size_t sm = 3 * swsize(LL * Sh::TC) * sizeof(C);                                \
-        cudaError_t e = allow_smem<k_z_conv<T, LL>>(sm);                                      \
-        if (e != cudaSuccess) return e;                                                       \
-        const int grid = (ncols + Sh::TC - 1) / Sh::TC;                                       \
-        k_z_conv<T, LL><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, \
-                                                 tw, twstride);                               \
-        return cudaGetLastError();                                                            \
+    if (2 * nrows > L && L > 1) return cudaErrorInvalidValue;  // the z pass always has padding
+    if (L <= 16) {
+        const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
+#define DEMAG_CASE(LL)                                                                         \
+    case LL:                                                                                   \
+        k_z_conv1<T, LL><<<grid, Tile2<T>::NT, 0, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx); \
+        return cudaGetLastError();
+        switch (L) { DEMAG_CASE(1) DEMAG_CASE(2) DEMAG_CASE(4) DEMAG_CASE(8) DEMAG_CASE(16) default: return cudaErrorInvalidValue; }
+#undef DEMAG_CASE
     }
-    switch (L) { DEMAG_FOR_EACH_L(DEMAG_CASE) default: return cudaErrorInvalidValue; }
+    if (L == 1024) {
+        // three length-1024 columns do not fit the two-stage register layout
+        using Sh = TileShape<T, 1024>;
+        const size_t sm = 3 * swsize(1024 * Sh::TC) * sizeof(C);
+        cudaError_t e = allow_smem<k_z_conv<T, 1024>>(sm);
+        if (e != cudaSuccess) return e;
+        const int grid = (ncols + Sh::TC - 1) / Sh::TC;
+        k_z_conv<T, 1024><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride);
+        return cudaGetLastError();
+    }
+#define DEMAG_CASE(LL)                                                                         \
+    case LL:                                                                                   \
+        return variant == 1 ? zconv_launch<LL, 1>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
+                            : zconv_launch<LL, 0>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+    switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE
 }
 

@@ -56,10 +56,17 @@ template <typename T> struct Passes {
     static cudaError_t col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss,
                            int64_t irs, int nin, int64_t oss, int64_t ors, int nout, const C *tw,
                            int twstride, cudaStream_t st);
+    template <int L, bool INV, bool PIN, bool POUT>
+    static cudaError_t col_launch(const C *in, C *out, int ncols, int width, int64_t iss, int64_t irs, int nin,
+                                  int64_t oss, int64_t ors, int nout, const C *tw, int twstride,
+                                  cudaStream_t st);
     // fused z forward, spectral product, z inverse (in place)
     static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
-                             cudaStream_t st);
+                             cudaStream_t st, int variant = 0);
+    template <int L, int V>
+    static cudaError_t zconv_launch(C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                    const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st);
     // Px == 1: rows of one value; same prologue / epilogue as above
     static cudaError_t x1_fwd(const XIn<T> &a, int64_t n, C *out, cudaStream_t st);
     static cudaError_t x1_inv(const C *in, int64_t n, const XOut<T> &o, int nblocks, cudaStream_t st);
@@ -102,6 +109,8 @@ struct demag_plan {
     void *dM, *dH;
     bool setup_done;
     double imag_max;
+    // tuning choices (kernel variants), set by demag_autotune or defaults
+    int zvariant;
     // timing
     bool timing;
     void *ring;  // per-kernel timing events (api.cu)

@@ -56,6 +56,12 @@ SHAPES = [
     ((64, 16, 1), (2e-9, 2e-9, 2e-9)),       # 2-D film, Pz = 1
     ((48, 40, 3), (3e-9, 3e-9, 3e-9)),
     ((3, 130, 9), (1e-9, 1e-9, 1e-9)),       # long y axis, short x
+    ((70, 5, 3), (1e-9, 1e-9, 1e-9)),        # x transform of 128 complex points
+    ((140, 6, 3), (1e-9, 1e-9, 1e-9)),       # 256
+    ((300, 3, 2), (1e-9, 1e-9, 1e-9)),       # 512 (padded 1024)
+    ((9, 5, 40), (1e-9, 1e-9, 1e-9)),        # z pass of length 128
+    ((5, 4, 70), (1e-9, 1e-9, 1e-9)),        # z pass of length 256
+    ((4, 3, 130), (1e-9, 1e-9, 1e-9)),       # z pass of length 512
 ]
 
 
