@@ -186,6 +186,57 @@ demag_status demag_energy_noalloc(int nx, int ny, int nz, double dx, double dy, 
                                   demag_prec prec, const void *M, const void *H, double *E_dev,
                                   void *stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent magnetization states on grids of uneven sizes, evaluated
+ * together (each state is one DM stray-field problem of paper Sec. 3.1 with
+ * its own geometry and tensor). */
+typedef struct demag_batch *demag_batch_t;
+
+/* n states; dims: 3n ints (nx, ny, nz per state); cells: 3n doubles (dx, dy,
+ * dz). Creates one plan per state and runs every tensor setup (blocking),
+ * then prepares the persistent batch kernel when the precision is DEMAG_F32
+ * and every padded length is supported by it (x: 32..1024, y: 8..512,
+ * z: 4..256); otherwise the batch uses branch mode. */
+demag_status demag_batch_create(int n, const int *dims, const double *cells, demag_prec prec,
+                                demag_batch_t *out);
+
+/* Fields and energies of all states. M, H: arrays of n device pointers
+ * ([3][nz][ny][nx] per state, 16-byte aligned, H[i] not overlapping M[i]).
+ * E_dev: optional device array of n doubles receiving each state's energy.
+ * Mode 0 (persistent): one CUDA-graph launch holding a counter reset and one
+ * persistent kernel that works through all (pass, state, tile) items; its
+ * dependency waits are bounded (see demag_batch_set_timeout), and a wait
+ * that runs out is reported by demag_batch_status. Mode 1 (branches): one
+ * CUDA-graph launch of the per-state pipelines as independent branches. The
+ * graphs are built at the first call and rebuilt when the pointers change.
+ * Asynchronous. */
+demag_status demag_batch_field(demag_batch_t batch, const void *const *M, void *const *H, double *E_dev,
+                               void *stream);
+
+/* 0 = persistent kernel (DEMAG_ERR_UNSUPPORTED if not available), 1 = graph
+ * of per-state branches. */
+demag_status demag_batch_set_mode(demag_batch_t batch, int mode);
+
+/* Limit of each dependency wait of the persistent kernel, in seconds of GPU
+ * clock (default about 2 s; normal waits take microseconds). stall_state >= 0
+ * is a test hook: that state's first pass is made to look one tile short, so
+ * its waiters run out of time; -1 restores normal operation. */
+demag_status demag_batch_set_timeout(demag_batch_t batch, double seconds, int stall_state);
+
+/* Synchronises the stream and reports DEMAG_ERR_TIMEOUT if a wait of the
+ * persistent kernel gave up since the last status call (then clears it). */
+demag_status demag_batch_status(demag_batch_t batch, void *stream);
+
+/* Mode in use, whether the persistent kernel is available, its work items,
+ * grid size and dynamic shared memory (any pointer may be NULL). */
+demag_status demag_batch_info(demag_batch_t batch, int *mode, int *persistent_ok, int *items, int *grid,
+                              size_t *smem);
+
+/* Graph launches made by this batch. */
+long demag_batch_launch_count(demag_batch_t batch);
+
+void demag_batch_destroy(demag_batch_t batch);
+
 /* Number of kernels this plan has launched since creation. */
 long demag_launch_count(demag_plan_t plan);
 

@@ -33,6 +33,8 @@ EXPORTS = [
     "demag_field_host", "demag_plan_info", "demag_set_timing", "demag_get_timing",
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
     "demag_energy_noalloc",
+    "demag_batch_create", "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
+    "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
 ]
 
 
@@ -94,6 +96,15 @@ def load(path: str | Path | None = None):
         "demag_last_error": (ctypes.c_char_p, []),
         "demag_status_string": (ctypes.c_char_p, [I]),
         "demag_energy_noalloc": (S, [I, I, I, D, D, D, I, P, P, P, P]),
+        "demag_batch_create": (S, [I, P, P, I, POINTER(c_void_p)]),
+        "demag_batch_field": (S, [P, P, P, P, P]),
+        "demag_batch_set_mode": (S, [P, I]),
+        "demag_batch_set_timeout": (S, [P, D, I]),
+        "demag_batch_status": (S, [P, P]),
+        "demag_batch_info": (S, [P, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                 POINTER(c_size_t)]),
+        "demag_batch_launch_count": (c_long, [P]),
+        "demag_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +210,53 @@ def demag_energy_noalloc(nx, ny, nz, dx, dy, dz, prec, M, H, E_dev, stream=0):
                                          int(prec), _p(M), _p(H), _p(E_dev), _p(stream))
     if status != 0:
         raise DemagError(status, "demag_energy_noalloc", "see include/demag.h for the conditions")
+
+
+def demag_batch_create(dims, cells, prec=DEMAG_F32):
+    """dims: [(nx, ny, nz), ...]; cells: [(dx, dy, dz), ...]."""
+    n = len(dims)
+    d = (c_int * (3 * n))(*[int(v) for t in dims for v in t])
+    c = (c_double * (3 * n))(*[float(v) for t in cells for v in t])
+    h = c_void_p()
+    _check(load().demag_batch_create(n, d, c, int(prec), ctypes.byref(h)), "demag_batch_create")
+    return h.value
+
+
+def demag_batch_field(batch, M_ptrs, H_ptrs, E_dev=None, stream=0):
+    n = len(M_ptrs)
+    m = (c_void_p * n)(*[int(v) for v in M_ptrs])
+    h = (c_void_p * n)(*[int(v) for v in H_ptrs])
+    _check(load().demag_batch_field(_p(batch), m, h, _p(E_dev), _p(stream)), "demag_batch_field")
+
+
+def demag_batch_set_mode(batch, mode):
+    _check(load().demag_batch_set_mode(_p(batch), int(mode)), "demag_batch_set_mode")
+
+
+def demag_batch_set_timeout(batch, seconds, stall_state=-1):
+    _check(load().demag_batch_set_timeout(_p(batch), float(seconds), int(stall_state)), "demag_batch_set_timeout")
+
+
+def demag_batch_status(batch, stream=0):
+    _check(load().demag_batch_status(_p(batch), _p(stream)), "demag_batch_status")
+
+
+def demag_batch_info(batch) -> dict:
+    mode, ok, items, grid = c_int(), c_int(), c_int(), c_int()
+    smem = c_size_t()
+    _check(load().demag_batch_info(_p(batch), ctypes.byref(mode), ctypes.byref(ok), ctypes.byref(items),
+                                   ctypes.byref(grid), ctypes.byref(smem)), "demag_batch_info")
+    return {"mode": mode.value, "persistent_ok": bool(ok.value), "items": items.value, "grid": grid.value,
+            "smem": smem.value}
+
+
+def demag_batch_launch_count(batch) -> int:
+    return int(load().demag_batch_launch_count(_p(batch)))
+
+
+def demag_batch_destroy(batch):
+    if batch:
+        load().demag_batch_destroy(_p(batch))
 
 
 def demag_status_string(s: int) -> str:

@@ -308,6 +308,8 @@ FieldJob plain_job(const void *M, void *H, double *E_dev)
 
 }  // namespace
 
+void demag::set_last_error(const std::string &msg) { g_err = msg; }
+
 extern "C" {
 
 const char *demag_last_error(void) { return g_err.c_str(); }

@@ -59,6 +59,15 @@ __device__ __forceinline__ void twiddle_row(C *v, int k, const C *__restrict__ t
     }
 }
 
+// Global load of a buffer that another CTA of the same launch may have
+// written (persistent batch kernel): bypass L1, which is not coherent.
+template <bool CG, typename V>
+__device__ __forceinline__ V ldp(const V *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // 4-byte asynchronous global -> shared copy (no register staging).
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
@@ -76,18 +85,16 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Strided column transform, column f = slab * width + off, element r at
 // slab * ss + r * rs + off. PIN: rows >= L/2 of the input are zero (nin <=
 // L/2). POUT: only rows < L/2 are stored (nout <= L/2).
-template <typename T, int L, bool INV, bool PIN, bool POUT>
-__global__ void __launch_bounds__(Tile2<T>::NT)
-k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+template <typename T, int L, bool INV, bool PIN, bool POUT, bool CG>
+__device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
        int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
-       const typename Cplx<T>::type *__restrict__ tw, int twstride)
+       const typename Cplx<T>::type *__restrict__ tw, int twstride, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
     using S = ColShape<T, L>;
     constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TC = S::TC;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int f0 = blockIdx.x * TC;
+    const int f0 = tile * TC;
     // stage 1: radix R1 over rows j1 + r R2, j1 < R2
 #pragma unroll
     for (int q = 0; q < (TC * R2 + NT - 1) / NT; ++q) {
@@ -105,7 +112,7 @@ k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__
             for (int r = 0; r < R1; ++r) {
                 const int row = j1 + r * R2;
                 u[r] = cmk<C>(0, 0);
-                if (!(PIN && r >= R1 / 2) && ok && row < nin) u[r] = in[base + (int64_t)row * irs];
+                if (!(PIN && r >= R1 / 2) && ok && row < nin) u[r] = ldp<CG>(&in[base + (int64_t)row * irs]);
             }
             RegDFT<R1, INV, C>::run(u);
 #pragma unroll
@@ -137,24 +144,42 @@ k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__
     }
 }
 
-// Short columns (L <= 16): one thread per column, no shared memory.
-template <typename T, int L, bool INV>
+template <typename T, int L, bool INV, bool PIN, bool POUT>
 __global__ void __launch_bounds__(Tile2<T>::NT)
-k_col1(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
-       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout)
+k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
+       const typename Cplx<T>::type *__restrict__ tw, int twstride)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_col2_tile<T, L, INV, PIN, POUT, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, blockIdx.x, smraw);
+}
+
+// Short columns (L <= 16): one thread per column, no shared memory.
+template <typename T, int L, bool INV, bool CG>
+__device__ __forceinline__ void k_col1_tile(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
-    const int f = blockIdx.x * Tile2<T>::NT + threadIdx.x;
+    const int f = tile * Tile2<T>::NT + threadIdx.x;
     if (f >= ncols) return;
     const int slab = f / width, off = f - slab * width;
     const int64_t bi = (int64_t)slab * iss + off, bo = (int64_t)slab * oss + off;
     C u[L];
 #pragma unroll
-    for (int r = 0; r < L; ++r) u[r] = r < nin ? in[bi + (int64_t)r * irs] : cmk<C>(0, 0);
+    for (int r = 0; r < L; ++r) u[r] = r < nin ? ldp<CG>(&in[bi + (int64_t)r * irs]) : cmk<C>(0, 0);
     RegDFT<L, INV, C>::run(u);
 #pragma unroll
     for (int r = 0; r < L; ++r)
         if (r < nout) out[bo + (int64_t)r * ors] = u[r];
+}
+
+template <typename T, int L, bool INV>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_col1(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_col1_tile<T, L, INV, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, blockIdx.x, smraw);
 }
 
 // ---------------------------------------------------------------- z pass
@@ -201,11 +226,10 @@ __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem)
 // + kx with ky = ky_pair_order(i). The CTA's block of the tensor spectrum
 // ([6][L/2+1][Py/2+1][Kx], folded in ky and kz) is copied to shared memory
 // asynchronously while the first stage runs.
-template <typename T, int L, int V>
-__global__ void __launch_bounds__(ZShape<T, L, V>::NT, 1)
-k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+template <typename T, int L, int V, bool CG>
+__device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
           int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
-          int twstride)
+          int twstride, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
     using Sh = ZShape<T, L, V>;
@@ -215,10 +239,9 @@ k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
     constexpr int HZ = L / 2 + 1;
     static_assert(NT % TC == 0, "tensor prefetch assumes TC divides the threads");
     static_assert((R1 * TC) % 32 == 0 && (R2 * TC) % 32 == 0, "shared-memory offsets need 32-aligned rows");
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
     T *smT = reinterpret_cast<T *>(sm + 3 * TS);  // [kzf][comp][c] tensor block
-    const int f0 = blockIdx.x * TC;
+    const int f0 = tile * TC;
     const int hy = Py / 2 + 1;
     const int64_t plane = (int64_t)HZ * hy * Kx;
 
@@ -251,7 +274,7 @@ k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
                 const C *col = S + (int64_t)ky_pair_order(i, Py) * ss + (f - i * width) + comp * cs + j1 * rs;
 #pragma unroll
                 for (int r = 0; r < R1 / 2; ++r)
-                    if (j1 + r * R2 < nrows) u[r] = col[(int64_t)r * R2 * rs];
+                    if (j1 + r * R2 < nrows) u[r] = ldp<CG>(&col[(int64_t)r * R2 * rs]);
             }
             RegDFT<R1, false, C>::run(u);
             C *s = sm + comp * TS + sw(j1 * R1 * TC + c);
@@ -350,14 +373,23 @@ k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
     }
 }
 
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(ZShape<T, L, V>::NT, 1)
+k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+          int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
+          int twstride)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_z_conv2_tile<T, L, V, false>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, blockIdx.x, smraw);
+}
+
 // Fused z pass for L <= 16: one thread per column, all in registers.
-template <typename T, int L>
-__global__ void __launch_bounds__(Tile2<T>::NT, (L >= 16 ? 1 : 2))
-k_z_conv1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
-          int nrows, const T *__restrict__ nhat, int Py, int Kx)
+template <typename T, int L, bool CG>
+__device__ __forceinline__ void k_z_conv1_tile(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+          int nrows, const T *__restrict__ nhat, int Py, int Kx, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
-    const int f = blockIdx.x * Tile2<T>::NT + threadIdx.x;
+    const int f = tile * Tile2<T>::NT + threadIdx.x;
     if (f >= ncols) return;
     const int ky = f / width, kx = f - ky * width;
     const int64_t base = (int64_t)ky * ss + kx;
@@ -365,9 +397,9 @@ k_z_conv1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
 #pragma unroll
     for (int r = 0; r < L; ++r) {
         const bool ok = r < nrows;
-        a[r] = ok ? S[base + (int64_t)r * rs] : cmk<C>(0, 0);
-        b[r] = ok ? S[base + (int64_t)r * rs + cs] : cmk<C>(0, 0);
-        c[r] = ok ? S[base + (int64_t)r * rs + 2 * cs] : cmk<C>(0, 0);
+        a[r] = ok ? ldp<CG>(&S[base + (int64_t)r * rs]) : cmk<C>(0, 0);
+        b[r] = ok ? ldp<CG>(&S[base + (int64_t)r * rs + cs]) : cmk<C>(0, 0);
+        c[r] = ok ? ldp<CG>(&S[base + (int64_t)r * rs + 2 * cs]) : cmk<C>(0, 0);
     }
     RegDFT<L, false, C>::run(a);
     RegDFT<L, false, C>::run(b);
@@ -394,6 +426,15 @@ k_z_conv1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
             S[base + (int64_t)r * rs + cs] = b[r];
             S[base + (int64_t)r * rs + 2 * cs] = c[r];
         }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile2<T>::NT, (L >= 16 ? 1 : 2))
+k_z_conv1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+          int nrows, const T *__restrict__ nhat, int Py, int Kx)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_z_conv1_tile<T, L, false>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, blockIdx.x, smraw);
 }
 
 }  // namespace demag
@@ -433,17 +474,15 @@ __device__ __forceinline__ C shfl_c(C v, int lane)
 // Real-to-complex along x (see k_x_fwd for the packing), two stages.
 // PIN: the row has at most L reals (the zero-padded field), so the upper half
 // of the packed sequence is zero; otherwise all 2L reals are read (setup).
-template <typename T, int L, bool PIN>
-__global__ void __launch_bounds__(Tile2<T>::NT)
-k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
-         const typename Cplx<T>::type *__restrict__ twx)
+template <typename T, int L, bool PIN, bool CG>
+__device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
+         const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
     using S = XShape<T, L>;
     constexpr int R1 = S::R1, R2 = S::R2, TR = S::TR, RS = S::RS;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int row0 = blockIdx.x * TR;
+    const int row0 = tile * TR;
     // stage 1: thread (row, j1) reads z[j1 + r R2] (r < R1/2 when PIN: the rest is padding)
     if (threadIdx.x < TR * R2) {
         const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
@@ -503,18 +542,25 @@ k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ o
     }
 }
 
-// Complex-to-real along x (see k_x_inv), two stages, XOut epilogue.
-template <typename T, int L>
+template <typename T, int L, bool PIN>
 __global__ void __launch_bounds__(Tile2<T>::NT)
-k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
+k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
          const typename Cplx<T>::type *__restrict__ twx)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_x_fwd2_tile<T, L, PIN, false>(a, nrows, nvalid, out, out_rs, twx, blockIdx.x, smraw);
+}
+
+// Complex-to-real along x (see k_x_inv), two stages, XOut epilogue.
+template <typename T, int L, bool CG>
+__device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
+         const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
     using S = XShape<T, L>;
     constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TR = S::TR, RS = S::RS;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int row0 = blockIdx.x * TR;
+    const int row0 = tile * TR;
     // stage 1: thread (row, j1) builds Z[k], k = j1 + r R2, from X[k] and X[L-k]
     if (threadIdx.x < TR * R2) {
         const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
@@ -526,8 +572,8 @@ k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows
 #pragma unroll
             for (int r = 0; r < R1; ++r) {
                 const int k = j1 + r * R2;
-                const C a = p[k];
-                const C b = p[L - k];
+                const C a = ldp<CG>(&p[k]);
+                const C b = ldp<CG>(&p[L - k]);
                 const C E2 = cmk<C>(a.x + b.x, a.y - b.y);
                 const C D = cmk<C>(a.x - b.x, a.y + b.y);
                 const C O2 = cmulc(D, __ldg(&twx[k]));
@@ -574,7 +620,16 @@ k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows
             }
         }
     }
-    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials);
+    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials, tile);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
+         const typename Cplx<T>::type *__restrict__ twx)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_x_inv2_tile<T, L, false>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
 }
 
 }  // namespace demag

@@ -186,9 +186,9 @@ __device__ __forceinline__ T cell_weight(const T *wcell, int row, int rows_per_c
     return wcell ? __ldg(&wcell[(int64_t)(row % rows_per_comp) * rs + x]) : (T)1;
 }
 
-// Block sum of a per-thread double into partials[blockIdx.x].
+// Block sum of a per-thread double into partials[slot] (slot = the tile).
 template <int NT>
-__device__ __forceinline__ void block_partial(double v, double *partials)
+__device__ __forceinline__ void block_partial(double v, double *partials, int slot)
 {
     __shared__ double red[NT / 32];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -197,7 +197,7 @@ __device__ __forceinline__ void block_partial(double v, double *partials)
     if (threadIdx.x == 0) {
         double s = 0;
         for (int w = 0; w < NT / 32; ++w) s += red[w];
-        partials[blockIdx.x] = s;
+        partials[slot] = s;
     }
 }
 
@@ -206,17 +206,15 @@ __device__ __forceinline__ void block_partial(double v, double *partials)
 // 2L): pack z[n] = x[2n] + i x[2n+1], transform length L, then split into the
 // spectrum X[k], k = 0..L, of the length-2L real sequence. twx is the table of
 // the x axis (length 2L).
-template <typename T, int L>
-__global__ void __launch_bounds__(Tile<T>::NT)
-k_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
-        const typename Cplx<T>::type *__restrict__ twx)
+template <typename T, int L, bool CG>
+__device__ __forceinline__ void k_x_fwd_tile(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
+        const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
     using S = TileShape<T, L>;
     constexpr int NT = S::NT, TC = S::TC;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int row0 = blockIdx.x * TC;
+    const int row0 = tile * TC;
     for (int e = threadIdx.x; e < L * TC; e += NT) {
         const int n = e % L, rr = e / L, row = row0 + rr;
         C z = cmk<C>(0, 0);
@@ -245,28 +243,35 @@ k_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ ou
     }
 }
 
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile<T>::NT)
+k_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
+        const typename Cplx<T>::type *__restrict__ twx)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_x_fwd_tile<T, L, false>(a, nrows, nvalid, out, out_rs, twx, blockIdx.x, smraw);
+}
+
 // ---------------------------------------------------------------- x inverse
 // Complex-to-real along x: from X[k], k = 0..L, rebuild the packed sequence
 // Z[k] = (X[k] + conj X[L-k]) + i W^-k (X[k] - conj X[L-k]), inverse transform
 // of length L, unpack to 2L reals, keep x < nvalid; epilogue per XOut.
-template <typename T, int L>
-__global__ void __launch_bounds__(Tile<T>::NT)
-k_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
-        const typename Cplx<T>::type *__restrict__ twx)
+template <typename T, int L, bool CG>
+__device__ __forceinline__ void k_x_inv_tile(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
+        const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
     using S = TileShape<T, L>;
     constexpr int NT = S::NT, TC = S::TC;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int row0 = blockIdx.x * TC;
+    const int row0 = tile * TC;
     for (int e = threadIdx.x; e < L * TC; e += NT) {
         const int k = e % L, rr = e / L, row = row0 + rr;
         C z = cmk<C>(0, 0);
         if (row < nrows) {
             const C *p = in + (int64_t)row * in_rs;
-            const C a = p[k];
-            const C b = p[L - k];
+            const C a = CG ? __ldcg(&p[k]) : p[k];
+            const C b = CG ? __ldcg(&p[L - k]) : p[L - k];
             const C E2 = cmk<C>(a.x + b.x, a.y - b.y);
             const C D = cmk<C>(a.x - b.x, a.y + b.y);
             const C O2 = cmulc(D, __ldg(&twx[k]));
@@ -299,7 +304,16 @@ k_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows,
             }
         }
     }
-    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials);
+    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials, tile);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile<T>::NT)
+k_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
+        const typename Cplx<T>::type *__restrict__ twx)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_x_inv_tile<T, L, false>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
 }
 
 // ---------------------------------------------------------------- columns

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_x1_inv(const typename Cplx<T>::type *__
         if (o.out) o.out[i] = h * o.oscale * g * w;
         if (o.partials) acc += (double)(o.mscale * w * o.Mref[i] * h);
     }
-    if (o.partials) block_partial<256>(acc, o.partials);
+    if (o.partials) block_partial<256>(acc, o.partials, blockIdx.x);
 }
 
 }  // namespace

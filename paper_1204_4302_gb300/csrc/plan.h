@@ -72,6 +72,33 @@ template <typename T> struct Passes {
     static cudaError_t x1_inv(const C *in, int64_t n, const XOut<T> &o, int nblocks, cudaStream_t st);
 };
 
+// One state of a batch, as the persistent batch kernel sees it (device
+// memory). Pointers come from the state's plan and the caller's arrays.
+struct BatchState {
+    const float *M;
+    float *H;
+    float2 *S1, *S2;
+    const float *nhat;
+    const float2 *tw[3];
+    double *partials;
+    double *E;
+    int nx, ny, nz, Px, Py, Pz, Kx, Kxp;
+    int ntiles[6];  // tiles of each pass (x fwd, y fwd, z, y inv, x inv, energy)
+    double efactor; // -(mu0/2) V
+};
+
+// Shared description of one batch launch (kernel argument).
+struct BatchDesc {
+    BatchState *states;
+    int n;
+    const int *start;  // [6][n+1] first item of (pass, state); start[6*(n+1)-1] = total
+    int total;
+    int *counter;      // next item to claim
+    int *done;         // [6][n] finished tiles
+    int *error;        // set to 1 when a wait gives up
+    long long timeout_cycles;
+};
+
 // Tensor setup kernels (tensor.cu).
 cudaError_t tensor_octant(double *out, int nx, int ny, int nz, double dx, double dy, double dz,
                           cudaStream_t st);
@@ -80,6 +107,9 @@ cudaError_t tensor_wrap(const double *oct, int comp, int nx, int ny, int nz, int
 cudaError_t tensor_extract(const double2 *S, int comp, int Px, int Py, int Pz, int Kxp,
                            double *nhat64, float *nhat32, unsigned long long *imag_max,
                            cudaStream_t st);
+// Sets the calling thread's demag_last_error() message (api.cu).
+void set_last_error(const std::string &msg);
+
 cudaError_t energy_finalize(const double *partials, int n, double factor, double *E,
                             cudaStream_t st);
 
