@@ -184,6 +184,8 @@ def run_ours(args, rank, world, local_rank):
     plan = Plan(n, CELL, prec="f32", device=dev)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
+    tuned_ms = plan.autotune(use_cache=False)
+    variants = plan.variants()
     info = plan.info()
     P = (info["px"], info["py"], info["pz"])
     H = torch.empty_like(M)
@@ -329,6 +331,10 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * cells / tmax, "unit": "cells/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": round(tmax * 1e3, 4)}
 
+    batch = None
+    if not args.skip_batch:
+        batch = run_batch(args, dev, rank)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cpu = cpu_baseline(args.cpu_sample)
@@ -354,6 +360,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs and spectra (~2 GB) larger than L2, no flush needed"},
             "gpu_launches": launches,
             "setup_ms": round(setup_ms, 1),
+            "autotune": {"z_variant": variants[0], "y_variant": variants[1], "ms_per_field": round(tuned_ms, 4)},
+            "batch": batch,
             "energy_J": E_val,
             "passes": per_pass,
             "roofline": roof,
@@ -369,6 +377,51 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     plan.close()
+
+
+def run_batch(args, dev, rank):
+    """64 independent states of uneven sizes (32..128 x 32..128 x 8..32 cells of
+    3 nm, seeded random unit m), FP32, one graph launch per batch call."""
+    import torch
+
+    from paper_1204_4302_gb300 import inputs
+    from paper_1204_4302_gb300.batch import Batch
+    dims = inputs.batch_sizes(64, lo=(32, 32, 8), hi=(128, 128, 32), seed=4)
+    d = 3e-9
+    cells = [(d, d, d)] * len(dims)
+    ms = [torch.tensor(MS * inputs.random_unit(nn, seed=1000 * rank + i), dtype=torch.float32, device=dev)
+          for i, nn in enumerate(dims)]
+    hs = [torch.empty_like(m) for m in ms]
+    b = Batch(dims, cells)
+    t_p, t_b = b.autotune(use_cache=False)
+    E = torch.empty(len(dims), dtype=torch.float64, device=dev)
+    from paper_1204_4302_gb300 import binding as B
+    st = torch.cuda.current_stream(dev)
+    mp, hp = [m.data_ptr() for m in ms], [h.data_ptr() for h in hs]
+    for _ in range(3):
+        B.demag_batch_field(b.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+    torch.cuda.synchronize()
+    k = max(5, args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count()
+    e0.record(st)
+    for _ in range(k):
+        B.demag_batch_field(b.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+    e1.record(st)
+    e1.synchronize()
+    b.status()
+    ms_call = e0.elapsed_time(e1) / k
+    cells_total = sum(a * bb * c for a, bb, c in dims)
+    info = b.info()
+    out = {"workload": "64 states, 32..128 x 32..128 x 8..32 cells of 3 nm, FP32, field + energy",
+           "cells": cells_total, "mode": "persistent" if info["mode"] == 0 else "graph branches",
+           "ms_per_call": round(ms_call, 4), "cells_per_s": cells_total / (ms_call / 1e3),
+           "ms_persistent": round(t_p, 4), "ms_branches": round(t_b, 4),
+           "graph_launches_per_call": (b.launch_count() - l0) / k,
+           "persistent_items": info["items"], "persistent_grid": info["grid"]}
+    b.close()
+    return out
 
 
 # ------------------------------------------------------------------- oracle side
@@ -455,6 +508,7 @@ def main():
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -232,6 +232,13 @@ demag_status demag_batch_status(demag_batch_t batch, void *stream);
 demag_status demag_batch_info(demag_batch_t batch, int *mode, int *persistent_ok, int *items, int *grid,
                               size_t *smem);
 
+/* Autotunes every state's plan (demag_autotune), then times the persistent
+ * and the branch mode on temporary fields and keeps the faster mode.
+ * ms_persistent / ms_branches (may be NULL) receive the time per call of each
+ * mode (-1 when the persistent mode is unavailable). Synchronises. */
+demag_status demag_batch_autotune(demag_batch_t batch, int use_cache, double *ms_persistent,
+                                  double *ms_branches, void *stream);
+
 /* Graph launches made by this batch. */
 long demag_batch_launch_count(demag_batch_t batch);
 
@@ -239,6 +246,22 @@ void demag_batch_destroy(demag_batch_t batch);
 
 /* Number of kernels this plan has launched since creation. */
 long demag_launch_count(demag_plan_t plan);
+
+/* Autotuner: times the kernel variants that exist for this plan's sizes (the
+ * z-pass tile width and the y-pass radix order of the two-stage transforms)
+ * with CUDA events on the plan's own sizes (five timed calls after two
+ * warm-up calls each, on stream) and keeps the fastest. With use_cache != 0 a
+ * previous result for the same GPU, precision and sizes is reused from the
+ * cache file (DEMAG_TUNE_CACHE, default $HOME/.cache/demag_tune.txt) and a new
+ * result is appended to it. best_ms (may be NULL) receives the time of one
+ * field call with the chosen variants. Allocates and frees two temporary
+ * fields; synchronises. */
+demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, void *stream);
+
+/* Current variant choice (z tile width 0/1, y radix order 0/1), and a way to
+ * set it by hand. */
+demag_status demag_get_variants(demag_plan_t plan, int *z, int *y);
+demag_status demag_set_variants(demag_plan_t plan, int z, int y);
 
 /* Destroy a plan and free its device memory (NULL is ignored). */
 void demag_plan_destroy(demag_plan_t plan);

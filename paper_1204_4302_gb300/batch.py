@@ -41,6 +41,11 @@ class Batch:
                             torch.cuda.current_stream(self.device).cuda_stream)
         return Hs, E
 
+    def autotune(self, use_cache: bool = True):
+        """Tune every state's plan and choose the faster batch mode; returns
+        (ms per call persistent, ms per call branches)."""
+        return B.demag_batch_autotune(self.handle, use_cache, torch.cuda.current_stream(self.device).cuda_stream)
+
     def set_mode(self, mode: int):
         B.demag_batch_set_mode(self.handle, mode)
 

@@ -35,6 +35,7 @@ EXPORTS = [
     "demag_energy_noalloc",
     "demag_batch_create", "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
+    "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
 ]
 
 
@@ -105,6 +106,10 @@ def load(path: str | Path | None = None):
                                  POINTER(c_size_t)]),
         "demag_batch_launch_count": (c_long, [P]),
         "demag_batch_destroy": (None, [P]),
+        "demag_autotune": (S, [P, I, POINTER(c_double), P]),
+        "demag_get_variants": (S, [P, POINTER(c_int), POINTER(c_int)]),
+        "demag_set_variants": (S, [P, I, I]),
+        "demag_batch_autotune": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -257,6 +262,29 @@ def demag_batch_launch_count(batch) -> int:
 def demag_batch_destroy(batch):
     if batch:
         load().demag_batch_destroy(_p(batch))
+
+
+def demag_autotune(plan, use_cache=True, stream=0) -> float:
+    ms = c_double()
+    _check(load().demag_autotune(_p(plan), int(bool(use_cache)), ctypes.byref(ms), _p(stream)), "demag_autotune")
+    return ms.value
+
+
+def demag_get_variants(plan):
+    z, y = c_int(), c_int()
+    _check(load().demag_get_variants(_p(plan), ctypes.byref(z), ctypes.byref(y)), "demag_get_variants")
+    return z.value, y.value
+
+
+def demag_set_variants(plan, z, y):
+    _check(load().demag_set_variants(_p(plan), int(z), int(y)), "demag_set_variants")
+
+
+def demag_batch_autotune(batch, use_cache=True, stream=0):
+    a, b = c_double(), c_double()
+    _check(load().demag_batch_autotune(_p(batch), int(bool(use_cache)), ctypes.byref(a), ctypes.byref(b),
+                                       _p(stream)), "demag_batch_autotune")
+    return a.value, b.value
 
 
 def demag_status_string(s: int) -> str:

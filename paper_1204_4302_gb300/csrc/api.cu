@@ -10,8 +10,10 @@
 // "demag" evaluated through Eq. "convolution").
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <string>
@@ -216,7 +218,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     // y forward
     if (Py > 1) {
         e = Passes<T>::col(Py, false, S1, S2, 3 * nz * Kx, Kx, (int64_t)ny * Kxp, Kxp, ny,
-                           (int64_t)Py * Kxp, Kxp, Py, twy, 1, st);
+                           (int64_t)Py * Kxp, Kxp, Py, twy, 1, st, p->yvariant);
         if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y forward: ") + cudaGetErrorString(e));
         p->launches++;
     }
@@ -230,7 +232,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     // y inverse
     if (Py > 1) {
         e = Passes<T>::col(Py, true, S2, S1, 3 * nz * Kx, Kx, (int64_t)Py * Kxp, Kxp, Py, (int64_t)ny * Kxp, Kxp,
-                           ny, twy, 1, st);
+                           ny, twy, 1, st, p->yvariant);
         if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y inverse: ") + cudaGetErrorString(e));
         p->launches++;
     }
@@ -295,6 +297,55 @@ demag_status run_job(demag_plan *p, const FieldJob &job, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prec == DEMAG_F32) return run_field<float>(p, job, st);
     return run_field<double>(p, job, st);
+}
+
+// ----- autotuner cache: one line per tuned geometry, "key zvariant yvariant ms"
+std::string tune_path()
+{
+    if (const char *e = getenv("DEMAG_TUNE_CACHE")) return e;
+    const char *home = getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/demag_tune.txt";
+}
+
+std::string tune_key(const demag_plan *p)
+{
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) name = prop.name;
+    for (auto &c : name)
+        if (c == ' ') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%s|%dx%dx%d|%dx%dx%d", name.c_str(), p->prec == DEMAG_F32 ? "f32" : "f64", p->Px,
+             p->Py, p->Pz, p->nx, p->ny, p->nz);
+    return buf;
+}
+
+bool tune_lookup(const std::string &key, int &z, int &y, double &ms)
+{
+    FILE *f = fopen(tune_path().c_str(), "r");
+    if (!f) return false;
+    char k[512];
+    int zz, yy;
+    double m;
+    bool found = false;
+    while (fscanf(f, "%511s %d %d %lf", k, &zz, &yy, &m) == 4)
+        if (key == k) { z = zz; y = yy; ms = m; found = true; }  // the last entry wins
+    fclose(f);
+    return found;
+}
+
+void tune_store(const std::string &key, int z, int y, double ms)
+{
+    const std::string path = tune_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        mkdir(dir.c_str(), 0755);  // one level is enough for the default location
+    }
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;  // a cache that cannot be written is not an error
+    fprintf(f, "%s %d %d %.6f\n", key.c_str(), z, y, ms);
+    fclose(f);
 }
 
 FieldJob plain_job(const void *M, void *H, double *E_dev)
@@ -381,7 +432,6 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
     p->Px = P[0]; p->Py = P[1]; p->Pz = P[2];
     p->Kx = P[0] == 1 ? 1 : P[0] / 2 + 1;
     p->Kxp = P[0] == 1 ? 1 : (p->Kx + 1) / 2 * 2;
-    if (const char *zv = getenv("DEMAG_ZVARIANT")) p->zvariant = atoi(zv) == 1 ? 1 : 0;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -624,5 +674,86 @@ demag_status demag_get_timing(demag_plan_t p, double *ms, long *counts, int n)
 }
 
 long demag_launch_count(demag_plan_t p) { return p ? p->launches : 0; }
+
+demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    const std::string key = tune_key(p);
+    int zc = 0, yc = 0;
+    double ms_cached = 0;
+    if (use_cache && tune_lookup(key, zc, yc, ms_cached)) {
+        p->zvariant = zc;
+        p->yvariant = yc;
+        p->tuned = true;
+        if (best_ms) *best_ms = ms_cached;
+        return DEMAG_OK;
+    }
+    // candidates: z-pass tile width where the two-stage z kernel runs, y-pass
+    // radix order where the two radices differ
+    std::vector<int> zs = {0}, ys = {0};
+    if (p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
+    if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
+    const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
+    void *M = nullptr, *H = nullptr;
+    DEMAG_CUDA(cudaMalloc(&M, bytes));
+    if (cudaMalloc(&H, bytes) != cudaSuccess) {
+        cudaFree(M);
+        return fail(DEMAG_ERR_OOM, "autotune buffers");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(M, 0, bytes, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool timing = p->timing;
+    p->timing = false;
+    double best = 1e30;
+    int bz = 0, by = 0;
+    demag_status rs = DEMAG_OK;
+    for (int z : zs)
+        for (int y : ys) {
+            p->zvariant = z;
+            p->yvariant = y;
+            for (int w = 0; w < 2 && rs == DEMAG_OK; ++w) rs = run_job(p, plain_job(M, H, nullptr), stream);
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 5 && rs == DEMAG_OK; ++r) rs = run_job(p, plain_job(M, H, nullptr), stream);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rs == DEMAG_OK && ms / 5 < best) { best = ms / 5; bz = z; by = y; }
+        }
+    p->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(M);
+    cudaFree(H);
+    if (rs != DEMAG_OK) return rs;
+    p->zvariant = bz;
+    p->yvariant = by;
+    p->tuned = true;
+    if (best_ms) *best_ms = best;
+    if (use_cache) tune_store(key, bz, by, best);
+    return DEMAG_OK;
+}
+
+demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (z) *z = p->zvariant;
+    if (y) *y = p->yvariant;
+    return DEMAG_OK;
+}
+
+demag_status demag_set_variants(demag_plan_t p, int z, int y)
+{
+    if (!p || z < 0 || z > 1 || y < 0 || y > 1) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
+    p->zvariant = z;
+    p->yvariant = y;
+    return DEMAG_OK;
+}
 
 }  // extern "C"

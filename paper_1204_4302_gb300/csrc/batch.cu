@@ -678,6 +678,58 @@ demag_status demag_batch_info(demag_batch_t b, int *mode, int *persistent_ok, in
 
 long demag_batch_launch_count(demag_batch_t b) { return b ? b->launches : 0; }
 
+demag_status demag_batch_autotune(demag_batch_t b, int use_cache, double *ms_persistent, double *ms_branches,
+                                  void *stream)
+{
+    if (!b) return bfail(DEMAG_ERR_INVALID_ARG, "batch is NULL");
+    for (int i = 0; i < b->n; ++i) {
+        demag_status s = demag_autotune(b->plans[i], use_cache, nullptr, stream);
+        if (s != DEMAG_OK) return s;
+    }
+    std::vector<void *> bufs(2 * b->n, nullptr);
+    auto release = [&]() {
+        for (void *q : bufs) cudaFree(q);
+        for (int i = 0; i < b->n; ++i) { b->curM[i] = nullptr; b->curH[i] = nullptr; }
+    };
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < b->n; ++i) {
+        const size_t bytes = field_bytes(b->plans[i]);
+        if (cudaMalloc(&bufs[2 * i], bytes) != cudaSuccess || cudaMalloc(&bufs[2 * i + 1], bytes) != cudaSuccess) {
+            release();
+            return bfail(DEMAG_ERR_OOM, "batch autotune buffers");
+        }
+        cudaMemsetAsync(bufs[2 * i], 0, bytes, st);
+    }
+    std::vector<const void *> M(b->n);
+    std::vector<void *> H(b->n);
+    for (int i = 0; i < b->n; ++i) { M[i] = bufs[2 * i]; H[i] = bufs[2 * i + 1]; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double t[2] = {1e30, 1e30};
+    demag_status rs = DEMAG_OK;
+    for (int mode = 0; mode < 2 && rs == DEMAG_OK; ++mode) {
+        if (mode == 0 && !b->persistent_ok) continue;
+        b->mode = mode;
+        for (int w = 0; w < 2 && rs == DEMAG_OK; ++w) rs = demag_batch_field(b, M.data(), H.data(), nullptr, stream);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && rs == DEMAG_OK; ++r) rs = demag_batch_field(b, M.data(), H.data(), nullptr, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t[mode] = ms / 5;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    if (rs != DEMAG_OK) return rs;
+    b->mode = (b->persistent_ok && t[0] <= t[1]) ? 0 : 1;
+    if (ms_persistent) *ms_persistent = b->persistent_ok ? t[0] : -1.0;
+    if (ms_branches) *ms_branches = t[1];
+    return demag_batch_status(b, stream);
+}
+
 void demag_batch_destroy(demag_batch_t b)
 {
     if (b) free_batch(b);

@@ -14,14 +14,19 @@
 
 namespace demag {
 
-// Radix pair (R1, R2) of a two-stage column transform of length L.
-template <int L> struct ColRadix;
-template <> struct ColRadix<32> { static constexpr int R1 = 8, R2 = 4; };
-template <> struct ColRadix<64> { static constexpr int R1 = 8, R2 = 8; };
-template <> struct ColRadix<128> { static constexpr int R1 = 16, R2 = 8; };
-template <> struct ColRadix<256> { static constexpr int R1 = 16, R2 = 16; };
-template <> struct ColRadix<512> { static constexpr int R1 = 32, R2 = 16; };
-template <> struct ColRadix<1024> { static constexpr int R1 = 32, R2 = 32; };
+// Radix pair (R1, R2) of a two-stage column transform of length L; variant 1
+// swaps the two stages (a tuning choice).
+template <int L> struct ColRadix0;
+template <> struct ColRadix0<32> { static constexpr int R1 = 8, R2 = 4; };
+template <> struct ColRadix0<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct ColRadix0<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct ColRadix0<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct ColRadix0<512> { static constexpr int R1 = 32, R2 = 16; };
+template <> struct ColRadix0<1024> { static constexpr int R1 = 32, R2 = 32; };
+template <int L, int V = 0> struct ColRadix {
+    static constexpr int R1 = V == 0 ? ColRadix0<L>::R1 : ColRadix0<L>::R2;
+    static constexpr int R2 = V == 0 ? ColRadix0<L>::R2 : ColRadix0<L>::R1;
+};
 
 // Radix pair of the fused z pass: the second stage keeps three components in
 // registers for the tensor product, so R2 = 16.
@@ -32,8 +37,8 @@ template <> struct Tile2<double> { static constexpr int NT = 128; };
 
 // Columns per CTA: the stage with fewer butterflies per column gives one
 // butterfly to every thread, the other stage loops.
-template <typename T, int L> struct ColShape {
-    static constexpr int R1 = ColRadix<L>::R1, R2 = ColRadix<L>::R2;
+template <typename T, int L, int V = 0> struct ColShape {
+    static constexpr int R1 = ColRadix<L, V>::R1, R2 = ColRadix<L, V>::R2;
     static constexpr int NT = Tile2<T>::NT;
     static constexpr int TC = NT / (R1 < R2 ? R1 : R2);
 };
@@ -85,13 +90,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Strided column transform, column f = slab * width + off, element r at
 // slab * ss + r * rs + off. PIN: rows >= L/2 of the input are zero (nin <=
 // L/2). POUT: only rows < L/2 are stored (nout <= L/2).
-template <typename T, int L, bool INV, bool PIN, bool POUT, bool CG>
+template <typename T, int L, bool INV, bool PIN, bool POUT, bool CG, int V = 0>
 __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
        int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
        const typename Cplx<T>::type *__restrict__ tw, int twstride, int tile, unsigned char *smraw)
 {
     using C = typename Cplx<T>::type;
-    using S = ColShape<T, L>;
+    using S = ColShape<T, L, V>;
     constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TC = S::TC;
     C *sm = reinterpret_cast<C *>(smraw);
     const int f0 = tile * TC;
@@ -144,14 +149,14 @@ __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__rest
     }
 }
 
-template <typename T, int L, bool INV, bool PIN, bool POUT>
+template <typename T, int L, bool INV, bool PIN, bool POUT, int V = 0>
 __global__ void __launch_bounds__(Tile2<T>::NT)
 k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
        int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
        const typename Cplx<T>::type *__restrict__ tw, int twstride)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    k_col2_tile<T, L, INV, PIN, POUT, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, blockIdx.x, smraw);
+    k_col2_tile<T, L, INV, PIN, POUT, false, V>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, blockIdx.x, smraw);
 }
 
 // Short columns (L <= 16): one thread per column, no shared memory.

@@ -144,25 +144,25 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
 }
 
 template <typename T>
-template <int L, bool INV, bool PIN, bool POUT>
+template <int L, bool INV, bool PIN, bool POUT, int V>
 cudaError_t Passes<T>::col_launch(const C *in, C *out, int ncols, int width, int64_t iss, int64_t irs, int nin,
                                   int64_t oss, int64_t ors, int nout, const C *tw, int twstride,
                                   cudaStream_t st)
 {
-    using S = ColShape<T, L>;
+    using S = ColShape<T, L, V>;
     const size_t sm = swsize(L * S::TC) * sizeof(C);
-    cudaError_t e = allow_smem<k_col2<T, L, INV, PIN, POUT>>(sm);
+    cudaError_t e = allow_smem<k_col2<T, L, INV, PIN, POUT, V>>(sm);
     if (e != cudaSuccess) return e;
     const int grid = (ncols + S::TC - 1) / S::TC;
-    k_col2<T, L, INV, PIN, POUT><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout,
-                                                         tw, twstride);
+    k_col2<T, L, INV, PIN, POUT, V><<<grid, S::NT, sm, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout,
+                                                            tw, twstride);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss,
                            int64_t irs, int nin, int64_t oss, int64_t ors, int nout, const C *tw,
-                           int twstride, cudaStream_t st)
+                           int twstride, cudaStream_t st, int variant)
 {
     if (ncols <= 0) return cudaSuccess;
     if (L <= 16) {
@@ -180,12 +180,15 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
     }
     // the zero padding halves the input (forward) or the output (inverse)
     const bool pin = 2 * nin <= L, pout = 2 * nout <= L;
+    // variant 1 (swapped radix order) exists for the pruned field passes
 #define DEMAG_CASE(LL)                                                                         \
     case LL:                                                                                   \
-        if (!inv && pin) return col_launch<LL, false, true, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
-        if (inv && pout) return col_launch<LL, true, false, true>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
-        if (inv) return col_launch<LL, true, false, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
-        return col_launch<LL, false, false, false>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st);
+        if (!inv && pin) return variant == 1 ? col_launch<LL, false, true, false, 1>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st) \
+                                             : col_launch<LL, false, true, false, 0>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
+        if (inv && pout) return variant == 1 ? col_launch<LL, true, false, true, 1>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st) \
+                                             : col_launch<LL, true, false, true, 0>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
+        if (inv) return col_launch<LL, true, false, false, 0>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st); \
+        return col_launch<LL, false, false, false, 0>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st);
     switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) DEMAG_CASE(1024) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE
 }

@@ -55,8 +55,8 @@ template <typename T> struct Passes {
     // strided column transforms (y passes, z forward of the setup)
     static cudaError_t col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss,
                            int64_t irs, int nin, int64_t oss, int64_t ors, int nout, const C *tw,
-                           int twstride, cudaStream_t st);
-    template <int L, bool INV, bool PIN, bool POUT>
+                           int twstride, cudaStream_t st, int variant = 0);
+    template <int L, bool INV, bool PIN, bool POUT, int V>
     static cudaError_t col_launch(const C *in, C *out, int ncols, int width, int64_t iss, int64_t irs, int nin,
                                   int64_t oss, int64_t ors, int nout, const C *tw, int twstride,
                                   cudaStream_t st);
@@ -141,6 +141,8 @@ struct demag_plan {
     double imag_max;
     // tuning choices (kernel variants), set by demag_autotune or defaults
     int zvariant;
+    int yvariant;
+    bool tuned;
     // timing
     bool timing;
     void *ring;  // per-kernel timing events (api.cu)

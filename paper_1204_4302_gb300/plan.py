@@ -133,6 +133,18 @@ class Plan:
         B.demag_field_host(self.handle, M_host.data_ptr(), H_host.data_ptr(), self._stream())
         return H_host
 
+    # ------------------------------------------------------------------ tuning
+    def autotune(self, use_cache: bool = True) -> float:
+        """Pick the fastest kernel variants for this plan; returns ms per field call."""
+        with torch.cuda.device(self.device):
+            return B.demag_autotune(self.handle, use_cache, self._stream())
+
+    def variants(self):
+        return B.demag_get_variants(self.handle)
+
+    def set_variants(self, z: int, y: int):
+        B.demag_set_variants(self.handle, z, y)
+
     # ------------------------------------------------------------------ timing
     def set_timing(self, enable: bool = True):
         B.demag_set_timing(self.handle, enable)

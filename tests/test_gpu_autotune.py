@@ -1,0 +1,61 @@
+"""Autotuner: every kernel variant it may choose computes the same field (and
+matches the oracle); the choice is cached per GPU, precision and sizes."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1204_4302_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_4302_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f64", 1e-12)])
+@pytest.mark.parametrize("n", [(20, 256, 40), (9, 17, 100), (30, 64, 16)])
+def test_every_variant_matches_oracle(n, prec, tol):
+    from paper_1204_4302_gb300.plan import Plan
+    d = (2e-9, 2e-9, 2e-9)
+    M = 8e5 * inputs.random_unit(n, seed=7)
+    Href = oracle.field_fft(M, d)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    p = Plan(n, d, prec=prec)
+    Mt = torch.tensor(M, dtype=dt, device="cuda")
+    for z in (0, 1):
+        for y in (0, 1):
+            p.set_variants(z, y)
+            H = p.field(Mt).double().cpu().numpy()
+            rel = np.max(np.abs(H - Href)) / np.max(np.abs(Href))
+            assert rel <= tol, (z, y, rel)
+    p.close()
+
+
+def test_autotune_picks_and_caches(tmp_path, monkeypatch):
+    from paper_1204_4302_gb300.plan import Plan
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("DEMAG_TUNE_CACHE", str(cache))
+    n, d = (64, 128, 64), (2e-9, 2e-9, 2e-9)
+    p = Plan(n, d, prec="f32")
+    ms = p.autotune(use_cache=True)
+    assert ms > 0
+    z, y = p.variants()
+    assert z in (0, 1) and y in (0, 1)
+    text = cache.read_text()
+    assert "f32|128x256x128|64x128x64" in text
+    p2 = Plan(n, d, prec="f32")
+    p2.set_variants(1 - z, 1 - y)
+    ms2 = p2.autotune(use_cache=True)      # served from the cache
+    assert p2.variants() == (z, y)
+    assert ms2 == pytest.approx(ms, rel=1e-5)
+    assert cache.read_text() == text       # nothing re-timed or appended
+    p.close()
+    p2.close()

@@ -128,3 +128,20 @@ def test_config_sized_batch_runs_persistent():
         assert float((a - c).abs().max() / c.abs().max()) <= 1e-6
     assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
     b.close()
+
+
+def test_batch_autotune_chooses_a_mode(tmp_path, monkeypatch):
+    from paper_1204_4302_gb300.batch import Batch
+    monkeypatch.setenv("DEMAG_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    dims, cells, ms = _states(5, (17, 9, 3), (70, 40, 20), seed=8)
+    b = Batch(dims, cells)
+    tp, tb = b.autotune()
+    assert tb > 0 and (tp > 0 or tp == -1)
+    assert b.info()["mode"] == (0 if (tp > 0 and tp <= tb) else 1)
+    Hs, _ = b.field(ms)
+    torch.cuda.synchronize()
+    for i in (0, 3):
+        Href = oracle.field_fft(ms[i].double().cpu().numpy(), cells[i])
+        rel = np.max(np.abs(Hs[i].double().cpu().numpy() - Href)) / np.max(np.abs(Href))
+        assert rel <= 1e-5
+    b.close()
