@@ -258,8 +258,9 @@ long demag_launch_count(demag_plan_t plan);
  * fields; synchronises. */
 demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, void *stream);
 
-/* Current variant choice (z tile width 0/1, y radix order 0/1), and a way to
- * set it by hand. */
+/* Current variant choice (z-pass tile 0/1/2, y radix order 0/1), and a way
+ * to set it by hand. z variant 2 exists for a z length of 512 only; other
+ * lengths treat it as 0. */
 demag_status demag_get_variants(demag_plan_t plan, int *z, int *y);
 demag_status demag_set_variants(demag_plan_t plan, int z, int y);
 

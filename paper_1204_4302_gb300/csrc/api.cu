@@ -695,6 +695,8 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     // radix order where the two radices differ
     std::vector<int> zs = {0}, ys = {0};
     if (p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
+    if (p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
+    if (p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
     if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
     const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
     void *M = nullptr, *H = nullptr;
@@ -750,7 +752,7 @@ demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
 
 demag_status demag_set_variants(demag_plan_t p, int z, int y)
 {
-    if (!p || z < 0 || z > 1 || y < 0 || y > 1) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
+    if (!p || z < 0 || z > 3 || y < 0 || y > 1) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->zvariant = z;
     p->yvariant = y;
     return DEMAG_OK;

@@ -35,6 +35,11 @@ template <int L> struct ZRadix { static constexpr int R2 = 16, R1 = L / 16; };
 template <typename T> struct Tile2 { static constexpr int NT = 256; };
 template <> struct Tile2<double> { static constexpr int NT = 128; };
 
+// CTAs per SM the memory-bound passes are compiled for (register cap); more
+// resident CTAs keep more loads in flight.
+template <typename T, int L> struct Occ { static constexpr int MIN_CTAS = L <= 256 ? 4 : (L <= 512 ? 3 : 2); };
+template <int L> struct Occ<double, L> { static constexpr int MIN_CTAS = 2; };
+
 // Columns per CTA: the stage with fewer butterflies per column gives one
 // butterfly to every thread, the other stage loops.
 template <typename T, int L, int V = 0> struct ColShape {
@@ -49,8 +54,8 @@ template <typename T, int L, int V = 0> struct ColShape {
 // Variant 1: half the columns.
 template <typename T, int L, int V = 0> struct ZShape {
     static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2;
-    static constexpr int TC = (V == 0 ? Tile2<T>::NT : Tile2<T>::NT / 2) / R1;
-    static constexpr int NT = R1 == 2 * R2 ? 3 * TC * R2 : TC * R1;
+    static constexpr int TC = (V == 1 ? Tile2<T>::NT / 2 : Tile2<T>::NT) / R1;
+    static constexpr int NT = (V == 0 && R1 == 2 * R2) ? 3 * TC * R2 : TC * R1;
 };
 
 // v[r] *= W_L^(r * k) (or its conjugate), table W_L^m at tw[m * twstride]
@@ -119,7 +124,8 @@ __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__rest
                 u[r] = cmk<C>(0, 0);
                 if (!(PIN && r >= R1 / 2) && ok && row < nin) u[r] = ldp<CG>(&in[base + (int64_t)row * irs]);
             }
-            RegDFT<R1, INV, C>::run(u);
+            if constexpr (PIN) RegDFTHalfIn<R1, INV, C>::run(u);
+            else RegDFT<R1, INV, C>::run(u);
 #pragma unroll
             for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
         }
@@ -135,7 +141,8 @@ __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__rest
 #pragma unroll
             for (int r = 0; r < R2; ++r) v[r] = sm[sw((j2 + r * R1) * TC + c)];
             twiddle_row<R2, L, INV>(v, j2, tw, twstride);
-            RegDFT<R2, INV, C>::run(v);
+            if constexpr (POUT) RegDFTHalfOut<R2, INV, C>::run(v);
+            else RegDFT<R2, INV, C>::run(v);
             if (f < ncols) {
                 const int slab = f / width;
                 const int64_t base = (int64_t)slab * oss + (f - slab * width);
@@ -150,7 +157,7 @@ __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__rest
 }
 
 template <typename T, int L, bool INV, bool PIN, bool POUT, int V = 0>
-__global__ void __launch_bounds__(Tile2<T>::NT)
+__global__ void __launch_bounds__(Tile2<T>::NT, Occ<T, L>::MIN_CTAS)
 k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
        int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
        const typename Cplx<T>::type *__restrict__ tw, int twstride)
@@ -281,7 +288,7 @@ __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restric
                 for (int r = 0; r < R1 / 2; ++r)
                     if (j1 + r * R2 < nrows) u[r] = ldp<CG>(&col[(int64_t)r * R2 * rs]);
             }
-            RegDFT<R1, false, C>::run(u);
+            RegDFTHalfIn<R1, false, C>::run(u);
             C *s = sm + comp * TS + sw(j1 * R1 * TC + c);
 #pragma unroll
             for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
@@ -366,7 +373,7 @@ __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restric
             }
 #pragma unroll
             for (int r = 1; r < R1; ++r) u[r] = cmulc(u[r], __ldg(&tw[r * j1 * twstride]));
-            RegDFT<R1, true, C>::run(u);
+            RegDFTHalfOut<R1, true, C>::run(u);
             if (f < ncols) {
                 const int i = f / width;
                 C *col = S + (int64_t)ky_pair_order(i, Py) * ss + (f - i * width) + comp * cs + j1 * rs;
@@ -386,6 +393,190 @@ k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     k_z_conv2_tile<T, L, V, false>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, blockIdx.x, smraw);
+}
+
+// Fused z pass, persistent and software pipelined (L >= 32): each CTA loops
+// over tiles; while a tile is transformed, the next tile's input rows
+// (three components, rows < nrows) and its tensor block are copied into
+// shared memory with cp.async, so the copies overlap the arithmetic of the
+// current tile. Same arithmetic and result as k_z_conv2.
+template <typename T, int L>
+__global__ void __launch_bounds__(ZShape<T, L, 0>::NT, 1)
+k_z_conv3(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+          int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
+          int twstride, int ntiles)
+{
+    using C = typename Cplx<T>::type;
+    using Sh = ZShape<T, L, 0>;
+    constexpr int R1 = Sh::R1, R2 = Sh::R2, NT = Sh::NT, TC = Sh::TC;
+    constexpr int TS = swsize(L * TC);
+    constexpr int NB1 = TC * R2;
+    constexpr int HZ = L / 2 + 1;
+    constexpr int NZ2 = L / 2;  // at most L/2 input rows
+    static_assert(NT % TC == 0, "tensor prefetch assumes TC divides the threads");
+    static_assert((R1 * TC) % 32 == 0 && (R2 * TC) % 32 == 0, "shared-memory offsets need 32-aligned rows");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);        // exchange [3][TS]
+    C *stg = sm + 3 * TS;                        // staged input [3][NZ2][TC]
+    T *smT = reinterpret_cast<T *>(stg + 3 * NZ2 * TC);  // tensor block [HZ][6][TC]
+    const int hy = Py / 2 + 1;
+    const int64_t plane = (int64_t)HZ * hy * Kx;
+
+    auto issue_input = [&](int tile) {
+        // thread -> fixed column c (NT is a multiple of TC); rows strided by NT / TC
+        const int c = threadIdx.x % TC, f = tile * TC + c;
+        if (f >= ncols) return;
+        const int i = f / width;
+        const C *base = S + (int64_t)ky_pair_order(i, Py) * ss + (f - i * width);
+        for (int row = threadIdx.x / TC; row < nrows; row += NT / TC) {
+            const C *src = base + (int64_t)row * rs;
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                C *dst = &stg[(comp * NZ2 + row) * TC + c];
+                if constexpr (sizeof(C) == 8) cp_async8(dst, src + comp * cs);
+                else {
+                    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + comp * cs) : "memory");
+                }
+            }
+        }
+    };
+    auto issue_tensor = [&](int tile) {
+        const int c = threadIdx.x % TC, f = tile * TC + c;
+        if (f < ncols) {
+            const int i = f / width, kx = f - i * width;
+            const int ky = ky_pair_order(i, Py);
+            const int kyf = ky > Py / 2 ? Py - ky : ky;
+            const T *src = nhat + (int64_t)kyf * Kx + kx;
+            for (int idx = threadIdx.x / TC; idx < HZ * 6; idx += NT / TC) {
+                const int kzf = idx / 6, comp = idx - kzf * 6;
+                cp_async_elem(&smT[idx * TC + c], src + comp * plane + (int64_t)kzf * hy * Kx);
+            }
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (tile < ntiles) {
+        issue_input(tile);
+        issue_tensor(tile);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        const int f0 = tile * TC;
+        // forward stage 1 from the staged rows
+#pragma unroll
+        for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+            const int b = threadIdx.x + q * NT;
+            if (b < 3 * NB1) {
+                const int comp = b / NB1, bb = b - comp * NB1;
+                const int c = bb % TC, j1 = bb / TC;
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+                if (f0 + c < ncols) {
+                    const C *col = stg + (comp * NZ2 + j1) * TC + c;
+#pragma unroll
+                    for (int r = 0; r < R1 / 2; ++r)
+                        if (j1 + r * R2 < nrows) u[r] = col[r * R2 * TC];
+                }
+                RegDFTHalfIn<R1, false, C>::run(u);
+                C *s = sm + comp * TS + sw(j1 * R1 * TC + c);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
+            }
+        }
+        __syncthreads();
+        if (next < ntiles) issue_input(next);  // the staging buffer is free again
+
+        const bool act2 = threadIdx.x < TC * R1;
+        const int c2 = threadIdx.x % TC, j2 = threadIdx.x / TC, f2 = f0 + c2;
+        C v0[R2], v1[R2], v2[R2];
+        if (act2) {
+            const C *s = sm + sw(j2 * TC + c2);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                constexpr int step = R1 * TC + (R1 * TC) / 32;
+                v0[r] = s[r * step];
+                v1[r] = s[TS + r * step];
+                v2[r] = s[2 * TS + r * step];
+            }
+#pragma unroll
+            for (int r = 1; r < R2; ++r) {
+                const C w = __ldg(&tw[r * j2 * twstride]);
+                v0[r] = cmul(v0[r], w);
+                v1[r] = cmul(v1[r], w);
+                v2[r] = cmul(v2[r], w);
+            }
+            RegDFT<R2, false, C>::run(v0);
+            RegDFT<R2, false, C>::run(v1);
+            RegDFT<R2, false, C>::run(v2);
+            if (f2 < ncols) {
+                const int ky = ky_pair_order(f2 / width, Py);
+                const T sy = ky > Py / 2 ? (T)-1 : (T)1;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    int kzf;
+                    T sz;
+                    if (r < R2 / 2) { kzf = j2 + r * R1; sz = (T)1; }
+                    else if (r == R2 / 2) { kzf = L / 2 - j2; sz = j2 == 0 ? (T)1 : (T)-1; }
+                    else { kzf = (R2 - r) * R1 - j2; sz = (T)-1; }
+                    const T *t = smT + kzf * 6 * TC + c2;
+                    const T nxx = t[0], nyy = t[TC], nzz = t[2 * TC];
+                    const T nxy = sy * t[3 * TC], nxz = sz * t[4 * TC], nyz = sy * sz * t[5 * TC];
+                    const C mx = v0[r], my = v1[r], mz = v2[r];
+                    v0[r] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+                    v1[r] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+                    v2[r] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+                }
+            }
+            RegDFT<R2, true, C>::run(v0);
+            RegDFT<R2, true, C>::run(v1);
+            RegDFT<R2, true, C>::run(v2);
+        }
+        __syncthreads();  // stage-2 reads of the exchange and the tensor block are done
+        if (next < ntiles) issue_tensor(next);
+        if (act2) {
+            C *s = sm + sw(j2 * R2 * TC + c2);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                const int o = r * TC + (r * TC) / 32;
+                s[o] = v0[r];
+                s[TS + o] = v1[r];
+                s[2 * TS + o] = v2[r];
+            }
+        }
+        __syncthreads();
+        // inverse stage 2, rows < nrows stored
+#pragma unroll
+        for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+            const int b = threadIdx.x + q * NT;
+            if (b < 3 * NB1) {
+                const int comp = b / NB1, bb = b - comp * NB1;
+                const int c = bb % TC, j1 = bb / TC, f = f0 + c;
+                const C *s = sm + comp * TS + sw(j1 * TC + c);
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    constexpr int step = R2 * TC + (R2 * TC) / 32;
+                    u[r] = s[r * step];
+                }
+#pragma unroll
+                for (int r = 1; r < R1; ++r) u[r] = cmulc(u[r], __ldg(&tw[r * j1 * twstride]));
+                RegDFTHalfOut<R1, true, C>::run(u);
+                if (f < ncols) {
+                    const int i = f / width;
+                    C *col = S + (int64_t)ky_pair_order(i, Py) * ss + (f - i * width) + comp * cs + j1 * rs;
+#pragma unroll
+                    for (int r = 0; r < R1 / 2; ++r)
+                        if (j1 + r * R2 < nrows) col[(int64_t)r * R2 * rs] = u[r];
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();  // next tile's copies have landed; the exchange is free
+    }
 }
 
 // Fused z pass for L <= 16: one thread per column, all in registers.
@@ -497,15 +688,30 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
         if (row < nrows) {
             const T *p = a.in + (int64_t)row * a.in_rs;
             const T ws = a.wscalar;
+            if ((a.in_rs & 1) == 0 && !a.wcell) {
+                // even rows: pairs are aligned, one vector load per complex value
 #pragma unroll
-            for (int r = 0; r < (PIN ? R1 / 2 : R1); ++r) {
-                const int x0 = 2 * (j1 + r * R2);
-                if (x0 < nvalid) u[r].x = p[x0] * ws * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
-                if (x0 + 1 < nvalid)
-                    u[r].y = p[x0 + 1] * ws * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0 + 1);
+                for (int r = 0; r < (PIN ? R1 / 2 : R1); ++r) {
+                    const int x0 = 2 * (j1 + r * R2);
+                    if (x0 + 1 < nvalid) {
+                        const C q = *reinterpret_cast<const C *>(p + x0);
+                        u[r] = cmk<C>(q.x * ws, q.y * ws);
+                    } else if (x0 < nvalid) {
+                        u[r].x = p[x0] * ws;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < (PIN ? R1 / 2 : R1); ++r) {
+                    const int x0 = 2 * (j1 + r * R2);
+                    if (x0 < nvalid) u[r].x = p[x0] * ws * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
+                    if (x0 + 1 < nvalid)
+                        u[r].y = p[x0 + 1] * ws * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0 + 1);
+                }
             }
         }
-        RegDFT<R1, false, C>::run(u);
+        if constexpr (PIN) RegDFTHalfIn<R1, false, C>::run(u);
+        else RegDFT<R1, false, C>::run(u);
         C *s = sm + rr * RS;
 #pragma unroll
         for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
@@ -600,7 +806,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
 #pragma unroll
         for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
-        RegDFT<R2, true, C>::run(v);
+        RegDFTHalfOut<R2, true, C>::run(v);
         if (row < nrows) {
             const T g = o.gdev ? (T)(*o.gdev) : (T)1;
             const T oscale = o.oscale * g;
@@ -629,7 +835,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(Tile2<T>::NT)
+__global__ void __launch_bounds__(Tile2<T>::NT, Occ<T, 2 * L>::MIN_CTAS)
 k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx)
 {

@@ -96,6 +96,50 @@ template <bool INV, typename C> struct RegDFT<1, INV, C> {
     static __device__ __forceinline__ void run(C *) {}
 };
 
+// DFT of N points whose inputs v[N/2..N) are zero (the zero padding of the
+// convolution): the same decimation in time, with the leaf butterflies of an
+// input and a zero reduced to copies. Output v[0..N) in natural order.
+template <int N, bool INV, typename C> struct RegDFTHalfIn {
+    static __device__ __forceinline__ void run(C *v)
+    {
+        C e[N / 2], o[N / 2];
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+        RegDFTHalfIn<N / 2, INV, C>::run(e);
+        RegDFTHalfIn<N / 2, INV, C>::run(o);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const C t = twconst<N, INV>(k, o[k]);
+            v[k] = cadd(e[k], t);
+            v[k + N / 2] = csub(e[k], t);
+        }
+    }
+};
+template <bool INV, typename C> struct RegDFTHalfIn<2, INV, C> {
+    static __device__ __forceinline__ void run(C *v) { v[1] = v[0]; }
+};
+template <bool INV, typename C> struct RegDFTHalfIn<1, INV, C> {
+    static __device__ __forceinline__ void run(C *) {}
+};
+
+// DFT of N points of which only the outputs v[0..N/2) are used: the last
+// butterfly level computes the sums only.
+template <int N, bool INV, typename C> struct RegDFTHalfOut {
+    static __device__ __forceinline__ void run(C *v)
+    {
+        C e[N / 2], o[N / 2];
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+        RegDFT<N / 2, INV, C>::run(e);
+        RegDFT<N / 2, INV, C>::run(o);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) v[k] = cadd(e[k], twconst<N, INV>(k, o[k]));
+    }
+};
+template <bool INV, typename C> struct RegDFTHalfOut<1, INV, C> {
+    static __device__ __forceinline__ void run(C *) {}
+};
+
 __device__ __forceinline__ int sw(int e) { return e + (e >> 5); }
 
 __host__ __device__ constexpr int swsize(int elems) { return elems + (elems >> 5) + 1; }

@@ -12,6 +12,18 @@ namespace {
 
 // Opt in to more than 48 KB of dynamic shared memory, once per kernel and
 // device (the cache is per template argument, i.e. per kernel).
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    return sms;
+}
+
 template <auto Kern>
 cudaError_t allow_smem(size_t bytes)
 {
@@ -208,10 +220,37 @@ cudaError_t Passes<T>::zconv_launch(C *S, int ncols, int width, int64_t ss, int6
 }
 
 template <typename T>
+template <int L>
+cudaError_t Passes<T>::zconv_pipe(C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                  const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st)
+{
+    using Sh = ZShape<T, L, 0>;
+    const size_t sm = 3 * swsize(L * Sh::TC) * sizeof(C) + 3 * (L / 2) * Sh::TC * sizeof(C) +
+                      (L / 2 + 1) * 6 * Sh::TC * sizeof(T);
+    if (sm > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem<k_z_conv3<T, L>>(sm);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
+    const int ntiles = (ncols + Sh::TC - 1) / Sh::TC;
+    const int grid = ntiles < sms ? ntiles : sms;
+    k_z_conv3<T, L><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, ntiles);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant)
 {
+    if (variant == 3 && ncols > 0 && 2 * nrows <= L) {
+        switch (L) {
+        case 64: return zconv_pipe<64>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        case 128: return zconv_pipe<128>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        case 256: return zconv_pipe<256>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        case 512: return zconv_pipe<512>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        default: variant = 0;
+        }
+    }
     if (ncols <= 0) return cudaSuccess;
     if (2 * nrows > L && L > 1) return cudaErrorInvalidValue;  // the z pass always has padding
     if (L <= 16) {
@@ -236,6 +275,7 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
 #define DEMAG_CASE(LL)                                                                         \
     case LL:                                                                                   \
         return variant == 1 ? zconv_launch<LL, 1>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
+             : variant == 2 ? zconv_launch<LL, 2>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
                             : zconv_launch<LL, 0>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
     switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE

@@ -64,6 +64,9 @@ template <typename T> struct Passes {
     static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant = 0);
+    template <int L>
+    static cudaError_t zconv_pipe(C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                  const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st);
     template <int L, int V>
     static cudaError_t zconv_launch(C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
                                     const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st);
