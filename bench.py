@@ -63,6 +63,22 @@ def pass_bytes(n, P, elem=4):
     }
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest value of x over all ranks (the slowest rank's time); x itself
+    without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time (cells/s)."""
+    return world * cells_per_rank * steps / (ms_max / 1e3)
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_1204_4302_gb300", "csrc"))):
@@ -184,7 +200,7 @@ def run_ours(args, rank, world, local_rank):
     plan = Plan(n, CELL, prec="f32", device=dev)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
-    tuned_ms = plan.autotune(use_cache=False)
+    tuned_ms = None if args.no_tune else plan.autotune(use_cache=False)
     variants = plan.variants()
     info = plan.info()
     P = (info["px"], info["py"], info["pz"])
@@ -220,12 +236,9 @@ def run_ours(args, rank, world, local_rank):
     pass_ms, pass_n = plan.get_timing(6)
     plan.set_timing(False)
     clocks = sampler.stop() if sampler else None
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = world * cells * args.steps / (ms / 1e3)
+    value = whole_job_rate(cells, world, args.steps, ms)
 
     # energy sanity (device value, read after timing)
     E_val = float(E.item())
@@ -322,11 +335,7 @@ def run_ours(args, rank, world, local_rank):
             B.demag_field_host(plan.handle, Mh.data_ptr(), Hh.data_ptr(), st.cuda_stream)
         barrier()
         te = (time.perf_counter() - t0) / ke
-        tmax = te
-        if dist is not None:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tmax = float(t.item())
+        tmax = max_over_ranks(te, dist, dev)
         nbytes = 3 * cells * 4
         e2e = {"value": world * cells / tmax, "unit": "cells/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": round(tmax * 1e3, 4)}
@@ -360,7 +369,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs and spectra (~2 GB) larger than L2, no flush needed"},
             "gpu_launches": launches,
             "setup_ms": round(setup_ms, 1),
-            "autotune": {"z_variant": variants[0], "y_variant": variants[1], "ms_per_field": round(tuned_ms, 4)},
+            "autotune": {"z_variant": variants[0], "y_variant": variants[1],
+                         "ms_per_field": None if tuned_ms is None else round(tuned_ms, 4)},
             "batch": batch,
             "energy_J": E_val,
             "passes": per_pass,
@@ -509,6 +519,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")
     ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")
     args = ap.parse_args()
     if args.warmup < 3:

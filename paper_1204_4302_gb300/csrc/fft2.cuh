@@ -729,8 +729,9 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
         RegDFT<R2, false, C>::run(v);
         const int lane = threadIdx.x & 31;
         const int partner = (lane & ~(R1 - 1)) | ((R1 - j2) & (R1 - 1));
-        C X[R2];
         const T h = (T)0.5;
+        C *o = out + (int64_t)row * out_rs;
+        const bool live = row < nrows;
 #pragma unroll
         for (int r = 0; r < R2; ++r) {
             const C q = shfl_c(v[R2 - 1 - r], partner);
@@ -738,18 +739,10 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
             const int k = j2 + r * R1;
             const C E = cmk<C>(h * (v[r].x + pz.x), h * (v[r].y - pz.y));
             const C O = cmk<C>(h * (v[r].y + pz.y), -h * (v[r].x - pz.x));
-            X[r] = cadd(E, cmul(O, __ldg(&twx[k])));
+            if (live) o[k] = cadd(E, cmul(O, __ldg(&twx[k])));
         }
-        if (row < nrows) {
-            C *o = out + (int64_t)row * out_rs;
-#pragma unroll
-            for (int r = 0; r < R2; ++r) o[j2 + r * R1] = X[r];
-            if (j2 == 0) {
-                // X[L] = E(0) - O(0) (W_{2L}^L = -1), from Z[0]
-                const C z0 = v[0];
-                o[L] = cmk<C>(z0.x - z0.y, (T)0);
-            }
-        }
+        // X[L] = E(0) - O(0) (W_{2L}^L = -1), from Z[0]
+        if (live && j2 == 0) o[L] = cmk<C>(v[0].x - v[0].y, (T)0);
     }
 }
 
@@ -797,7 +790,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
     }
     __syncthreads();
-    T acc = 0, cmp = 0;
+    T acc = 0;  // per-thread sum of a few dozen terms; blocks reduce in FP64
     if (threadIdx.x < TR * R1) {
         const int rr = threadIdx.x / R1, j2 = threadIdx.x % R1, row = row0 + rr;
         const C *s = sm + rr * RS;
@@ -821,21 +814,16 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
                     const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
                     const int64_t idx = (int64_t)row * o.out_rs + x;
                     if (o.out) o.out[idx] = hv[u] * oscale * w;
-                    if (o.partials) {
-                        const T t = o.mscale * w * o.Mref[idx] * hv[u];
-                        const T y = t - cmp, sum = acc + y;
-                        cmp = (sum - acc) - y;
-                        acc = sum;
-                    }
+                    if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
                 }
             }
         }
     }
-    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials, tile);
+    if (o.partials) block_partial<NT>((double)acc, o.partials, tile);
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(Tile2<T>::NT, Occ<T, 2 * L>::MIN_CTAS)
+__global__ void __launch_bounds__(Tile2<T>::NT, (L >= 512 ? Occ<T, 2 * L>::MIN_CTAS : Occ<T, L>::MIN_CTAS))
 k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx)
 {

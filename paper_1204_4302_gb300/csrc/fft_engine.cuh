@@ -327,7 +327,7 @@ __device__ __forceinline__ void k_x_inv_tile(const typename Cplx<T>::type *__res
     tile_fft<C, L, true, NT, TC>(sm, twx, 2);
     const T g = o.gdev ? (T)(*o.gdev) : (T)1;
     const T oscale = o.oscale * g;
-    T acc = 0, cmp = 0;  // compensated per-thread sum of mscale * w * Mref * h
+    T acc = 0;  // per-thread sum of mscale * w * Mref * h (a few dozen terms)
     for (int e = threadIdx.x; e < L * TC; e += NT) {
         const int n = e % L, rr = e / L, row = row0 + rr;
         if (row >= nrows) continue;
@@ -340,15 +340,10 @@ __device__ __forceinline__ void k_x_inv_tile(const typename Cplx<T>::type *__res
             const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
             const int64_t idx = (int64_t)row * o.out_rs + x;
             if (o.out) o.out[idx] = hv[u] * oscale * w;
-            if (o.partials) {
-                const T t = o.mscale * w * o.Mref[idx] * hv[u];
-                const T y = t - cmp, s = acc + y;
-                cmp = (s - acc) - y;
-                acc = s;
-            }
+            if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
         }
     }
-    if (o.partials) block_partial<NT>((double)acc - (double)cmp, o.partials, tile);
+    if (o.partials) block_partial<NT>((double)acc, o.partials, tile);
 }
 
 template <typename T, int L>
