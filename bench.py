@@ -323,22 +323,34 @@ def run_ours(args, rank, world, local_rank):
     # ------------------------------------------------ end to end (host buffers)
     e2e = None
     if not args.skip_e2e:
-        from paper_1204_4302_gb300 import binding as B
+        # end to end through the public API from pinned host buffers: every
+        # step uploads its M and downloads its H; streamed calls overlap one
+        # step's copies with the neighbouring steps' fields
         Mh = M.cpu().pin_memory()
-        Hh = torch.empty_like(Mh).pin_memory()
-        for _ in range(2):
-            B.demag_field_host(plan.handle, Mh.data_ptr(), Hh.data_ptr(), st.cuda_stream)
+        Hh = [torch.empty_like(Mh).pin_memory() for _ in range(2)]
+        for i in range(3):
+            plan.field_host_async(Mh, Hh[i % 2])
+        plan.host_wait()
         barrier()
-        ke = max(3, args.steps // 2)
+        ke = max(5, args.steps)
         t0 = time.perf_counter()
-        for _ in range(ke):
-            B.demag_field_host(plan.handle, Mh.data_ptr(), Hh.data_ptr(), st.cuda_stream)
+        for i in range(ke):
+            plan.field_host_async(Mh, Hh[i % 2])
+        plan.host_wait()
         barrier()
         te = (time.perf_counter() - t0) / ke
         tmax = max_over_ranks(te, dist, dev)
+        # the same calls one at a time (upload, field, download, synchronise)
+        from paper_1204_4302_gb300 import binding as B
+        t1 = time.perf_counter()
+        for i in range(3):
+            B.demag_field_host(plan.handle, Mh.data_ptr(), Hh[0].data_ptr(), st.cuda_stream)
+        ts = (time.perf_counter() - t1) / 3
         nbytes = 3 * cells * 4
         e2e = {"value": world * cells / tmax, "unit": "cells/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "ms_per_step": round(tmax * 1e3, 4)}
+               "d2h_bytes_per_step": nbytes, "ms_per_step": round(tmax * 1e3, 4),
+               "mode": "streamed demag_field_host_async calls, pinned buffers",
+               "ms_per_step_synchronous": round(ts * 1e3, 4)}
 
     batch = None
     if not args.skip_batch:

@@ -143,6 +143,20 @@ demag_status demag_energy_grad(demag_plan_t plan, const void *m, const void *w, 
  * works too. Uses plan-owned device buffers allocated at the first call. */
 demag_status demag_field_host(demag_plan_t plan, const void *M_host, void *H_host, void *stream);
 
+/* Streaming variant of demag_field_host for sequences of host-resident
+ * states: returns without synchronising. The upload runs on a copy stream,
+ * the field on `stream`, the download on a second copy stream, through two
+ * alternating device slots, so consecutive calls overlap one call's download
+ * and the next call's upload with the fields. The caller must keep M_host
+ * unchanged and must not read H_host until demag_host_wait() returns (or
+ * until two further calls have been issued and waited for); page-locked
+ * buffers are needed for the copies to overlap. Device buffers (two input
+ * and two output fields) are allocated at the first call. */
+demag_status demag_field_host_async(demag_plan_t plan, const void *M_host, void *H_host, void *stream);
+
+/* Waits for every upload and download issued by demag_field_host_async. */
+demag_status demag_host_wait(demag_plan_t plan);
+
 /* Plan sizes and memory. */
 demag_status demag_plan_info(demag_plan_t plan, demag_info *info);
 

@@ -36,6 +36,7 @@ EXPORTS = [
     "demag_batch_create", "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
+    "demag_field_host_async", "demag_host_wait",
 ]
 
 
@@ -110,6 +111,8 @@ def load(path: str | Path | None = None):
         "demag_get_variants": (S, [P, POINTER(c_int), POINTER(c_int)]),
         "demag_set_variants": (S, [P, I, I]),
         "demag_batch_autotune": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
+        "demag_field_host_async": (S, [P, P, P, P]),
+        "demag_host_wait": (S, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +179,14 @@ def demag_energy_grad(plan, m, w, Ms, E_dev, grad, gscale_dev=None, stream=0):
 
 def demag_field_host(plan, M_host, H_host, stream=0):
     _check(load().demag_field_host(_p(plan), _p(M_host), _p(H_host), _p(stream)), "demag_field_host")
+
+
+def demag_field_host_async(plan, M_host, H_host, stream=0):
+    _check(load().demag_field_host_async(_p(plan), _p(M_host), _p(H_host), _p(stream)), "demag_field_host_async")
+
+
+def demag_host_wait(plan):
+    _check(load().demag_host_wait(_p(plan)), "demag_host_wait")
 
 
 def demag_plan_info(plan) -> dict:

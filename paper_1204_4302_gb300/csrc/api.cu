@@ -392,6 +392,19 @@ void demag_plan_destroy(demag_plan_t p)
     cudaFree(p->e_dev);
     cudaFree(p->dM);
     cudaFree(p->dH);
+    if (p->async_ready) {
+        cudaStreamSynchronize(p->s_in);
+        cudaStreamSynchronize(p->s_out);
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(p->aM[k]);
+            cudaFree(p->aH[k]);
+            cudaEventDestroy(p->ev_in[k]);
+            cudaEventDestroy(p->ev_done[k]);
+            cudaEventDestroy(p->ev_out[k]);
+        }
+        cudaStreamDestroy(p->s_in);
+        cudaStreamDestroy(p->s_out);
+    }
     if (p->ring) {
         TimingRing *R = ring_of(p);
         for (int s = 0; s < kRing; ++s)
@@ -624,6 +637,56 @@ demag_status demag_energy_grad(demag_plan_t p, const void *m, const void *w, dou
     j.gdev = gscale_dev;
     j.E_dev = E_dev;
     return run_job(p, j, stream);
+}
+
+demag_status demag_field_host_async(demag_plan_t p, const void *M_host, void *H_host, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!M_host || !H_host) return fail(DEMAG_ERR_INVALID_ARG, "host buffers must not be NULL");
+    if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
+    if (!p->async_ready) {
+        for (int k = 0; k < 2; ++k) {
+            DEMAG_CUDA(cudaMalloc(&p->aM[k], bytes));
+            DEMAG_CUDA(cudaMalloc(&p->aH[k], bytes));
+            DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming));
+            DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_done[k], cudaEventDisableTiming));
+            DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming));
+            p->out_recorded[k] = false;
+        }
+        DEMAG_CUDA(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+        DEMAG_CUDA(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+        p->slot = 0;
+        p->async_ready = true;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int k = p->slot;
+    p->slot ^= 1;
+    // the slot's previous download must be done before its buffers are reused
+    if (p->out_recorded[k]) DEMAG_CUDA(cudaStreamWaitEvent(p->s_in, p->ev_out[k], 0));
+    DEMAG_CUDA(cudaMemcpyAsync(p->aM[k], M_host, bytes, cudaMemcpyHostToDevice, p->s_in));
+    DEMAG_CUDA(cudaEventRecord(p->ev_in[k], p->s_in));
+    DEMAG_CUDA(cudaStreamWaitEvent(st, p->ev_in[k], 0));
+    demag_status s = run_job(p, plain_job(p->aM[k], p->aH[k], nullptr), stream);
+    if (s != DEMAG_OK) return s;
+    DEMAG_CUDA(cudaEventRecord(p->ev_done[k], st));
+    DEMAG_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_done[k], 0));
+    DEMAG_CUDA(cudaMemcpyAsync(H_host, p->aH[k], bytes, cudaMemcpyDeviceToHost, p->s_out));
+    DEMAG_CUDA(cudaEventRecord(p->ev_out[k], p->s_out));
+    p->out_recorded[k] = true;
+    return DEMAG_OK;
+}
+
+demag_status demag_host_wait(demag_plan_t p)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->async_ready) return DEMAG_OK;
+    DeviceGuard g(p->device);
+    DEMAG_CUDA(cudaStreamSynchronize(p->s_in));
+    DEMAG_CUDA(cudaStreamSynchronize(p->s_out));
+    return DEMAG_OK;
 }
 
 demag_status demag_plan_info(demag_plan_t p, demag_info *info)

@@ -140,6 +140,13 @@ struct demag_plan {
     double *e_dev;
     // host-buffer entry point buffers
     void *dM, *dH;
+    // asynchronous host entry point: two device slots, copy streams, events
+    void *aM[2], *aH[2];
+    cudaStream_t s_in, s_out;
+    cudaEvent_t ev_in[2], ev_done[2], ev_out[2];
+    bool out_recorded[2];
+    int slot;
+    bool async_ready;
     bool setup_done;
     double imag_max;
     // tuning choices (kernel variants), set by demag_autotune or defaults

@@ -133,6 +133,17 @@ class Plan:
         B.demag_field_host(self.handle, M_host.data_ptr(), H_host.data_ptr(), self._stream())
         return H_host
 
+    def field_host_async(self, M_host, H_host):
+        """Queue an end-to-end field evaluation of pinned host buffers; call
+        host_wait() before reading H_host or changing M_host."""
+        for t in (M_host, H_host):
+            if t.device.type != "cpu" or t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors of the plan's dtype and shape")
+        B.demag_field_host_async(self.handle, M_host.data_ptr(), H_host.data_ptr(), self._stream())
+
+    def host_wait(self):
+        B.demag_host_wait(self.handle)
+
     # ------------------------------------------------------------------ tuning
     def autotune(self, use_cache: bool = True) -> float:
         """Pick the fastest kernel variants for this plan; returns ms per field call."""
