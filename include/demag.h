@@ -272,9 +272,13 @@ long demag_launch_count(demag_plan_t plan);
  * fields; synchronises. */
 demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, void *stream);
 
-/* Current variant choice (z-pass tile 0/1/2, y radix order 0/1), and a way
- * to set it by hand. z variant 2 exists for a z length of 512 only; other
- * lengths treat it as 0. */
+/* Current variant choice, and a way to set it by hand.
+ * z: 0 = two-stage fused pass, 1 = half-width tile, 2 = 256-thread tile
+ *    (z length 512 only), 3 = persistent pipelined pass (z lengths 64..512).
+ * y: 0 = two-stage column transform, 1 = swapped radix order (y lengths 32,
+ *    128, 512), 2 = three-stage transform with more CTAs per SM (y lengths
+ *    512 and 1024). A variant that does not exist for the plan's lengths runs
+ *    as variant 0. Out-of-range values: DEMAG_ERR_INVALID_ARG. */
 demag_status demag_get_variants(demag_plan_t plan, int *z, int *y);
 demag_status demag_set_variants(demag_plan_t plan, int z, int y);
 

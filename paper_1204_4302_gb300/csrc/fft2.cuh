@@ -166,6 +166,85 @@ k_col2(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__
     k_col2_tile<T, L, INV, PIN, POUT, false, V>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, blockIdx.x, smraw);
 }
 
+// Three-stage column transform for long columns (L = 512, 1024): radices
+// 8 x 8 x 8 (or 8 x 8 x 16), so each thread holds at most 16 values and many
+// more CTAs fit on an SM; one more shared-memory exchange than k_col2. First
+// stage from global memory, middle stage in shared memory, last stage to
+// global memory. A tuning variant of k_col2 with the same result.
+template <int L> struct Col3Radix;
+template <> struct Col3Radix<512> { static constexpr int R1 = 8, R2 = 8, R3 = 8; };
+template <> struct Col3Radix<1024> { static constexpr int R1 = 8, R2 = 8, R3 = 16; };
+
+template <typename T, int L> struct Col3Shape {
+    static constexpr int R1 = Col3Radix<L>::R1, R2 = Col3Radix<L>::R2, R3 = Col3Radix<L>::R3;
+    static constexpr int NT = 2 * Tile2<T>::NT;
+    static constexpr int TC = 8;
+};
+
+template <typename T, int L, bool INV, bool PIN, bool POUT>
+__global__ void __launch_bounds__(Col3Shape<T, L>::NT)
+k_col3(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,
+       int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
+       const typename Cplx<T>::type *__restrict__ tw, int twstride)
+{
+    using C = typename Cplx<T>::type;
+    using S = Col3Shape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, R3 = S::R3, NT = S::NT, TC = S::TC;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int f0 = blockIdx.x * TC;
+    // stage 1: radix R1 over rows j1 + r L/R1 -> rows j1 R1 + r
+#pragma unroll
+    for (int q = 0; q < (TC * (L / R1) + NT - 1) / NT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b < TC * (L / R1)) {
+            const int c = b % TC, j1 = b / TC, f = f0 + c;
+            C u[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+            if (f < ncols) {
+                const int slab = f / width;
+                const C *col = in + (int64_t)slab * iss + (f - slab * width);
+#pragma unroll
+                for (int r = 0; r < (PIN ? R1 / 2 : R1); ++r) {
+                    const int row = j1 + r * (L / R1);
+                    if (row < nin) u[r] = col[(int64_t)row * irs];
+                }
+            }
+            if constexpr (PIN) RegDFTHalfIn<R1, INV, C>::run(u);
+            else RegDFT<R1, INV, C>::run(u);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
+        }
+    }
+    __syncthreads();
+    // stage 2 in shared memory (radix R2, NS = R1)
+    fft_stage<C, L, R2, R1, INV, NT, TC>(sm, tw, twstride);
+    // stage 3: radix R3, NS = R1 R2 = L / R3; outputs rows j + r L/R3
+#pragma unroll
+    for (int q = 0; q < (TC * (L / R3) + NT - 1) / NT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b < TC * (L / R3)) {
+            const int c = b % TC, j = b / TC, f = f0 + c;
+            C v[R3];
+#pragma unroll
+            for (int r = 0; r < R3; ++r) v[r] = sm[sw((j + r * (L / R3)) * TC + c)];
+            twiddle_row<R3, L, INV>(v, j, tw, twstride);
+            if constexpr (POUT) RegDFTHalfOut<R3, INV, C>::run(v);
+            else RegDFT<R3, INV, C>::run(v);
+            if (f < ncols) {
+                const int slab = f / width;
+                C *col = out + (int64_t)slab * oss + (f - slab * width);
+#pragma unroll
+                for (int r = 0; r < (POUT ? R3 / 2 : R3); ++r) {
+                    const int row = j + r * (L / R3);
+                    if (row < nout) col[(int64_t)row * ors] = v[r];
+                }
+            }
+        }
+    }
+}
+
 // Short columns (L <= 16): one thread per column, no shared memory.
 template <typename T, int L, bool INV, bool CG>
 __device__ __forceinline__ void k_col1_tile(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols,

@@ -192,6 +192,28 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
     }
     // the zero padding halves the input (forward) or the output (inverse)
     const bool pin = 2 * nin <= L, pout = 2 * nout <= L;
+    if (variant == 2 && (L == 512 || L == 1024) && (pin || pout) && !(pin && inv) && !(pout && !inv)) {
+#define DEMAG_C3(LL)                                                                                    \
+    if (L == LL) {                                                                                      \
+        using S3 = Col3Shape<T, LL>;                                                                    \
+        const size_t sm3 = swsize(LL * S3::TC) * sizeof(C);                                             \
+        const int grid3 = (ncols + S3::TC - 1) / S3::TC;                                                \
+        cudaError_t e3;                                                                                 \
+        if (inv) {                                                                                      \
+            e3 = allow_smem<k_col3<T, LL, true, false, true>>(sm3);                                     \
+            if (e3 != cudaSuccess) return e3;                                                           \
+            k_col3<T, LL, true, false, true><<<grid3, S3::NT, sm3, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride); \
+        } else {                                                                                        \
+            e3 = allow_smem<k_col3<T, LL, false, true, false>>(sm3);                                    \
+            if (e3 != cudaSuccess) return e3;                                                           \
+            k_col3<T, LL, false, true, false><<<grid3, S3::NT, sm3, st>>>(in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride); \
+        }                                                                                               \
+        return cudaGetLastError();                                                                      \
+    }
+        DEMAG_C3(512)
+        DEMAG_C3(1024)
+#undef DEMAG_C3
+    }
     // variant 1 (swapped radix order) exists for the pruned field passes
 #define DEMAG_CASE(LL)                                                                         \
     case LL:                                                                                   \
