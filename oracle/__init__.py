@@ -21,6 +21,14 @@ What is computed (paper Sec. 2 and Sec. 3.1):
 
 Layout: M and H are float64 arrays of shape (3, nz, ny, nx) (x fastest).
 The tensor table has shape (6, nz, ny, nx) in the order xx, yy, zz, xy, xz, yz.
+
+The scalar-potential method (SP, Sec. 3.1, Eqs. "scpot" and "field") has its
+own oracle in ``scalar_potential.c`` and the ``sp_*`` functions below: the
+potential at the grid nodes as the sum over cells of M . S with the vector
+kernel S of one homogeneously magnetized cell, by direct sum or by zero-padded
+FFT convolution, and the field of each cell from the node potentials by
+finite differences (the cell average of minus the gradient of the trilinear
+interpolant). Potentials have shape (nz+1, ny+1, nx+1).
 """
 from __future__ import annotations
 
@@ -42,15 +50,18 @@ _lib = None
 COMPONENTS = ("xx", "yy", "zz", "xy", "xz", "yz")
 
 
+_SOURCES = ("newell.c", "scalar_potential.c")
+
+
 def build(force: bool = False) -> Path:
-    """Compile newell.c into oracle/_build/liboracle.so with gcc (no fast-math)."""
-    src = _HERE / "newell.c"
-    if _SO.exists() and not force and _SO.stat().st_mtime >= src.stat().st_mtime:
+    """Compile the oracle's C sources into oracle/_build/liboracle.so with gcc (no fast-math)."""
+    srcs = [_HERE / s for s in _SOURCES]
+    if _SO.exists() and not force and all(_SO.stat().st_mtime >= s.stat().st_mtime for s in srcs):
         return _SO
     _BUILD.mkdir(exist_ok=True)
     tmp = _BUILD / f"liboracle.{os.getpid()}.so"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-fno-fast-math",
-           str(src), "-o", str(tmp), "-lm"]
+           *[str(s) for s in srcs], "-o", str(tmp), "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -80,6 +91,16 @@ def _load():
     lib.oracle_field_bruteforce.restype = I
     lib.oracle_field_at.argtypes = [I, I, I, P, P, I, P, P]
     lib.oracle_field_at.restype = I
+    lib.oracle_sp_rect.argtypes = [D, D, D, D, D]
+    lib.oracle_sp_rect.restype = D
+    lib.oracle_sp_kernel_closed.argtypes = [D, D, D, D, D, D, P]
+    lib.oracle_sp_kernel_quad.argtypes = [D, D, D, D, D, D, I, I, I, P]
+    lib.oracle_sp_kernel_quad.restype = I
+    lib.oracle_sp_kernel.argtypes = [D, D, D, D, D, D, P]
+    lib.oracle_sp_kernel_nodes.argtypes = [I, I, I, D, D, D, I, P]
+    lib.oracle_sp_kernel_nodes.restype = I
+    lib.oracle_sp_potential_bruteforce.argtypes = [I, I, I, D, D, D, P, P]
+    lib.oracle_sp_potential_bruteforce.restype = I
     _lib = lib
     return lib
 
@@ -304,3 +325,131 @@ def rel_errors(H: np.ndarray, Href: np.ndarray) -> dict:
         "rel_rms": float(np.linalg.norm(diff.ravel())) / nref if nref > 0 else float(np.linalg.norm(diff.ravel())),
         "paper_relerr": float(math.sqrt(float(np.sum(diff * diff)) / ncell)) if ncell else 0.0,
     }
+
+
+# ----------------------------------------------------------------- SP method
+def sp_rect(a, V, W, hv, hw) -> float:
+    """Int over [-hv, hv] x [-hw, hw] of 1 / sqrt(a^2 + (V - v)^2 + (W - w)^2) (closed form)."""
+    return float(_load().oracle_sp_rect(float(a), float(V), float(W), float(hv), float(hw)))
+
+
+def sp_kernel_closed(R, d) -> np.ndarray:
+    """S(R) of one cell of edges d by its face integrals (closed form)."""
+    out = np.zeros(3)
+    _load().oracle_sp_kernel_closed(*(float(v) for v in R), *(float(v) for v in d), _ptr(out))
+    return out
+
+
+def sp_kernel_quad(R, d, nodes=(0, 0, 0)) -> np.ndarray:
+    """S(R) by Gauss-Legendre quadrature of (R - u) / |R - u|^3 over the cell."""
+    out = np.zeros(3)
+    rc = _load().oracle_sp_kernel_quad(*(float(v) for v in R), *(float(v) for v in d),
+                                       int(nodes[0]), int(nodes[1]), int(nodes[2]), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"quadrature not applicable at {R} (rc={rc})")
+    return out
+
+
+def sp_kernel(R, d) -> np.ndarray:
+    """The oracle's S(R): closed form within 2.5 edges per axis, quadrature beyond."""
+    out = np.zeros(3)
+    _load().oracle_sp_kernel(*(float(v) for v in R), *(float(v) for v in d), _ptr(out))
+    return out
+
+
+def sp_kernel_nodes(n, d, threads: int | None = None) -> np.ndarray:
+    """(3, nz, ny, nx): entry [c, k, j, i] = S_c((i+1/2) dx, (j+1/2) dy, (k+1/2) dz)."""
+    nx, ny, nz = (int(v) for v in n)
+    out = np.zeros((3, nz, ny, nx))
+    rc = _load().oracle_sp_kernel_nodes(nx, ny, nz, float(d[0]), float(d[1]), float(d[2]),
+                                        threads or default_threads(), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"bad kernel arguments n={n} d={d}")
+    return out
+
+
+def sp_padded_size(n: int) -> int:
+    """Smallest power of two >= 2n: node-minus-cell offsets take 2n values per axis."""
+    p = 1
+    while p < 2 * n:
+        p *= 2
+    return p
+
+
+def sp_wrapped_kernel(table: np.ndarray, P) -> np.ndarray:
+    """Place the half-integer octant table at wrapped offsets of a (3, Pz, Py, Px) array.
+
+    Node i minus cell j = q in [-(n-1), n] on each axis, at distance (q - 1/2) d;
+    q >= 1 reads table index q - 1, q <= 0 reads index -q with the parity sign
+    (component a is odd along axis a). Offset q goes to index q mod P."""
+    _, nz, ny, nx = table.shape
+    n = (nx, ny, nz)
+    Px, Py, Pz = (int(v) for v in P)
+    for a, p in zip(n, (Px, Py, Pz)):
+        if p < 2 * a:
+            raise ValueError("padded size too small for the node offsets")
+    W = np.zeros((3, Pz, Py, Px))
+    t = [np.arange(a) for a in n]
+    pos = [t[a] + 1 for a in range(3)]
+    neg = [(-t[a]) % p for a, p in zip(range(3), (Px, Py, Pz))]
+    for sz in (1, -1):
+        for sy in (1, -1):
+            for sx in (1, -1):
+                px = pos[0] if sx > 0 else neg[0]
+                py = pos[1] if sy > 0 else neg[1]
+                pz = pos[2] if sz > 0 else neg[2]
+                signs = (sx, sy, sz)
+                for c in range(3):
+                    W[c][np.ix_(pz, py, px)] = signs[c] * table[c]
+    return W
+
+
+def sp_potential_fft(M: np.ndarray, d, P=None, table: np.ndarray | None = None) -> np.ndarray:
+    """Node potential phi = S * M (Eq. "scpot" with Eq. "convolution") by a
+    zero-padded float64 FFT convolution; shape (nz+1, ny+1, nx+1)."""
+    M = _check_m(M)
+    _, nz, ny, nx = M.shape
+    if P is None:
+        P = (sp_padded_size(nx), sp_padded_size(ny), sp_padded_size(nz))
+    Px, Py, Pz = (int(v) for v in P)
+    if table is None:
+        table = sp_kernel_nodes((nx, ny, nz), d)
+    W = sp_wrapped_kernel(table, (Px, Py, Pz))
+    Sh = np.fft.rfftn(W, axes=(1, 2, 3))
+    Mh = np.fft.rfftn(M, s=(Pz, Py, Px), axes=(1, 2, 3))
+    ph = Sh[0] * Mh[0] + Sh[1] * Mh[1] + Sh[2] * Mh[2]
+    phi = np.fft.irfftn(ph, s=(Pz, Py, Px), axes=(0, 1, 2))
+    return np.ascontiguousarray(phi[:nz + 1, :ny + 1, :nx + 1])
+
+
+def sp_potential_bruteforce(M: np.ndarray, d) -> np.ndarray:
+    """Node potential by the direct sum over cells, every pair evaluated on its own."""
+    M = _check_m(M)
+    _, nz, ny, nx = M.shape
+    phi = np.zeros((nz + 1, ny + 1, nx + 1))
+    rc = _load().oracle_sp_potential_bruteforce(nx, ny, nz, float(d[0]), float(d[1]), float(d[2]),
+                                                _ptr(M), _ptr(phi))
+    if rc != 0:
+        raise ValueError("SP bruteforce failed")
+    return phi
+
+
+def sp_field_from_potential(phi: np.ndarray, d) -> np.ndarray:
+    """H = -grad phi by finite differences (Eq. "field"): per cell, the average
+    over its four edges along each axis of the node differences over the edge
+    length (the cell average of -grad of the trilinear interpolant)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    nz, ny, nx = (s - 1 for s in phi.shape)
+    H = np.zeros((3, nz, ny, nx))
+    ex = (phi[:, :, 1:] - phi[:, :, :-1]) / float(d[0])        # (nz+1, ny+1, nx)
+    H[0] = -0.25 * (ex[:-1, :-1] + ex[:-1, 1:] + ex[1:, :-1] + ex[1:, 1:])
+    ey = (phi[:, 1:, :] - phi[:, :-1, :]) / float(d[1])        # (nz+1, ny, nx+1)
+    H[1] = -0.25 * (ey[:-1, :, :-1] + ey[:-1, :, 1:] + ey[1:, :, :-1] + ey[1:, :, 1:])
+    ez = (phi[1:] - phi[:-1]) / float(d[2])                    # (nz, ny+1, nx+1)
+    H[2] = -0.25 * (ez[:, :-1, :-1] + ez[:, :-1, 1:] + ez[:, 1:, :-1] + ez[:, 1:, 1:])
+    return H
+
+
+def sp_field(M: np.ndarray, d, P=None) -> np.ndarray:
+    """SP stray field: FFT node potential, then the finite-difference field."""
+    return sp_field_from_potential(sp_potential_fft(M, d, P), d)
