@@ -56,6 +56,11 @@ typedef enum {
 
 typedef enum { DEMAG_F32 = 0, DEMAG_F64 = 1 } demag_prec;
 
+/* Stray-field method of a plan (paper Sec. 3.1): the demagnetization-tensor
+ * convolution (DM) or the scalar-potential convolution with a finite-
+ * difference gradient (SP). */
+typedef enum { DEMAG_METHOD_DM = 0, DEMAG_METHOD_SP = 1 } demag_method;
+
 /* Optional plan settings; zero-initialise and set what you need. */
 typedef struct {
     /* Padded FFT lengths per axis. 0 selects the smallest power of two
@@ -74,7 +79,10 @@ typedef struct {
     int launches_per_field;  /* kernels one demag_field call launches */
     double tensor_imag_max;  /* largest |imaginary part| of the tensor spectrum
                                 after setup (exactly 0 in exact arithmetic: the
-                                wrapped tensor is even or odd per axis) */
+                                wrapped tensor is even or odd per axis; for SP
+                                plans, of the kernel tables after removing the
+                                half-cell phase) */
+    int method;              /* demag_method */
 } demag_info;
 
 /* Create a plan for an nx x ny x nz grid with cell edges dx, dy, dz.
@@ -91,6 +99,38 @@ demag_status demag_plan_create(int nx, int ny, int nz, double dx, double dy, dou
 demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, double dz,
                                   demag_prec prec, const demag_options *opt,
                                   demag_plan_t *out);
+
+/* Scalar-potential plan (paper Sec. 3.1, Eqs. "scpot", "convolution" and
+ * "field"): the potential phi = S * M of the magnetization at the grid nodes
+ * (cell corners), S(R) = (1/4pi) Int_cell grad_u (1/|R - u|) du the vector
+ * kernel of one homogeneously magnetized cell, as a zero-padded FFT
+ * convolution; then H = -grad phi per cell as the cell average of -grad of
+ * the trilinear interpolant of the 8 corner potentials,
+ *   H_x = -(1/(4 dx)) sum over the cell's 4 x-edges of phi(x+) - phi(x-)
+ * (likewise y, z). This discretisation reproduces the SP energies the paper
+ * prints for its cube and thin-film states. It costs one inverse transform
+ * instead of three; the field is an approximation of the DM field with a
+ * finite-difference error (largest at the surfaces).
+ * Padded lengths: powers of two >= 2n (node-minus-cell offsets take 2n
+ * values); opt (may be NULL) can ask for larger ones. Sizes: nx, ny <= 512,
+ * nz <= 256. Same buffers and errors as demag_plan_create_ex.
+ * Entry points that accept an SP plan: demag_tensor_setup (computes the
+ * kernel spectrum), demag_field, demag_field_energy, demag_energy,
+ * demag_field_host(_async), demag_sp_potential, demag_plan_info,
+ * demag_autotune, timing and launch counts. demag_field_adjoint and
+ * demag_energy_grad return DEMAG_ERR_UNSUPPORTED (the discrete SP operator is
+ * not self-adjoint and its adjoint is not built); batches are DM only. In
+ * FP32 the potential carries the FFT's rounding relative to its own size, and
+ * the differences divide it by one cell: the field's relative rounding error
+ * grows like the grid extent in cells (about 1e-6 x the largest n). */
+demag_status demag_plan_create_sp(int nx, int ny, int nz, double dx, double dy, double dz,
+                                  demag_prec prec, const demag_options *opt, demag_plan_t *out);
+
+/* Node potential of an SP plan: phi[nz+1][ny+1][nx+1] (device, element type
+ * of the plan, node (i, j, k) at (i dx, j dy, k dz) from the grid's corner,
+ * x fastest), phi = S * M (paper Eq. "scpot"; units of M times length). phi
+ * must not overlap M. DEMAG_ERR_INVALID_ARG for a DM plan. Asynchronous. */
+demag_status demag_sp_potential(demag_plan_t plan, const void *M, void *phi, void *stream);
 
 /* Tensor setup, once per geometry (paper Sec. 4: the convolution kernel
  * depends only on geometry and discretisation). Evaluates the six tensor

@@ -16,6 +16,9 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / "libdemag.so"
 DEMAG_F32 = 0
 DEMAG_F64 = 1
 
+DEMAG_METHOD_DM = 0
+DEMAG_METHOD_SP = 1
+
 STATUS = {
     0: "DEMAG_OK",
     1: "DEMAG_ERR_INVALID_ARG",
@@ -37,6 +40,7 @@ EXPORTS = [
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
     "demag_field_host_async", "demag_host_wait",
+    "demag_plan_create_sp", "demag_sp_potential",
 ]
 
 
@@ -59,6 +63,7 @@ class demag_info(ctypes.Structure):
         ("device_bytes", c_size_t),
         ("launches_per_field", c_int),
         ("tensor_imag_max", c_double),
+        ("method", c_int),
     ]
 
 
@@ -113,6 +118,8 @@ def load(path: str | Path | None = None):
         "demag_batch_autotune": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
         "demag_field_host_async": (S, [P, P, P, P]),
         "demag_host_wait": (S, [P]),
+        "demag_plan_create_sp": (S, [I, I, I, D, D, D, I, POINTER(demag_options), POINTER(c_void_p)]),
+        "demag_sp_potential": (S, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -148,6 +155,19 @@ def demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=
                                        int(prec), ctypes.byref(opt), ctypes.byref(h)),
            "demag_plan_create_ex")
     return h.value
+
+
+def demag_plan_create_sp(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=0):
+    h = c_void_p()
+    opt = demag_options(int(px), int(py), int(pz))
+    _check(load().demag_plan_create_sp(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                       int(prec), ctypes.byref(opt), ctypes.byref(h)),
+           "demag_plan_create_sp")
+    return h.value
+
+
+def demag_sp_potential(plan, M, phi, stream=0):
+    _check(load().demag_sp_potential(_p(plan), _p(M), _p(phi), _p(stream)), "demag_sp_potential")
 
 
 def demag_tensor_setup(plan, stream=0):

@@ -122,7 +122,7 @@ std::vector<C> twiddles(int P)
 
 // --- per-kernel timing: a ring of call slots with one event per pass edge.
 constexpr int kRing = 64;
-constexpr int kEvPerCall = 7;
+constexpr int kEvPerCall = 8;
 
 struct TimingRing {
     cudaEvent_t ev[kRing][kEvPerCall];
@@ -169,6 +169,7 @@ struct PassTimer {
 // What one pass through the pipeline reads and writes (see XIn / XOut).
 struct FieldJob {
     const void *in;       // input field [3][nz][ny][nx]
+    void *phi = nullptr;  // SP only: optional node potential [nz+1][ny+1][nx+1]
     const void *wcell;    // optional per-cell weight [nz][ny][nx]
     double wscalar;       // input = in * wscalar * wcell
     void *out;            // optional output = H * oscale * wcell * g
@@ -259,6 +260,83 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     return DEMAG_OK;
 }
 
+// Scalar-potential method (paper Sec. 3.1): x and y forward passes as for
+// the tensor method, the SP z pass to the potential spectrum (one component,
+// nz + 1 node rows, written over component 0), inverse y and x passes of that
+// one component to the node potential (nz+1)(ny+1)(nx+1), then the field by
+// finite differences (and the energy partials).
+template <typename T>
+demag_status run_field_sp(demag_plan *p, const FieldJob &job, cudaStream_t st)
+{
+    using C = typename demag::CplxOf<T>::type;
+    C *S1 = static_cast<C *>(p->S1);
+    C *S2 = static_cast<C *>(p->S2);
+    const bool f32 = p->prec == DEMAG_F32;
+    auto pick = [&](float2 *a, double2 *b) { return f32 ? (const C *)(const void *)a : (const C *)(const void *)b; };
+    const C *twx = pick(p->tw32[0], p->tw64[0]), *twy = pick(p->tw32[1], p->tw64[1]), *twz = pick(p->tw32[2], p->tw64[2]);
+    const C *phx = pick(p->ph32[0], p->ph64[0]), *phy = pick(p->ph32[1], p->ph64[1]), *phz = pick(p->ph32[2], p->ph64[2]);
+    const T *that = f32 ? (const T *)(const void *)p->nhat32 : (const T *)(const void *)p->nhat64;
+    const int nx = p->nx, ny = p->ny, nz = p->nz, Px = p->Px, Py = p->Py, Pz = p->Pz, Kx = p->Kx, Kxp = p->Kxp;
+    demag::XIn<T> xi;
+    xi.in = static_cast<const T *>(job.in);
+    xi.in_rs = nx;
+    xi.wcell = nullptr;
+    xi.wscalar = (T)1;
+    xi.rows_per_comp = nz * ny;
+    T *phi = job.phi ? static_cast<T *>(job.phi) : reinterpret_cast<T *>(S2);  // S2 is free after y inverse
+    demag::XOut<T> xo;
+    xo.out = phi;
+    xo.out_rs = nx + 1;
+    xo.scale = (T)(1.0 / ((double)Px * Py * Pz));
+    xo.oscale = (T)1;
+    xo.wcell = nullptr;
+    xo.gdev = nullptr;
+    xo.Mref = nullptr;
+    xo.mscale = (T)1;
+    xo.partials = nullptr;
+    xo.rows_per_comp = (nz + 1) * (ny + 1);
+    PassTimer tm(p, st);
+    cudaError_t e = Passes<T>::x_fwd(Px / 2, xi, 3 * nz * ny, nx, S1, Kxp, twx, st);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x forward: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    e = Passes<T>::col(Py, false, S1, S2, 3 * nz * Kx, Kx, (int64_t)ny * Kxp, Kxp, ny, (int64_t)Py * Kxp, Kxp, Py,
+                       twy, 1, st, p->yvariant);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y forward: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    e = Passes<T>::sp_zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nz + 1, that, Py,
+                            Kx, twz, phx, phy, phz, st);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("SP z pass: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    e = Passes<T>::col(Py, true, S2, S1, (nz + 1) * Kx, Kx, (int64_t)Py * Kxp, Kxp, Py, (int64_t)(ny + 1) * Kxp, Kxp,
+                       ny + 1, twy, 1, st, 0);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y inverse: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    e = Passes<T>::x_inv(Px / 2, S1, Kxp, (nz + 1) * (ny + 1), nx + 1, xo, twx, st);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x inverse: ") + cudaGetErrorString(e));
+    p->launches++;
+    tm.mark();
+    if (job.out || job.E_dev) {
+        e = Passes<T>::sp_grad(phi, nx, ny, nz, p->dx, p->dy, p->dz, static_cast<T *>(job.out),
+                               job.E_dev ? static_cast<const T *>(job.in) : nullptr,
+                               job.E_dev ? p->partials : nullptr, st);
+        if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("SP field: ") + cudaGetErrorString(e));
+        p->launches++;
+        tm.mark();
+    }
+    if (job.E_dev) {
+        const double V = p->dx * p->dy * p->dz;
+        e = demag::energy_finalize(p->partials, Passes<T>::sp_grad_blocks(nx, ny, nz), -0.5 * kMu0 * V, job.E_dev, st);
+        if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
+        p->launches++;
+        tm.mark();
+    }
+    return DEMAG_OK;
+}
+
 demag_status check_scalar_ptr(const void *ptr, const char *name)
 {
     if (((uintptr_t)ptr & 7u) != 0) return fail(DEMAG_ERR_INVALID_ARG, std::string(name) + " is not 8-byte aligned");
@@ -293,6 +371,21 @@ demag_status run_job(demag_plan *p, const FieldJob &job, void *stream)
     }
     if (job.gdev && (s = check_scalar_ptr(job.gdev, "gradient scale")) != DEMAG_OK) return s;
     if (job.E_dev && (s = check_scalar_ptr(job.E_dev, "E_dev")) != DEMAG_OK) return s;
+    if (p->method == DEMAG_METHOD_SP) {
+        if (job.wcell || job.gdev || job.wscalar != 1.0 || job.oscale != 1.0)
+            return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential plans take plain fields (no weights or scales)");
+        if (job.phi) {
+            if ((s = check_dev_ptr(p, job.phi, "phi")) != DEMAG_OK) return s;
+            const size_t pb = (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1) * elem_size(p);
+            if (overlap2(job.phi, pb, job.in, bytes) || (job.out && overlap2(job.phi, pb, job.out, bytes)))
+                return fail(DEMAG_ERR_INVALID_ARG, "phi overlaps the input or the output");
+        }
+        if (!job.out && !job.E_dev && !job.phi)
+            return fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no output, no energy)");
+        cudaStream_t st = (cudaStream_t)stream;
+        if (p->prec == DEMAG_F32) return run_field_sp<float>(p, job, st);
+        return run_field_sp<double>(p, job, st);
+    }
     if (!job.out && !job.E_dev) return fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no output, no energy)");
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prec == DEMAG_F32) return run_field<float>(p, job, st);
@@ -315,8 +408,8 @@ std::string tune_key(const demag_plan *p)
     for (auto &c : name)
         if (c == ' ') c = '_';
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%s|%dx%dx%d|%dx%dx%d", name.c_str(), p->prec == DEMAG_F32 ? "f32" : "f64", p->Px,
-             p->Py, p->Pz, p->nx, p->ny, p->nz);
+    snprintf(buf, sizeof buf, "%s|%s|%dx%dx%d|%dx%dx%d%s", name.c_str(), p->prec == DEMAG_F32 ? "f32" : "f64", p->Px,
+             p->Py, p->Pz, p->nx, p->ny, p->nz, p->method == DEMAG_METHOD_SP ? "|sp" : "");
     return buf;
 }
 
@@ -357,6 +450,100 @@ FieldJob plain_job(const void *M, void *H, double *E_dev)
     return j;
 }
 
+constexpr int kMaxSPZ = 256;  // the SP z pass is built for padded z lengths <= 512
+
+// SP padding: node-minus-cell offsets take 2n values per axis.
+int sp_pad(int n)
+{
+    int p = 2;
+    while (p < 2 * n) p *= 2;
+    return p;
+}
+
+// Allocates a plan with padded lengths P for the given method (no launches).
+demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec, const int P[3],
+                         int method, demag_plan_t *out)
+{
+    demag_plan *p = new demag_plan;
+    memset(p, 0, sizeof(*p));
+    p->method = method;
+    p->nx = nx; p->ny = ny; p->nz = nz;
+    p->dx = dx; p->dy = dy; p->dz = dz;
+    p->prec = prec;
+    p->Px = P[0]; p->Py = P[1]; p->Pz = P[2];
+    p->Kx = P[0] == 1 ? 1 : P[0] / 2 + 1;
+    p->Kxp = P[0] == 1 ? 1 : (p->Kx + 1) / 2 * 2;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(DEMAG_ERR_CUDA, "no CUDA device");
+    }
+    const size_t cs = prec == DEMAG_F32 ? sizeof(float2) : sizeof(double2);
+    const bool sp = method == DEMAG_METHOD_SP;
+    // SP: the inverse y pass writes (nz+1)(ny+1) rows of one component into S1
+    const size_t s1 = std::max((size_t)3 * nz * ny, sp ? (size_t)(nz + 1) * (ny + 1) : (size_t)0) * p->Kxp * cs;
+    const int ntab = sp ? 3 : 6;
+    const size_t s2 = (size_t)3 * nz * p->Py * p->Kxp * cs;
+    const size_t plane = (size_t)(p->Pz / 2 + 1) * (p->Py / 2 + 1) * p->Kx;
+    const int rows = 3 * nz * ny;
+    p->npartials = p->Px == 1 ? std::max(1, std::min(4096, (rows + 255) / 256))
+                              : (prec == DEMAG_F32 ? Passes<float>::x_blocks(p->Px / 2, rows)
+                                                   : Passes<double>::x_blocks(p->Px / 2, rows));
+    if (sp) p->npartials = Passes<float>::sp_grad_blocks(nx, ny, nz);
+    auto cleanup_fail = [&](cudaError_t e, const char *what) {
+        demag_plan_destroy(p);
+        return fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->S1, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S1");
+    if (p->Py > 1) {
+        if ((e = cudaMalloc(&p->S2, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S2");
+    } else {
+        p->S2 = p->S1;
+    }
+    if (prec == DEMAG_F32) {
+        if ((e = cudaMalloc(&p->nhat32, ntab * plane * sizeof(float))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
+    } else {
+        if ((e = cudaMalloc(&p->nhat64, ntab * plane * sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
+    }
+    if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc partials");
+    if ((e = cudaMalloc(&p->e_dev, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc energy");
+    for (int a = 0; a < 3; ++a) {
+        const auto t64 = twiddles<double2>(P[a]);
+        if ((e = cudaMalloc(&p->tw64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
+        if ((e = cudaMemcpy(p->tw64[a], t64.data(), sizeof(double2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cleanup_fail(e, "twiddle upload");
+        if (prec == DEMAG_F32) {
+            const auto t32 = twiddles<float2>(P[a]);
+            if ((e = cudaMalloc(&p->tw32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
+            if ((e = cudaMemcpy(p->tw32[a], t32.data(), sizeof(float2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cleanup_fail(e, "twiddle upload");
+        }
+        if (sp) {  // exp(-pi i k / P): the half-cell shift of the node offsets
+            const auto h64 = twiddles<double2>(2 * P[a]);
+            if ((e = cudaMalloc(&p->ph64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc phases");
+            if ((e = cudaMemcpy(p->ph64[a], h64.data(), sizeof(double2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cleanup_fail(e, "phase upload");
+            if (prec == DEMAG_F32) {
+                const auto h32 = twiddles<float2>(2 * P[a]);
+                if ((e = cudaMalloc(&p->ph32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc phases");
+                if ((e = cudaMemcpy(p->ph32[a], h32.data(), sizeof(float2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
+                    return cleanup_fail(e, "phase upload");
+            }
+        }
+    }
+    if ((e = cudaMemset(p->S1, 0, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+    if (p->S2 != p->S1 && (e = cudaMemset(p->S2, 0, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+    p->device_bytes = s1 + (p->S2 != p->S1 ? s2 : 0) + ntab * plane * (prec == DEMAG_F32 ? 4 : 8) +
+                      sizeof(double) * (p->npartials + 1) +
+                      (size_t)(P[0] + P[1] + P[2]) * (sizeof(double2) + (prec == DEMAG_F32 ? sizeof(float2) : 0)) *
+                          (sp ? 2 : 1);
+    *out = p;
+    g_err.clear();
+    return DEMAG_OK;
+}
+
 }  // namespace
 
 void demag::set_last_error(const std::string &msg) { g_err = msg; }
@@ -387,7 +574,10 @@ void demag_plan_destroy(demag_plan_t p)
     cudaFree(p->S1);
     cudaFree(p->nhat32);
     cudaFree(p->nhat64);
-    for (int a = 0; a < 3; ++a) { cudaFree(p->tw64[a]); cudaFree(p->tw32[a]); }
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(p->tw64[a]); cudaFree(p->tw32[a]);
+        cudaFree(p->ph64[a]); cudaFree(p->ph32[a]);
+    }
     cudaFree(p->partials);
     cudaFree(p->e_dev);
     cudaFree(p->dM);
@@ -437,72 +627,102 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
             P[a] = req[a];
         }
     }
-    demag_plan *p = new demag_plan;
-    memset(p, 0, sizeof(*p));
-    p->nx = nx; p->ny = ny; p->nz = nz;
-    p->dx = dx; p->dy = dy; p->dz = dz;
-    p->prec = prec;
-    p->Px = P[0]; p->Py = P[1]; p->Pz = P[2];
-    p->Kx = P[0] == 1 ? 1 : P[0] / 2 + 1;
-    p->Kxp = P[0] == 1 ? 1 : (p->Kx + 1) / 2 * 2;
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
-        cudaGetLastError();
-        delete p;
-        return fail(DEMAG_ERR_CUDA, "no CUDA device");
-    }
-    const size_t cs = prec == DEMAG_F32 ? sizeof(float2) : sizeof(double2);
-    const size_t s1 = (size_t)3 * nz * ny * p->Kxp * cs;
-    const size_t s2 = (size_t)3 * nz * p->Py * p->Kxp * cs;
-    const size_t plane = (size_t)(p->Pz / 2 + 1) * (p->Py / 2 + 1) * p->Kx;
-    const int rows = 3 * nz * ny;
-    p->npartials = p->Px == 1 ? std::max(1, std::min(4096, (rows + 255) / 256))
-                              : (prec == DEMAG_F32 ? Passes<float>::x_blocks(p->Px / 2, rows)
-                                                   : Passes<double>::x_blocks(p->Px / 2, rows));
-    auto cleanup_fail = [&](cudaError_t e, const char *what) {
-        demag_plan_destroy(p);
-        return fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
-                    std::string(what) + ": " + cudaGetErrorString(e));
-    };
-    cudaError_t e;
-    if ((e = cudaMalloc(&p->S1, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S1");
-    if (p->Py > 1) {
-        if ((e = cudaMalloc(&p->S2, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S2");
-    } else {
-        p->S2 = p->S1;
-    }
-    if (prec == DEMAG_F32) {
-        if ((e = cudaMalloc(&p->nhat32, 6 * plane * sizeof(float))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
-    } else {
-        if ((e = cudaMalloc(&p->nhat64, 6 * plane * sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
-    }
-    if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc partials");
-    if ((e = cudaMalloc(&p->e_dev, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc energy");
-    for (int a = 0; a < 3; ++a) {
-        const auto t64 = twiddles<double2>(P[a]);
-        if ((e = cudaMalloc(&p->tw64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
-        if ((e = cudaMemcpy(p->tw64[a], t64.data(), sizeof(double2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
-            return cleanup_fail(e, "twiddle upload");
-        if (prec == DEMAG_F32) {
-            const auto t32 = twiddles<float2>(P[a]);
-            if ((e = cudaMalloc(&p->tw32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
-            if ((e = cudaMemcpy(p->tw32[a], t32.data(), sizeof(float2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
-                return cleanup_fail(e, "twiddle upload");
+    return create_plan(nx, ny, nz, dx, dy, dz, prec, P, DEMAG_METHOD_DM, out);
+}
+
+demag_status demag_plan_create_sp(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
+                                  const demag_options *opt, demag_plan_t *out)
+{
+    if (!out) return fail(DEMAG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DEMAG_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz))
+        return fail(DEMAG_ERR_INVALID_ARG, "cell edges must be positive and finite");
+    if (prec != DEMAG_F32 && prec != DEMAG_F64) return fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
+    if (nx > kMaxN || ny > kMaxN || nz > kMaxSPZ)
+        return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential grids are built up to 512 x 512 x 256");
+    int P[3] = {sp_pad(nx), sp_pad(ny), sp_pad(nz)};
+    const int n[3] = {nx, ny, nz};
+    if (opt) {
+        const int req[3] = {opt->px, opt->py, opt->pz};
+        for (int a = 0; a < 3; ++a) {
+            if (req[a] == 0) continue;
+            if (!is_pow2(req[a]) || req[a] < 2 * n[a])
+                return fail(DEMAG_ERR_INVALID_ARG, "scalar-potential padded lengths must be powers of two >= 2n");
+            if (req[a] > (a == 2 ? 2 * kMaxSPZ : kMaxP))
+                return fail(DEMAG_ERR_UNSUPPORTED, "padded length above what is built");
+            P[a] = req[a];
         }
     }
-    if ((e = cudaMemset(p->S1, 0, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
-    if (p->S2 != p->S1 && (e = cudaMemset(p->S2, 0, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
-    p->device_bytes = s1 + (p->S2 != p->S1 ? s2 : 0) + 6 * plane * (prec == DEMAG_F32 ? 4 : 8) +
-                      sizeof(double) * (p->npartials + 1) +
-                      (size_t)(P[0] + P[1] + P[2]) * (sizeof(double2) + (prec == DEMAG_F32 ? sizeof(float2) : 0));
-    *out = p;
-    g_err.clear();
-    return DEMAG_OK;
+    return create_plan(nx, ny, nz, dx, dy, dz, prec, P, DEMAG_METHOD_SP, out);
 }
 
 demag_status demag_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
                                demag_plan_t *out)
 {
     return demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec, nullptr, out);
+}
+
+// Kernel setup of the scalar-potential method: the cell kernel S at the
+// half-integer node offsets (FP64), per component wrapped onto the padded
+// grid, transformed, and reduced to the real table T_j (phase removed).
+demag_status sp_setup(demag_plan *p, cudaStream_t st)
+{
+    const int nx = p->nx, ny = p->ny, nz = p->nz, Px = p->Px, Py = p->Py, Pz = p->Pz, Kx = p->Kx, Kxp = p->Kxp;
+    const size_t plane = (size_t)(Pz / 2 + 1) * (Py / 2 + 1) * Kx;
+    double *oct = nullptr, *W = nullptr, *t64 = p->nhat64;
+    double2 *St = nullptr;
+    unsigned long long *imag = nullptr;
+    bool own64 = false;
+    demag_status rs = DEMAG_OK;
+    auto done = [&](demag_status s) {
+        cudaFree(oct); cudaFree(W); cudaFree(St); cudaFree(imag);
+        if (own64) cudaFree(t64);
+        return s;
+    };
+#define SETUP_CUDA(call)                                                                       \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            rs = fail(e_ == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,        \
+                      std::string("SP kernel setup: ") + #call + ": " + cudaGetErrorString(e_)); \
+            return done(rs);                                                                   \
+        }                                                                                      \
+    } while (0)
+    SETUP_CUDA(cudaMalloc(&oct, sizeof(double) * 3 * (size_t)nx * ny * nz));
+    SETUP_CUDA(cudaMalloc(&W, sizeof(double) * (size_t)Px * Py * Pz));
+    SETUP_CUDA(cudaMalloc(&St, sizeof(double2) * (size_t)Pz * Py * Kxp));
+    SETUP_CUDA(cudaMalloc(&imag, sizeof(unsigned long long)));
+    SETUP_CUDA(cudaMemsetAsync(imag, 0, sizeof(unsigned long long), st));
+    if (!t64) {
+        SETUP_CUDA(cudaMalloc(&t64, sizeof(double) * 3 * plane));
+        own64 = true;
+    }
+    SETUP_CUDA(demag::sp_octant(oct, nx, ny, nz, p->dx, p->dy, p->dz, st));
+    demag::XIn<double> xin;
+    xin.in = W;
+    xin.in_rs = Px;
+    xin.wcell = nullptr;
+    xin.wscalar = 1.0;
+    xin.rows_per_comp = Pz * Py;
+    for (int c = 0; c < 3; ++c) {
+        SETUP_CUDA(demag::sp_wrap(oct, c, nx, ny, nz, Px, Py, Pz, W, st));
+        SETUP_CUDA(Passes<double>::x_fwd(Px / 2, xin, Pz * Py, Px, St, Kxp, p->tw64[0], st));
+        SETUP_CUDA(Passes<double>::col(Py, false, St, St, Pz * Kx, Kx, (int64_t)Py * Kxp, Kxp, Py, (int64_t)Py * Kxp,
+                                       Kxp, Py, p->tw64[1], 1, st));
+        SETUP_CUDA(Passes<double>::col(Pz, false, St, St, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, Pz, Kxp,
+                                       (int64_t)Py * Kxp, Pz, p->tw64[2], 1, st));
+        SETUP_CUDA(demag::sp_extract(St, c, Px, Py, Pz, Kxp, t64, p->nhat32, imag, st));
+    }
+    unsigned long long bits = 0;
+    SETUP_CUDA(cudaMemcpyAsync(&bits, imag, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    SETUP_CUDA(cudaStreamSynchronize(st));
+    memcpy(&p->imag_max, &bits, sizeof(double));
+    p->launches += 1 + 3 * 5;
+    p->setup_done = true;
+    g_err.clear();
+    return done(DEMAG_OK);
+#undef SETUP_CUDA
 }
 
 demag_status demag_tensor_setup(demag_plan_t p, void *stream)
@@ -512,6 +732,7 @@ demag_status demag_tensor_setup(demag_plan_t p, void *stream)
     DeviceGuard g(p->device);
     if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->method == DEMAG_METHOD_SP) return sp_setup(p, st);
     const int nx = p->nx, ny = p->ny, nz = p->nz, Px = p->Px, Py = p->Py, Pz = p->Pz, Kx = p->Kx, Kxp = p->Kxp;
     const size_t plane = (size_t)(Pz / 2 + 1) * (Py / 2 + 1) * Kx;
     double *oct = nullptr, *W = nullptr, *nh64 = p->nhat64;
@@ -572,6 +793,16 @@ demag_status demag_tensor_setup(demag_plan_t p, void *stream)
 #undef SETUP_CUDA
 }
 
+demag_status demag_sp_potential(demag_plan_t p, const void *M, void *phi, void *stream)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (p->method != DEMAG_METHOD_SP) return fail(DEMAG_ERR_INVALID_ARG, "not a scalar-potential plan");
+    if (!phi) return fail(DEMAG_ERR_INVALID_ARG, "phi is NULL");
+    FieldJob j = plain_job(M, nullptr, nullptr);
+    j.phi = phi;
+    return run_job(p, j, stream);
+}
+
 demag_status demag_field(demag_plan_t p, const void *M, void *H, void *stream)
 {
     if (!H) return fail(DEMAG_ERR_INVALID_ARG, "H is NULL");
@@ -582,6 +813,8 @@ demag_status demag_field_adjoint(demag_plan_t p, const void *G, void *out, void 
 {
     // N_ij = N_ji and N(-r) = N(r): the operator equals its adjoint.
     if (!out) return fail(DEMAG_ERR_INVALID_ARG, "out is NULL");
+    if (p && p->method == DEMAG_METHOD_SP)
+        return fail(DEMAG_ERR_UNSUPPORTED, "the scalar-potential operator is not self-adjoint; its adjoint is not built");
     return run_job(p, plain_job(G, out, nullptr), stream);
 }
 
@@ -628,6 +861,8 @@ demag_status demag_energy_grad(demag_plan_t p, const void *m, const void *w, dou
                                void *grad, const double *gscale_dev, void *stream)
 {
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (p->method == DEMAG_METHOD_SP)
+        return fail(DEMAG_ERR_UNSUPPORTED, "energy gradients need the adjoint, which scalar-potential plans do not build");
     if (!isfinite(Ms)) return fail(DEMAG_ERR_INVALID_ARG, "Ms must be finite");
     FieldJob j;
     j.in = m; j.wcell = w; j.wscalar = Ms;
@@ -697,8 +932,9 @@ demag_status demag_plan_info(demag_plan_t p, demag_info *info)
     info->kx = p->Kx;
     info->prec = p->prec;
     info->device_bytes = p->device_bytes;
-    info->launches_per_field = 3 + 2 * (p->Py > 1);
+    info->launches_per_field = p->method == DEMAG_METHOD_SP ? 6 : 3 + 2 * (p->Py > 1);
     info->tensor_imag_max = p->imag_max;
+    info->method = p->method;
     return DEMAG_OK;
 }
 
@@ -757,9 +993,10 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     // candidates: z-pass tile width where the two-stage z kernel runs, y-pass
     // radix order where the two radices differ
     std::vector<int> zs = {0}, ys = {0};
-    if (p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
-    if (p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
-    if (p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
+    const bool dm = p->method == DEMAG_METHOD_DM;  // the SP z pass has one form
+    if (dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
+    if (dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
+    if (dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
     if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
     if (p->Py == 512 || p->Py == 1024) ys.push_back(2);  // three-stage, more CTAs per SM
     const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);

@@ -835,7 +835,7 @@ k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ o
 }
 
 // Complex-to-real along x (see k_x_inv), two stages, XOut epilogue.
-template <typename T, int L, bool CG>
+template <typename T, int L, bool CG, bool P1 = false>
 __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
 {
@@ -878,12 +878,13 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
 #pragma unroll
         for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
-        RegDFTHalfOut<R2, true, C>::run(v);
+        if constexpr (P1) RegDFTHalfOutP1<R2, true, C>::run(v);
+        else RegDFTHalfOut<R2, true, C>::run(v);
         if (row < nrows) {
             const T g = o.gdev ? (T)(*o.gdev) : (T)1;
             const T oscale = o.oscale * g;
 #pragma unroll
-            for (int r = 0; r < R2 / 2; ++r) {  // z[n], n = j2 + r R1 < L/2
+            for (int r = 0; r < (P1 ? R2 / 2 + 1 : R2 / 2); ++r) {  // z[n], n = j2 + r R1 (< L/2 unless P1)
                 const int n = j2 + r * R1;
                 const T hv[2] = {v[r].x * o.scale, v[r].y * o.scale};
 #pragma unroll
@@ -901,13 +902,15 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
     if (o.partials) block_partial<NT>((double)acc, o.partials, tile);
 }
 
-template <typename T, int L>
+// P1: one more output pair per row (x = L, L + 1, ...: rows of nx + 1 >= L
+// values, the node potential of the scalar-potential method).
+template <typename T, int L, bool P1 = false>
 __global__ void __launch_bounds__(Tile2<T>::NT, (L >= 512 ? Occ<T, 2 * L>::MIN_CTAS : Occ<T, L>::MIN_CTAS))
 k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    k_x_inv2_tile<T, L, false>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
+    k_x_inv2_tile<T, L, false, P1>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
 }
 
 }  // namespace demag

@@ -140,6 +140,22 @@ template <bool INV, typename C> struct RegDFTHalfOut<1, INV, C> {
     static __device__ __forceinline__ void run(C *) {}
 };
 
+// DFT of N points of which the outputs v[0..N/2] are used: one output more
+// than RegDFTHalfOut, v[N/2] = E[0] - O[0].
+template <int N, bool INV, typename C> struct RegDFTHalfOutP1 {
+    static __device__ __forceinline__ void run(C *v)
+    {
+        C e[N / 2], o[N / 2];
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+        RegDFT<N / 2, INV, C>::run(e);
+        RegDFT<N / 2, INV, C>::run(o);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) v[k] = cadd(e[k], twconst<N, INV>(k, o[k]));
+        v[N / 2] = csub(e[0], o[0]);
+    }
+};
+
 __device__ __forceinline__ int sw(int e) { return e + (e >> 5); }
 
 __host__ __device__ constexpr int swsize(int elems) { return elems + (elems >> 5) + 1; }

@@ -5,6 +5,7 @@
 #include "fft2.cuh"
 #include "fft_engine.cuh"
 #include "plan.h"
+#include "sp.cuh"
 
 namespace demag {
 
@@ -131,7 +132,9 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
         using S = XShape<T, LL>;                                                               \
         const size_t sm = (size_t)S::TR * S::RS * sizeof(C);                                   \
         const int grid = (nrows + S::TR - 1) / S::TR;                                          \
-        k_x_inv2<T, LL><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx);             \
+        if (nvalid <= LL) k_x_inv2<T, LL><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx); \
+        else if (nvalid == LL + 1) k_x_inv2<T, LL, true><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx); \
+        else return cudaErrorInvalidValue;                                                     \
         return cudaGetLastError();                                                             \
     }
         switch (L) { DEMAG_CASE2(64) DEMAG_CASE2(128) DEMAG_CASE2(256) DEMAG_CASE2(512) default: return cudaErrorInvalidValue; }
@@ -301,6 +304,75 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
                             : zconv_launch<LL, 0>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
     switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE
+}
+
+template <typename T>
+cudaError_t Passes<T>::sp_zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                int nout, const T *that, int Py, int Kx, const C *tw, const C *phx, const C *phy,
+                                const C *phz, cudaStream_t st)
+{
+    if (ncols <= 0) return cudaSuccess;
+    // zero padding: nz + 1 node rows out of L >= 2 nz
+    if (L < 2 || 2 * nrows > L || nout != nrows + 1 || cs != (int64_t)nrows * rs) return cudaErrorInvalidValue;
+    if (L <= 16) {
+        const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
+#define DEMAG_CASE(LL)                                                                         \
+    case LL:                                                                                   \
+        k_sp_z1<T, LL><<<grid, Tile2<T>::NT, 0, st>>>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, phx, phy, phz); \
+        return cudaGetLastError();
+        switch (L) { DEMAG_CASE(2) DEMAG_CASE(4) DEMAG_CASE(8) DEMAG_CASE(16) default: return cudaErrorInvalidValue; }
+#undef DEMAG_CASE
+    }
+#define DEMAG_CASE(LL)                                                                         \
+    case LL: {                                                                                 \
+        using Sh = ZShape<T, LL, 0>;                                                           \
+        const size_t sm = 3 * swsize(LL * Sh::TC) * sizeof(C) + (LL / 2 + 1) * 3 * Sh::TC * sizeof(T); \
+        const int grid = (ncols + Sh::TC - 1) / Sh::TC;                                        \
+        cudaError_t e;                                                                         \
+        if (2 * nout <= LL) {                                                                  \
+            if ((e = allow_smem<k_sp_z2<T, LL, true>>(sm)) != cudaSuccess) return e;           \
+            k_sp_z2<T, LL, true><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz); \
+        } else {                                                                               \
+            if ((e = allow_smem<k_sp_z2<T, LL, false>>(sm)) != cudaSuccess) return e;          \
+            k_sp_z2<T, LL, false><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz); \
+        }                                                                                      \
+        return cudaGetLastError();                                                             \
+    }
+    switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorInvalidValue; }
+#undef DEMAG_CASE
+}
+
+namespace {
+// Cell layers per block of the field stencil: enough blocks to fill the GPU
+// a few times over, each marching over a contiguous run of layers.
+int sp_zchunk(int nx, int ny, int nz)
+{
+    const int64_t xy = (int64_t)((nx + 31) / 32) * ((ny + 7) / 8);
+    const int64_t want = 8 * (int64_t)sm_count();
+    int chunk = (int)((xy * nz + want - 1) / want);
+    if (chunk < 1) chunk = 1;
+    if (chunk > 16) chunk = 16;
+    if (chunk > nz) chunk = nz;
+    return chunk;
+}
+}  // namespace
+
+template <typename T>
+int Passes<T>::sp_grad_blocks(int nx, int ny, int nz)
+{
+    const int chunk = sp_zchunk(nx, ny, nz);
+    return ((nx + 31) / 32) * ((ny + 7) / 8) * ((nz + chunk - 1) / chunk);
+}
+
+template <typename T>
+cudaError_t Passes<T>::sp_grad(const T *phi, int nx, int ny, int nz, double dx, double dy, double dz, T *H,
+                               const T *Mref, double *partials, cudaStream_t st)
+{
+    const int chunk = sp_zchunk(nx, ny, nz);
+    const dim3 grid((nx + 31) / 32, (ny + 7) / 8, (nz + chunk - 1) / chunk);
+    k_sp_grad<T><<<grid, dim3(32, 8), 0, st>>>(phi, nx, ny, nz, chunk, (T)(0.25 / dx), (T)(0.25 / dy),
+                                               (T)(0.25 / dz), H, Mref, (T)1, partials);
+    return cudaGetLastError();
 }
 
 template <typename T>

@@ -73,6 +73,14 @@ template <typename T> struct Passes {
     // Px == 1: rows of one value; same prologue / epilogue as above
     static cudaError_t x1_fwd(const XIn<T> &a, int64_t n, C *out, cudaStream_t st);
     static cudaError_t x1_inv(const C *in, int64_t n, const XOut<T> &o, int nblocks, cudaStream_t st);
+    // scalar-potential method: fused z pass (three spectra in, the potential
+    // spectrum out, nout = nz + 1 node rows) and the finite-difference field
+    static cudaError_t sp_zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+                                int nrows, int nout, const T *that, int Py, int Kx, const C *tw,
+                                const C *phx, const C *phy, const C *phz, cudaStream_t st);
+    static cudaError_t sp_grad(const T *phi, int nx, int ny, int nz, double dx, double dy, double dz, T *H,
+                               const T *Mref, double *partials, cudaStream_t st);
+    static int sp_grad_blocks(int nx, int ny, int nz);
 };
 
 // One state of a batch, as the persistent batch kernel sees it (device
@@ -116,10 +124,20 @@ void set_last_error(const std::string &msg);
 cudaError_t energy_finalize(const double *partials, int n, double factor, double *E,
                             cudaStream_t st);
 
+// Scalar-potential kernel setup (tensor.cu): octant of the cell kernel S at
+// half-integer offsets [3][nz][ny][nx], its wrapped node grid, and the real
+// tables T_j of its spectrum (phase exp(-pi i sum k/P) removed).
+cudaError_t sp_octant(double *out, int nx, int ny, int nz, double dx, double dy, double dz, cudaStream_t st);
+cudaError_t sp_wrap(const double *oct, int comp, int nx, int ny, int nz, int Px, int Py, int Pz, double *out,
+                    cudaStream_t st);
+cudaError_t sp_extract(const double2 *S, int comp, int Px, int Py, int Pz, int Kxp, double *t64, float *t32,
+                       unsigned long long *imag_max, cudaStream_t st);
+
 }  // namespace demag
 
 // The opaque plan.
 struct demag_plan {
+    int method;  // demag_method: DM (tensor) or SP (scalar potential)
     int nx, ny, nz;
     double dx, dy, dz;
     demag_prec prec;
@@ -128,9 +146,12 @@ struct demag_plan {
     size_t device_bytes;
     // spectra: S1 [3][nz][ny][Kxp], S2 [3][nz][Py][Kxp] (S2 == S1 when Py == 1)
     void *S1, *S2;
-    // tensor spectrum [6][Pz/2+1][Py/2+1][Kx]
+    // tensor spectrum [6][Pz/2+1][Py/2+1][Kx] (SP: kernel tables [3][...])
     double *nhat64;
     float *nhat32;
+    // SP: half-sample phase factors exp(-pi i k / P) per axis, k < P
+    double2 *ph64[3];
+    float2 *ph32[3];
     // forward twiddle tables W_P^m, m < P, per axis
     double2 *tw64[3];
     float2 *tw32[3];

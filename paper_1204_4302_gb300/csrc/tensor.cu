@@ -205,11 +205,11 @@ __device__ __forceinline__ int tidx(int b1, int b2, int b3)
     return n * (n + 1) * (n + 2) / 6 + b1 * (n + 1) - b1 * (b1 - 1) / 2 + b2;
 }
 
-__device__ void far_multipole(double X, double Y, double Z, double a, double b, double c, double *out)
+// Taylor coefficients t_beta = (1/beta!) d^beta_y 1/|R - y| at y = 0 for all
+// multi-indices of order <= kTaylor (index tidx), by the three-term
+// recurrence n R^2 t_beta = (2n-1) sum_a R_a t_{beta-e_a} - (n-1) sum_a t_{beta-2e_a}.
+__device__ void taylor_inv_r(double X, double Y, double Z, double *t)
 {
-    // Taylor coefficients t_beta = (1/beta!) d^beta_y 1/|R - y| at y = 0, which
-    // equal (1/beta!) d^beta (1/|R|) for even |beta| (the only ones used).
-    double t[kNumTaylor];
     const double R2 = X * X + Y * Y + Z * Z;
     const double Rv[3] = {X, Y, Z};
     t[0] = rsqrt(R2);
@@ -235,6 +235,13 @@ __device__ void far_multipole(double X, double Y, double Z, double a, double b, 
                 t[tidx(b1, b2, b3)] = s * inv;
             }
     }
+}
+
+__device__ void far_multipole(double X, double Y, double Z, double a, double b, double c, double *out)
+{
+    // t_beta equal (1/beta!) d^beta (1/|R|) for even |beta| (the only ones used).
+    double t[kNumTaylor];
+    taylor_inv_r(X, Y, Z, t);
     // per-axis moment factors m_k(d) = mu_{2k}(d) / (2k)! = 2 d^{2k} / (2k+2)!
     double fact[kTaylor + 1];
     fact[0] = 1.0;
@@ -351,6 +358,202 @@ __global__ void k_energy_finalize(const double *__restrict__ partials, int n, do
     if (threadIdx.x == 0) *E = factor * (ss[0] + sc[0]);
 }
 
+// ------------------------------------------------------------------ SP kernel
+// Vector kernel of the scalar-potential method (paper Sec. 3.1, Eq. "scpot"):
+// the potential at R of a cell of edges (a, b, c) centred at 0 with unit
+// magnetization along j,
+//   S_j(R) = (1/4pi) Int_cell d/du_j (1/|R - u|) du
+//          = (1/4pi) (Int over the face u_j = +d_j/2 - over u_j = -d_j/2) dA / |R - u|.
+// Offsets are node-minus-cell-centre, (i + 1/2, j + 1/2, k + 1/2) edges in
+// the stored octant. Lengths scaled by the longest edge (S scales like a
+// length). Three regimes:
+//   near (|X| <= 2.5a, |Y| <= 2.5b, |Z| <= 2.5c): closed form of each face
+//        integral, a signed corner sum of F(p, v, w) = v ln(w + r) +
+//        w ln(v + r) - p atan(v w / (p r)), r = |(p, v, w)| (d^2F/dv dw = 1/r);
+//   mid: Gauss-Legendre quadrature of (R - u)_j / |R - u|^3 over the cell,
+//        nodes per axis from the Bernstein ellipse through the nearest
+//        singularity of the integrand (R_a + i rho, rho >= the distance of R
+//        from the cell in the other two axes);
+//   far (|R| >= 20 max d): multipole expansion of the cell's Newtonian
+//        potential, S_j = (1/4pi) sum_beta mu_beta (beta_j + 1) t_{beta + e_j}
+//        over even beta of order <= 10, mu_beta = V prod_a h_a^beta_a /
+//        (beta_a + 1), h = d/2.
+
+// ln(w + r), r = sqrt(q2 + w^2): the form without cancellation for w < 0.
+__device__ __forceinline__ double sp_lnwr(double w, double r, double q2)
+{
+    return w >= 0.0 ? log(w + r) : log(q2 / (r - w));
+}
+
+__device__ double sp_F(double p, double v, double w)
+{
+    const double pp = p * p, vv = v * v, ww = w * w;
+    const double r = sqrt(pp + vv + ww);
+    if (r == 0.0) return 0.0;
+    double s = 0.0;
+    if (v != 0.0) s += v * sp_lnwr(w, r, pp + vv);
+    if (w != 0.0) s += w * sp_lnwr(v, r, pp + ww);
+    if (p != 0.0) s -= p * atan(v * w / (p * r));
+    return s;
+}
+
+// Integral of 1/|(p, V - v, W - w)| over v in [-hv, hv], w in [-hw, hw].
+__device__ double sp_face(double p, double V, double W, double hv, double hw)
+{
+    return (sp_F(p, V + hv, W + hw) - sp_F(p, V - hv, W + hw)) - (sp_F(p, V + hv, W - hw) - sp_F(p, V - hv, W - hw));
+}
+
+__device__ void sp_near(double X, double Y, double Z, double a, double b, double c, double *out)
+{
+    const double k = 1.0 / (4.0 * 3.14159265358979323846);
+    out[0] = k * (sp_face(X - 0.5 * a, Y, Z, 0.5 * b, 0.5 * c) - sp_face(X + 0.5 * a, Y, Z, 0.5 * b, 0.5 * c));
+    out[1] = k * (sp_face(Y - 0.5 * b, Z, X, 0.5 * c, 0.5 * a) - sp_face(Y + 0.5 * b, Z, X, 0.5 * c, 0.5 * a));
+    out[2] = k * (sp_face(Z - 0.5 * c, X, Y, 0.5 * a, 0.5 * b) - sp_face(Z + 0.5 * c, X, Y, 0.5 * a, 0.5 * b));
+}
+
+// GL node count on [-h, h] for a singularity at Ra + i rho: the ellipse with
+// foci -+h through it has semi-major axis s h, s = (|z - 1| + |z + 1|) / 2,
+// z = (Ra + i rho)/h, and parameter s + sqrt(s^2 - 1).
+__device__ int sp_axis_nodes(double Ra, double rho, double h)
+{
+    const double x = Ra / h, y = rho / h;
+    const double s = 0.5 * (sqrt((x - 1.0) * (x - 1.0) + y * y) + sqrt((x + 1.0) * (x + 1.0) + y * y));
+    const double e = s + sqrt(fmax(s * s - 1.0, 0.0));
+    const int n = e > 1.0 ? (int)ceil(17.0 / log(e)) : kMaxGL;
+    return n < 2 ? 2 : (n > kMaxGL ? kMaxGL : n);
+}
+
+__device__ void sp_mid(double X, double Y, double Z, double a, double b, double c, double *out)
+{
+    const double R[3] = {X, Y, Z}, h[3] = {0.5 * a, 0.5 * b, 0.5 * c};
+    double g[3];
+    for (int q = 0; q < 3; ++q) g[q] = fmax(0.0, fabs(R[q]) - h[q]);
+    int n[3];
+    for (int q = 0; q < 3; ++q) {
+        const double g1 = g[(q + 1) % 3], g2 = g[(q + 2) % 3];
+        n[q] = sp_axis_nodes(fabs(R[q]), sqrt(g1 * g1 + g2 * g2), h[q]);
+    }
+    const int bx = n[0] * (n[0] - 1) / 2, by = n[1] * (n[1] - 1) / 2, bz = n[2] * (n[2] - 1) / 2;
+    double s[3] = {0, 0, 0};
+    for (int k = 0; k < n[2]; ++k) {
+        const double rz = Z - h[2] * c_glx[bz + k], wz = h[2] * c_glw[bz + k];
+        for (int j = 0; j < n[1]; ++j) {
+            const double ry = Y - h[1] * c_glx[by + j], wy = h[1] * c_glw[by + j];
+            double p[3] = {0, 0, 0};
+            for (int i = 0; i < n[0]; ++i) {
+                const double rx = X - h[0] * c_glx[bx + i];
+                const double r2 = rx * rx + ry * ry + rz * rz;
+                const double ir = rsqrt(r2);
+                const double f = h[0] * c_glw[bx + i] * ir * ir * ir;
+                p[0] += f * rx;
+                p[1] += f * ry;
+                p[2] += f * rz;
+            }
+            const double w = wy * wz;
+            for (int q = 0; q < 3; ++q) s[q] += w * p[q];
+        }
+    }
+    for (int q = 0; q < 3; ++q) out[q] = s[q] * (1.0 / (4.0 * 3.14159265358979323846));
+}
+
+__device__ void sp_far(double X, double Y, double Z, double a, double b, double c, double *out)
+{
+    double t[kNumTaylor];
+    taylor_inv_r(X, Y, Z, t);
+    // per-axis moments h^{2k} / (2k + 1), h = d/2
+    double mx[kOrder / 2 + 1], my[kOrder / 2 + 1], mz[kOrder / 2 + 1];
+    for (int k = 0; k <= kOrder / 2; ++k) {
+        mx[k] = pow(0.5 * a, 2 * k) / (2 * k + 1);
+        my[k] = pow(0.5 * b, 2 * k) / (2 * k + 1);
+        mz[k] = pow(0.5 * c, 2 * k) / (2 * k + 1);
+    }
+    for (int q = 0; q < 3; ++q) {
+        double s = 0.0;
+        for (int k1 = kOrder / 2; k1 >= 0; --k1)
+            for (int k2 = kOrder / 2 - k1; k2 >= 0; --k2)
+                for (int k3 = kOrder / 2 - k1 - k2; k3 >= 0; --k3) {
+                    int be[3] = {2 * k1, 2 * k2, 2 * k3};
+                    const double fac = be[q] + 1.0;
+                    be[q] += 1;
+                    s += mx[k1] * my[k2] * mz[k3] * fac * t[tidx(be[0], be[1], be[2])];
+                }
+        out[q] = a * b * c / (4.0 * 3.14159265358979323846) * s;
+    }
+}
+
+// Octant of S at half-integer offsets: out[3][nz][ny][nx], entry (k, j, i)
+// = S((i + 1/2) a, (j + 1/2) b, (k + 1/2) c), edges scaled by the longest (L);
+// the stored value is L * S (S scales like a length).
+__global__ void k_sp_octant(double *__restrict__ out, int nx, int ny, int nz, double a, double b, double c,
+                            double L)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % nx), j = (int)((idx / nx) % ny), k = (int)(idx / ((int64_t)nx * ny));
+        const double X = (i + 0.5) * a, Y = (j + 0.5) * b, Z = (k + 0.5) * c;
+        const double dmax = fmax(a, fmax(b, c));
+        double v[3];
+        if (X <= 2.5 * a && Y <= 2.5 * b && Z <= 2.5 * c) sp_near(X, Y, Z, a, b, c, v);
+        else if (X * X + Y * Y + Z * Z >= (kFar * dmax) * (kFar * dmax)) sp_far(X, Y, Z, a, b, c, v);
+        else sp_mid(X, Y, Z, a, b, c, v);
+        for (int q = 0; q < 3; ++q) out[q * n + idx] = L * v[q];
+    }
+}
+
+// Wrapped node kernel of component comp on the padded grid: index p of an
+// axis with n cells holds node-minus-cell offset q = p (p <= n) or p - P
+// (p >= P - n + 1), at distance (q - 1/2) d, i.e. octant index q - 1 (q >= 1)
+// or -q (q <= 0, where component comp takes the sign of its own axis).
+__global__ void k_sp_wrap(const double *__restrict__ oct, int comp, int nx, int ny, int nz, int Px, int Py,
+                          int Pz, double *__restrict__ out)
+{
+    const int64_t total = (int64_t)Px * Py * Pz;
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int px = (int)(idx % Px), py = (int)((idx / Px) % Py), pz = (int)(idx / ((int64_t)Px * Py));
+        const int qx = px <= nx ? px : (px >= Px - nx + 1 ? px - Px : INT_MIN);
+        const int qy = py <= ny ? py : (py >= Py - ny + 1 ? py - Py : INT_MIN);
+        const int qz = pz <= nz ? pz : (pz >= Pz - nz + 1 ? pz - Pz : INT_MIN);
+        double v = 0.0;
+        if (qx != INT_MIN && qy != INT_MIN && qz != INT_MIN) {
+            const int tx = qx >= 1 ? qx - 1 : -qx, ty = qy >= 1 ? qy - 1 : -qy, tz = qz >= 1 ? qz - 1 : -qz;
+            v = oct[comp * n + ((int64_t)tz * ny + ty) * nx + tx];
+            const int q = comp == 0 ? qx : (comp == 1 ? qy : qz);
+            if (q <= 0) v = -v;
+        }
+        out[idx] = v;
+    }
+}
+
+// T_comp(k) = Re(i conj(Phi(k)) S^(k)), Phi(k) = exp(-pi i (kx/Px + ky/Py + kz/Pz)),
+// for kx < Kx, ky <= Py/2, kz <= Pz/2; the largest |Im| goes to imag_max.
+__global__ void k_sp_extract(const double2 *__restrict__ S, int comp, int Px, int Kx, int Py, int Pz, int Kxp,
+                             double *__restrict__ t64, float *__restrict__ t32,
+                             unsigned long long *__restrict__ imag_max)
+{
+    const int hy = Py / 2 + 1, hz = Pz / 2 + 1;
+    const int64_t plane = (int64_t)hz * hy * Kx;
+    double local = 0.0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < plane;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(idx % Kx), ky = (int)((idx / Kx) % hy), kz = (int)(idx / ((int64_t)Kx * hy));
+        const double2 v = S[((int64_t)kz * Py + ky) * Kxp + kx];
+        // theta / pi, reduced exactly: kx/Px + ky/Py + kz/Pz with power-of-two P
+        const double th = (double)kx / Px + (double)ky / Py + (double)kz / Pz;
+        double sn, cs;
+        sincospi(th, &sn, &cs);
+        // i conj(Phi) = -sin + i cos
+        const double re = -sn * v.x - cs * v.y;
+        const double im = cs * v.x - sn * v.y;
+        t64[comp * plane + idx] = re;
+        if (t32) t32[comp * plane + idx] = (float)re;
+        local = fmax(local, fabs(im));
+    }
+    atomicMax(imag_max, (unsigned long long)__double_as_longlong(local));
+}
+
 int grid_for(int64_t n, int block)
 {
     const int64_t g = (n + block - 1) / block;
@@ -384,6 +587,32 @@ cudaError_t tensor_extract(const double2 *S, int comp, int Px, int Py, int Pz, i
     const int Kx = Px / 2 + 1;
     const int64_t plane = (int64_t)(Pz / 2 + 1) * (Py / 2 + 1) * Kx;
     k_extract<<<grid_for(plane, 256), 256, 0, st>>>(S, comp, Kx, Py, Pz, Kxp, nhat64, nhat32, imag_max);
+    return cudaGetLastError();
+}
+
+cudaError_t sp_octant(double *out, int nx, int ny, int nz, double dx, double dy, double dz, cudaStream_t st)
+{
+    if (!upload_rules()) return cudaErrorUnknown;
+    const double h = fmax(dx, fmax(dy, dz));
+    const int64_t n = (int64_t)nx * ny * nz;
+    k_sp_octant<<<grid_for(n, 64), 64, 0, st>>>(out, nx, ny, nz, dx / h, dy / h, dz / h, h);
+    return cudaGetLastError();
+}
+
+cudaError_t sp_wrap(const double *oct, int comp, int nx, int ny, int nz, int Px, int Py, int Pz, double *out,
+                    cudaStream_t st)
+{
+    const int64_t total = (int64_t)Px * Py * Pz;
+    k_sp_wrap<<<grid_for(total, 256), 256, 0, st>>>(oct, comp, nx, ny, nz, Px, Py, Pz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t sp_extract(const double2 *S, int comp, int Px, int Py, int Pz, int Kxp, double *t64, float *t32,
+                       unsigned long long *imag_max, cudaStream_t st)
+{
+    const int Kx = Px / 2 + 1;
+    const int64_t plane = (int64_t)(Pz / 2 + 1) * (Py / 2 + 1) * Kx;
+    k_sp_extract<<<grid_for(plane, 256), 256, 0, st>>>(S, comp, Px, Kx, Py, Pz, Kxp, t64, t32, imag_max);
     return cudaGetLastError();
 }
 

@@ -13,9 +13,14 @@ from . import binding as B
 
 
 class Plan:
-    """Stray field of an nx x ny x nz grid of cells with edges (dx, dy, dz)."""
+    """Stray field of an nx x ny x nz grid of cells with edges (dx, dy, dz).
 
-    def __init__(self, n, d, prec: str = "f32", pad=None, device=None, setup: bool = True):
+    method="dm": the demagnetization-tensor convolution (paper Sec. 3.1, Eq.
+    "demag"); method="sp": the scalar-potential convolution at the grid nodes
+    with the finite-difference field (Eqs. "scpot" and "field")."""
+
+    def __init__(self, n, d, prec: str = "f32", pad=None, device=None, setup: bool = True,
+                 method: str = "dm"):
         if not torch.cuda.is_available():
             raise RuntimeError("libdemag needs a CUDA device; there is no CPU path")
         self.n = tuple(int(v) for v in n)
@@ -23,6 +28,9 @@ class Plan:
         if prec not in ("f32", "f64"):
             raise ValueError("prec must be 'f32' or 'f64'")
         self.prec = prec
+        if method not in ("dm", "sp"):
+            raise ValueError("method must be 'dm' or 'sp'")
+        self.method = method
         self.dtype = torch.float32 if prec == "f32" else torch.float64
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
@@ -30,7 +38,9 @@ class Plan:
         code = B.DEMAG_F32 if prec == "f32" else B.DEMAG_F64
         self.handle = None
         with torch.cuda.device(self.device):
-            if pad is None:
+            if method == "sp":
+                self.handle = B.demag_plan_create_sp(nx, ny, nz, *self.d, code, *(pad or (0, 0, 0)))
+            elif pad is None:
                 self.handle = B.demag_plan_create(nx, ny, nz, *self.d, code)
             else:
                 self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, *pad)
@@ -86,6 +96,18 @@ class Plan:
         H = torch.empty_like(M) if out is None else self._field_arg(out, "out")
         B.demag_field(self.handle, M.data_ptr(), H.data_ptr(), self._stream())
         return H
+
+    def potential(self, M: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """SP plans: node potential phi = S * M, shape (nz+1, ny+1, nx+1) (Eq. "scpot")."""
+        M = self._field_arg(M, "M")
+        nx, ny, nz = self.n
+        shape = (nz + 1, ny + 1, nx + 1)
+        if out is None:
+            out = torch.empty(shape, dtype=self.dtype, device=self.device)
+        elif tuple(out.shape) != shape or out.dtype != self.dtype or out.device != self.device:
+            raise ValueError(f"out must be a {self.dtype} tensor of shape {shape} on {self.device}")
+        B.demag_sp_potential(self.handle, M.data_ptr(), out.data_ptr(), self._stream())
+        return out
 
     def field_adjoint(self, G: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         G = self._field_arg(G, "G")

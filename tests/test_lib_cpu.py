@@ -63,6 +63,22 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
     assert binding.demag_launch_count(None) == 0
 
 
+def test_sp_plan_arguments_are_checked_before_any_device_call(lib):
+    """Scalar-potential plans: padding must be a power of two >= 2n (not 2n - 1),
+    z is built up to 256 cells, and the usual size and edge checks apply."""
+    from paper_1204_4302_gb300 import binding
+    cases = [((0, 4, 4, 1.0, 1.0, 1.0), {}, "DEMAG_ERR_INVALID_ARG"),
+             ((4, 4, 4, 1.0, 0.0, 1.0), {}, "DEMAG_ERR_INVALID_ARG"),
+             ((8, 8, 257, 1.0, 1.0, 1.0), {}, "DEMAG_ERR_UNSUPPORTED"),
+             ((513, 8, 8, 1.0, 1.0, 1.0), {}, "DEMAG_ERR_UNSUPPORTED"),
+             ((8, 8, 8, 1.0, 1.0, 1.0), {"px": 15}, "DEMAG_ERR_INVALID_ARG"),
+             ((8, 8, 8, 1.0, 1.0, 1.0), {"py": 8}, "DEMAG_ERR_INVALID_ARG")]
+    for args, pad, status in cases:
+        with pytest.raises(binding.DemagError) as e:
+            binding.demag_plan_create_sp(*args, 0, **pad)
+        assert e.value.name == status, (args, pad)
+
+
 def test_no_device_gives_a_cuda_status():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
