@@ -63,6 +63,36 @@ def pass_bytes(n, P, elem=4):
     }
 
 
+SP_PASS_NAMES = ["x_fwd", "y_fwd", "sp_z", "y_inv", "x_inv", "sp_grad"]
+
+
+def sp_pass_bytes(n, P, elem=4):
+    """Algorithmic HBM bytes per launch of the scalar-potential pipeline: the
+    forward passes as for DM; the SP z pass reads three spectra and the three
+    real kernel tables and writes one spectrum of nz + 1 rows; the inverse
+    passes move one component; the field stencil reads the node potential and
+    M (for the energy) and writes H."""
+    nx, ny, nz = n
+    Px, Py, Pz = P
+    Kx = Px // 2 + 1
+    c = 2 * elem
+    cells = nx * ny * nz
+    nodes = (nx + 1) * (ny + 1) * (nz + 1)
+    s1 = 3 * nz * ny * Kx * c
+    s2 = 3 * nz * Py * Kx * c
+    phi_hat = (nz + 1) * Py * Kx * c
+    phi_y = (nz + 1) * (ny + 1) * Kx * c
+    tab = 3 * (Pz // 2 + 1) * (Py // 2 + 1) * Kx * elem
+    return {
+        "x_fwd": 3 * cells * elem + s1,
+        "y_fwd": s1 + s2,
+        "sp_z": s2 + tab + phi_hat,
+        "y_inv": phi_hat + phi_y,
+        "x_inv": phi_y + nodes * elem,
+        "sp_grad": nodes * elem + 3 * cells * elem + 3 * cells * elem,
+    }
+
+
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     """Largest value of x over all ranks (the slowest rank's time); x itself
     without a process group."""
@@ -356,6 +386,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.skip_batch:
         batch = run_batch(args, dev, rank)
 
+    sp = None
+    if not args.skip_sp:
+        sp = run_sp(args, dev, M, H, peak)
+        sp["speedup_over_dm"] = round(ms_per_step / sp["ms_per_step"], 3)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cpu = cpu_baseline(args.cpu_sample)
@@ -384,6 +419,7 @@ def run_ours(args, rank, world, local_rank):
             "autotune": {"z_variant": variants[0], "y_variant": variants[1],
                          "ms_per_field": None if tuned_ms is None else round(tuned_ms, 4)},
             "batch": batch,
+            "scalar_potential": sp,
             "energy_J": E_val,
             "passes": per_pass,
             "roofline": roof,
@@ -399,6 +435,67 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     plan.close()
+
+
+def run_sp(args, dev, M, H_dm, peak):
+    """The scalar-potential method (paper Sec. 3.1) on the same state: FP32
+    field + energy per step, per-pass times and HBM fractions, and its FP32
+    error against the FP64 SP path. (Its field differs from the DM field by the
+    finite-difference error, which for a random state is of order one and for
+    the paper's smooth states about 1e-3; the tests check the latter.)"""
+    import torch
+
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300.plan import Plan
+
+    n = N_GRID
+    cells = n[0] * n[1] * n[2]
+    st = torch.cuda.current_stream(dev)
+    plan = Plan(n, CELL, prec="f32", device=dev, method="sp")
+    tuned = None if args.no_tune else plan.autotune(use_cache=False)
+    info = plan.info()
+    P = (info["px"], info["py"], info["pz"])
+    H = torch.empty_like(M)
+    E = torch.empty((), dtype=torch.float64, device=dev)
+
+    def step():
+        B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    k = max(5, args.steps)
+    plan.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(k):
+        step()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    pass_ms, pass_n = plan.get_timing(7)
+    plan.set_timing(False)
+    pb = sp_pass_bytes(n, P, 4)
+    passes = {}
+    for i, nm in enumerate(SP_PASS_NAMES):
+        if pass_n[i]:
+            t = pass_ms[i] / pass_n[i]
+            gbs = pb[nm] / (t * 1e-3) / 1e9
+            passes[nm] = {"ms": round(t, 4), "bytes": pb[nm], "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    out = {"ms_per_step": round(ms, 4), "cells_per_s": cells / (ms / 1e3), "passes": passes,
+           "y_variant": plan.variants()[1], "energy_J": float(E.item()),
+           "speedup_over_dm": None}
+    plan.close()
+    if not args.skip_f64:
+        p64 = Plan(n, CELL, prec="f64", device=dev, method="sp")
+        H64 = p64.field(M.double())
+        out["f32_rel_max_err_vs_f64"] = float((H.double() - H64).abs().max() / H64.abs().max())
+        p64.close()
+        del H64
+    del H
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args, dev, rank):
@@ -531,6 +628,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-sp", action="store_true", help="skip the scalar-potential method leg")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")
     ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")
     args = ap.parse_args()
