@@ -324,6 +324,23 @@ demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, v
 demag_status demag_get_variants(demag_plan_t plan, int *z, int *y);
 demag_status demag_set_variants(demag_plan_t plan, int z, int y);
 
+/* x-pass variant: 0 = one CTA per tile of rows; 1 (default) = the forward
+ * pass by persistent CTAs that stream their row tiles through shared memory
+ * with bulk asynchronous copies (TMA) on mbarriers, two tiles in flight, where
+ * the rows are contiguous 16-byte multiples (nx % 4 == 0, no cell weight),
+ * else as 0; 2 = the inverse pass pipelined the same way too. The autotuner
+ * times all three. Out-of-range x: DEMAG_ERR_INVALID_ARG. */
+demag_status demag_get_x_variant(demag_plan_t plan, int *x);
+demag_status demag_set_x_variant(demag_plan_t plan, int x);
+
+/* The pipelined x passes wait for their bulk copies with a bound (about two
+ * seconds); if a wait gives up, the kernel waits (bounded) for its copies in
+ * flight, records the failure and returns, leaving that call's output
+ * incomplete. This call synchronises the device and returns
+ * DEMAG_ERR_TIMEOUT if that happened since the last check (and clears it),
+ * else DEMAG_OK. */
+demag_status demag_check_pipeline(demag_plan_t plan);
+
 /* Destroy a plan and free its device memory (NULL is ignored). */
 void demag_plan_destroy(demag_plan_t plan);
 

@@ -41,6 +41,7 @@ EXPORTS = [
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
     "demag_field_host_async", "demag_host_wait",
     "demag_plan_create_sp", "demag_sp_potential",
+    "demag_get_x_variant", "demag_set_x_variant", "demag_check_pipeline",
 ]
 
 
@@ -120,6 +121,9 @@ def load(path: str | Path | None = None):
         "demag_host_wait": (S, [P]),
         "demag_plan_create_sp": (S, [I, I, I, D, D, D, I, POINTER(demag_options), POINTER(c_void_p)]),
         "demag_sp_potential": (S, [P, P, P, P]),
+        "demag_get_x_variant": (S, [P, POINTER(c_int)]),
+        "demag_set_x_variant": (S, [P, I]),
+        "demag_check_pipeline": (S, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -168,6 +172,20 @@ def demag_plan_create_sp(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=
 
 def demag_sp_potential(plan, M, phi, stream=0):
     _check(load().demag_sp_potential(_p(plan), _p(M), _p(phi), _p(stream)), "demag_sp_potential")
+
+
+def demag_get_x_variant(plan) -> int:
+    x = c_int()
+    _check(load().demag_get_x_variant(_p(plan), ctypes.byref(x)), "demag_get_x_variant")
+    return x.value
+
+
+def demag_set_x_variant(plan, x):
+    _check(load().demag_set_x_variant(_p(plan), int(x)), "demag_set_x_variant")
+
+
+def demag_check_pipeline(plan):
+    _check(load().demag_check_pipeline(_p(plan)), "demag_check_pipeline")
 
 
 def demag_tensor_setup(plan, stream=0):

@@ -212,7 +212,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     cudaError_t e;
     // x forward
     if (Px == 1) e = Passes<T>::x1_fwd(xi, rows, S1, st);
-    else e = Passes<T>::x_fwd(Px / 2, xi, rows, nx, S1, Kxp, twx, st);
+    else e = Passes<T>::x_fwd(Px / 2, xi, rows, nx, S1, Kxp, twx, st, p->xvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x forward: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -245,7 +245,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
         e = Passes<T>::x1_inv(S1, rows, xo, nblocks, st);
     } else {
         nblocks = Passes<T>::x_blocks(Px / 2, rows);
-        e = Passes<T>::x_inv(Px / 2, S1, Kxp, rows, nx, xo, twx, st);
+        e = Passes<T>::x_inv(Px / 2, S1, Kxp, rows, nx, xo, twx, st, p->xvariant);
     }
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x inverse: ") + cudaGetErrorString(e));
     p->launches++;
@@ -296,7 +296,7 @@ demag_status run_field_sp(demag_plan *p, const FieldJob &job, cudaStream_t st)
     xo.partials = nullptr;
     xo.rows_per_comp = (nz + 1) * (ny + 1);
     PassTimer tm(p, st);
-    cudaError_t e = Passes<T>::x_fwd(Px / 2, xi, 3 * nz * ny, nx, S1, Kxp, twx, st);
+    cudaError_t e = Passes<T>::x_fwd(Px / 2, xi, 3 * nz * ny, nx, S1, Kxp, twx, st, p->xvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x forward: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -315,7 +315,7 @@ demag_status run_field_sp(demag_plan *p, const FieldJob &job, cudaStream_t st)
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("y inverse: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
-    e = Passes<T>::x_inv(Px / 2, S1, Kxp, (nz + 1) * (ny + 1), nx + 1, xo, twx, st);
+    e = Passes<T>::x_inv(Px / 2, S1, Kxp, (nz + 1) * (ny + 1), nx + 1, xo, twx, st, p->xvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("x inverse: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -408,26 +408,28 @@ std::string tune_key(const demag_plan *p)
     for (auto &c : name)
         if (c == ' ') c = '_';
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%s|%dx%dx%d|%dx%dx%d%s", name.c_str(), p->prec == DEMAG_F32 ? "f32" : "f64", p->Px,
+    snprintf(buf, sizeof buf, "v2|%s|%s|%dx%dx%d|%dx%dx%d%s", name.c_str(), p->prec == DEMAG_F32 ? "f32" : "f64", p->Px,
              p->Py, p->Pz, p->nx, p->ny, p->nz, p->method == DEMAG_METHOD_SP ? "|sp" : "");
     return buf;
 }
 
-bool tune_lookup(const std::string &key, int &z, int &y, double &ms)
+bool tune_lookup(const std::string &key, int &z, int &y, int &x, double &ms)
 {
     FILE *f = fopen(tune_path().c_str(), "r");
     if (!f) return false;
-    char k[512];
-    int zz, yy;
+    char line[768], k[512];
+    int zz, yy, xx;
     double m;
     bool found = false;
-    while (fscanf(f, "%511s %d %d %lf", k, &zz, &yy, &m) == 4)
-        if (key == k) { z = zz; y = yy; ms = m; found = true; }  // the last entry wins
+    while (fgets(line, sizeof line, f))
+        if (sscanf(line, "%511s %d %d %d %lf", k, &zz, &yy, &xx, &m) == 5 && key == k) {
+            z = zz; y = yy; x = xx; ms = m; found = true;  // the last entry wins
+        }
     fclose(f);
     return found;
 }
 
-void tune_store(const std::string &key, int z, int y, double ms)
+void tune_store(const std::string &key, int z, int y, int x, double ms)
 {
     const std::string path = tune_path();
     const size_t slash = path.rfind('/');
@@ -437,7 +439,7 @@ void tune_store(const std::string &key, int z, int y, double ms)
     }
     FILE *f = fopen(path.c_str(), "a");
     if (!f) return;  // a cache that cannot be written is not an error
-    fprintf(f, "%s %d %d %.6f\n", key.c_str(), z, y, ms);
+    fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), z, y, x, ms);
     fclose(f);
 }
 
@@ -467,6 +469,7 @@ demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz
     demag_plan *p = new demag_plan;
     memset(p, 0, sizeof(*p));
     p->method = method;
+    p->xvariant = 1;  // pipelined x passes where the rows allow them
     p->nx = nx; p->ny = ny; p->nz = nz;
     p->dx = dx; p->dy = dy; p->dz = dz;
     p->prec = prec;
@@ -981,18 +984,19 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     DeviceGuard g(p->device);
     if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
     const std::string key = tune_key(p);
-    int zc = 0, yc = 0;
+    int zc = 0, yc = 0, xc = 1;
     double ms_cached = 0;
-    if (use_cache && tune_lookup(key, zc, yc, ms_cached)) {
+    if (use_cache && tune_lookup(key, zc, yc, xc, ms_cached)) {
         p->zvariant = zc;
         p->yvariant = yc;
+        p->xvariant = xc;
         p->tuned = true;
         if (best_ms) *best_ms = ms_cached;
         return DEMAG_OK;
     }
     // candidates: z-pass tile width where the two-stage z kernel runs, y-pass
     // radix order where the two radices differ
-    std::vector<int> zs = {0}, ys = {0};
+    std::vector<int> zs = {0}, ys = {0}, xs = {0, 1, 2};
     const bool dm = p->method == DEMAG_METHOD_DM;  // the SP z pass has one form
     if (dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
     if (dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
@@ -1014,12 +1018,14 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     const bool timing = p->timing;
     p->timing = false;
     double best = 1e30;
-    int bz = 0, by = 0;
+    int bz = 0, by = 0, bx = 1;
     demag_status rs = DEMAG_OK;
+    for (int x : xs)
     for (int z : zs)
         for (int y : ys) {
             p->zvariant = z;
             p->yvariant = y;
+            p->xvariant = x;
             for (int w = 0; w < 2 && rs == DEMAG_OK; ++w) rs = run_job(p, plain_job(M, H, nullptr), stream);
             cudaEventRecord(e0, st);
             for (int r = 0; r < 5 && rs == DEMAG_OK; ++r) rs = run_job(p, plain_job(M, H, nullptr), stream);
@@ -1027,7 +1033,7 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
             cudaEventSynchronize(e1);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rs == DEMAG_OK && ms / 5 < best) { best = ms / 5; bz = z; by = y; }
+            if (rs == DEMAG_OK && ms / 5 < best) { best = ms / 5; bz = z; by = y; bx = x; }
         }
     p->timing = timing;
     cudaEventDestroy(e0);
@@ -1037,9 +1043,10 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     if (rs != DEMAG_OK) return rs;
     p->zvariant = bz;
     p->yvariant = by;
+    p->xvariant = bx;
     p->tuned = true;
     if (best_ms) *best_ms = best;
-    if (use_cache) tune_store(key, bz, by, best);
+    if (use_cache) tune_store(key, bz, by, bx, best);
     return DEMAG_OK;
 }
 
@@ -1056,6 +1063,31 @@ demag_status demag_set_variants(demag_plan_t p, int z, int y)
     if (!p || z < 0 || z > 3 || y < 0 || y > 2) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->zvariant = z;
     p->yvariant = y;
+    return DEMAG_OK;
+}
+
+demag_status demag_get_x_variant(demag_plan_t p, int *x)
+{
+    if (!p || !x) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
+    *x = p->xvariant;
+    return DEMAG_OK;
+}
+
+demag_status demag_set_x_variant(demag_plan_t p, int x)
+{
+    if (!p || x < 0 || x > 2) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
+    p->xvariant = x;
+    return DEMAG_OK;
+}
+
+demag_status demag_check_pipeline(demag_plan_t p)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    DEMAG_CUDA(cudaDeviceSynchronize());
+    const int e = Passes<float>::pipe_error_take() | Passes<double>::pipe_error_take();
+    if (e) return fail(DEMAG_ERR_TIMEOUT, "a pipelined x pass gave up waiting for a bulk copy");
     return DEMAG_OK;
 }
 

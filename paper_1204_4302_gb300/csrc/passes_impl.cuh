@@ -6,6 +6,7 @@
 #include "fft_engine.cuh"
 #include "plan.h"
 #include "sp.cuh"
+#include "xpipe.cuh"
 
 namespace demag {
 
@@ -69,11 +70,79 @@ __global__ void __launch_bounds__(256) k_x1_inv(const typename Cplx<T>::type *__
 #define DEMAG_FOR_EACH_L(M) \
     M(1) M(2) M(4) M(8) M(16) M(32) M(64) M(128) M(256) M(512) M(1024)
 
+namespace {
+// Resident CTAs per SM of a kernel at a given dynamic shared-memory size
+// (cached per kernel for the last size asked).
+template <auto Kern>
+int resident_ctas(int threads, size_t smem)
+{
+    static size_t last = (size_t)-1;
+    static int occ = 1;
+    if (smem != last) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, Kern, threads, smem) != cudaSuccess || o < 1) o = 1;
+        occ = o;
+        last = smem;
+    }
+    return occ;
+}
+
+template <typename T, int L>
+cudaError_t x_fwd_pipe(const XIn<T> &a, int nrows, int nvalid, typename Cplx<T>::type *out, int64_t out_rs,
+                       const typename Cplx<T>::type *twx, cudaStream_t st)
+{
+    using S = XShape<T, L>;
+    const size_t sm = XPipeSmem<T, L, T>::bytes(S::TR * nvalid);
+    cudaError_t e = allow_smem<k_x_fwd_tma<T, L>>(sm);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (nrows + S::TR - 1) / S::TR;
+    const int cap = sm_count() * resident_ctas<k_x_fwd_tma<T, L>>(S::NT, sm);
+    k_x_fwd_tma<T, L><<<ntiles < cap ? ntiles : cap, S::NT, sm, st>>>(a.in, a.wscalar, nrows, nvalid, out, out_rs,
+                                                                      twx, ntiles);
+    return cudaGetLastError();
+}
+
+template <typename T, int L, bool P1>
+cudaError_t x_inv_pipe(const typename Cplx<T>::type *in, int in_rs, int nrows, int nvalid, const XOut<T> &o,
+                       const typename Cplx<T>::type *twx, cudaStream_t st)
+{
+    using S = XShape<T, L>;
+    const size_t sm = XPipeSmem<T, L, typename Cplx<T>::type>::bytes(S::TR * in_rs);
+    cudaError_t e = allow_smem<k_x_inv_tma<T, L, P1>>(sm);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (nrows + S::TR - 1) / S::TR;
+    const int cap = sm_count() * resident_ctas<k_x_inv_tma<T, L, P1>>(S::NT, sm);
+    k_x_inv_tma<T, L, P1><<<ntiles < cap ? ntiles : cap, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, ntiles);
+    return cudaGetLastError();
+}
+}  // namespace
+
+template <typename T>
+int Passes<T>::pipe_error_take()
+{
+    int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_xpipe_error, sizeof(int)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_xpipe_error, &zero, sizeof(int));
+    return v;
+}
+
 template <typename T>
 cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *out, int64_t out_rs,
-                             const C *twx, cudaStream_t st)
+                             const C *twx, cudaStream_t st, int variant)
 {
     if (nrows <= 0) return cudaSuccess;
+    // pipelined form: rows of the plain field (no per-cell weight) stored back
+    // to back, 16-byte multiples, zero-padded half
+    if (variant >= 1 && L >= 64 && nvalid <= L && !a.wcell && a.in_rs == nvalid && nvalid % 4 == 0 &&
+        ((uintptr_t)a.in & 15) == 0) {
+        switch (L) {
+        case 64: return x_fwd_pipe<T, 64>(a, nrows, nvalid, out, out_rs, twx, st);
+        case 128: return x_fwd_pipe<T, 128>(a, nrows, nvalid, out, out_rs, twx, st);
+        case 256: return x_fwd_pipe<T, 256>(a, nrows, nvalid, out, out_rs, twx, st);
+        case 512: return x_fwd_pipe<T, 512>(a, nrows, nvalid, out, out_rs, twx, st);
+        default: break;
+        }
+    }
     if (L >= 64) {
 #define DEMAG_CASE2(LL)                                                                        \
     case LL: {                                                                                 \
@@ -123,9 +192,18 @@ int Passes<T>::x_blocks(int L, int nrows)
 
 template <typename T>
 cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int nvalid, const XOut<T> &o,
-                             const C *twx, cudaStream_t st)
+                             const C *twx, cudaStream_t st, int variant)
 {
     if (nrows <= 0) return cudaSuccess;
+    if (variant == 2 && L >= 64 && in_rs % 2 == 0 && in_rs <= 2 * L && nvalid <= L + 1 && ((uintptr_t)in & 15) == 0) {
+        const bool p1 = nvalid > L;
+#define DEMAG_PIPE(LL)                                                                         \
+    case LL:                                                                                   \
+        return p1 ? x_inv_pipe<T, LL, true>(in, (int)in_rs, nrows, nvalid, o, twx, st)         \
+                  : x_inv_pipe<T, LL, false>(in, (int)in_rs, nrows, nvalid, o, twx, st);
+        switch (L) { DEMAG_PIPE(64) DEMAG_PIPE(128) DEMAG_PIPE(256) DEMAG_PIPE(512) default: break; }
+#undef DEMAG_PIPE
+    }
     if (L >= 64) {
 #define DEMAG_CASE2(LL)                                                                        \
     case LL: {                                                                                 \

@@ -46,11 +46,16 @@ template <typename T> struct XOut {
 template <typename T> struct Passes {
     using C = typename CplxOf<T>::type;
     // real-to-complex along x; L = Px/2 (complex length), Px >= 2
+    // variant 1: the forward pass by persistent CTAs streaming row tiles
+    // with bulk asynchronous copies (where the rows allow it); variant 2: the
+    // inverse pass too; otherwise the one-tile-per-CTA kernels
     static cudaError_t x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *out, int64_t out_rs,
-                             const C *twx, cudaStream_t st);
+                             const C *twx, cudaStream_t st, int variant = 0);
     // complex-to-real along x with the XOut epilogue
     static cudaError_t x_inv(int L, const C *in, int64_t in_rs, int nrows, int nvalid, const XOut<T> &o,
-                             const C *twx, cudaStream_t st);
+                             const C *twx, cudaStream_t st, int variant = 0);
+    // 1 if a bounded wait of a pipelined pass gave up since the last call (clears it)
+    static int pipe_error_take();
     static int x_blocks(int L, int nrows);
     // strided column transforms (y passes, z forward of the setup)
     static cudaError_t col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss,
@@ -173,6 +178,7 @@ struct demag_plan {
     // tuning choices (kernel variants), set by demag_autotune or defaults
     int zvariant;
     int yvariant;
+    int xvariant;
     bool tuned;
     // timing
     bool timing;

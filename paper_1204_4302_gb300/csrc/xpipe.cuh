@@ -1,0 +1,328 @@
+// Pipelined x passes: persistent CTAs stream their tiles of whole rows
+// through shared memory with bulk asynchronous copies (TMA, cp.async.bulk)
+// completing on mbarriers, two tiles in flight per CTA, so the loads of the
+// next tiles overlap the transforms of the current one. Same arithmetic and
+// results as k_x_fwd2 / k_x_inv2; used when the tile's rows are contiguous
+// and 16-byte multiples (the field passes of plans with nx % 4 == 0 for the
+// forward pass; always for the inverse pass, whose rows are Kxp complex).
+#pragma once
+#include "fft2.cuh"
+
+namespace demag {
+
+// Set when a bounded wait for a bulk copy gave up (read and cleared by the
+// host through Passes<T>::pipe_error_take). One per element type.
+static __device__ int g_xpipe_error;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// Arrive once and expect `bytes` of asynchronous transactions on the barrier.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the barrier's phase with the given parity, giving up after
+// `budget` SM clock cycles. Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long budget)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > budget) return false;
+    return true;
+}
+
+// Global -> shared bulk copy of `bytes` (16-byte aligned addresses, size a
+// multiple of 16) completing as transactions on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later asynchronous-proxy ones (a bulk copy into a buffer just read).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+constexpr long long kPipeWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// Shared-memory plan of a pipelined x pass: exchange rows [TR][RS] complex,
+// two input buffers of `in_elems` elements of type E each, two barriers.
+template <typename T, int L, typename E>
+struct XPipeSmem {
+    static constexpr int TR = XShape<T, L>::TR, RS = XShape<T, L>::RS;
+    static size_t bytes(int in_elems)
+    {
+        const size_t ex = (size_t)TR * RS * sizeof(typename Cplx<T>::type);
+        const size_t in = ((size_t)in_elems * sizeof(E) + 15) / 16 * 16;
+        return ex + 2 * in + 2 * sizeof(uint64_t);
+    }
+};
+
+// Issue the bulk copy of tile t (rows [t TR, min((t+1) TR, nrows)) of
+// rowlen elements, contiguous in global memory) into buffer b.
+template <typename E>
+__device__ __forceinline__ void xpipe_issue(const E *src, int rowlen, int nrows, int TR, int t, E *buf,
+                                            uint64_t *bar)
+{
+    const int r0 = t * TR;
+    const int rows = min(TR, nrows - r0);
+    const unsigned bytes = (unsigned)((size_t)rows * rowlen * sizeof(E));
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(buf, src + (int64_t)r0 * rowlen, bytes, bar);
+}
+
+// Error exit: wait (bounded) for copies this CTA still has in flight, flag
+// the failure for the host.
+__device__ __forceinline__ void xpipe_abort(uint64_t *bars, int next_i, int gridstep, int ntiles)
+{
+    if (threadIdx.x == 0) {
+        for (int i = next_i; i < next_i + 2; ++i) {
+            const int t = blockIdx.x + i * gridstep;
+            if (t < ntiles) mbar_wait_bounded(&bars[i & 1], (unsigned)((i >> 1) & 1), kPipeWaitCycles);
+        }
+        atomicExch(&g_xpipe_error, 1);
+    }
+}
+
+// Forward R2C rows (PIN: at most L reals per row, rows of nvalid reals stored
+// back to back, nvalid % 4 == 0), persistent over tiles.
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out,
+            int64_t out_rs, const typename Cplx<T>::type *__restrict__ twx, int ntiles)
+{
+    using C = typename Cplx<T>::type;
+    using S = XShape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, TR = S::TR, RS = S::RS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const size_t inb = ((size_t)TR * nvalid * sizeof(T) + 15) / 16 * 16;
+    T *buf[2] = {reinterpret_cast<T *>(smraw + (size_t)TR * RS * sizeof(C)),
+                 reinterpret_cast<T *>(smraw + (size_t)TR * RS * sizeof(C) + inb)};
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + (size_t)TR * RS * sizeof(C) + 2 * inb);
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int step = gridDim.x;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 2; ++i) {
+            const int t = blockIdx.x + i * step;
+            if (t < ntiles) xpipe_issue(in, nvalid, nrows, TR, t, buf[i], &bars[i]);
+        }
+    for (int i = 0;; ++i) {
+        const int t = blockIdx.x + i * step;
+        if (t >= ntiles) break;
+        const int b = i & 1;
+        if (!mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1), kPipeWaitCycles)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) {
+            xpipe_abort(bars, i + 1, step, ntiles);
+            return;
+        }
+        const int row0 = t * TR;
+        // stage 1 from shared memory: thread (row, j1) reads z[j1 + r R2], r < R1/2
+        if (threadIdx.x < TR * R2) {
+            const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
+            C u[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+            if (row < nrows) {
+                const T *p = buf[b] + rr * nvalid;
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r) {
+                    const int x0 = 2 * (j1 + r * R2);
+                    if (x0 < nvalid) {  // nvalid is even
+                        const C q = *reinterpret_cast<const C *>(p + x0);
+                        u[r] = cmk<C>(q.x * wscalar, q.y * wscalar);
+                    }
+                }
+            }
+            RegDFTHalfIn<R1, false, C>::run(u);
+            C *s = sm + rr * RS;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+        }
+        __syncthreads();  // buffer b consumed, exchange rows written
+        if (threadIdx.x == 0) {
+            const int tn = blockIdx.x + (i + 2) * step;
+            if (tn < ntiles) {
+                fence_proxy_async_smem();
+                xpipe_issue(in, nvalid, nrows, TR, tn, buf[b], &bars[b]);
+            }
+        }
+        // stage 2 + split, as k_x_fwd2
+        if (threadIdx.x < TR * R1) {
+            const int rr = threadIdx.x / R1, j2 = threadIdx.x % R1, row = row0 + rr;
+            const C *s = sm + rr * RS;
+            C v[R2];
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+#pragma unroll
+            for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], __ldg(&twx[2 * r * j2]));
+            RegDFT<R2, false, C>::run(v);
+            const int lane = threadIdx.x & 31;
+            const int partner = (lane & ~(R1 - 1)) | ((R1 - j2) & (R1 - 1));
+            const T h = (T)0.5;
+            C *o = out + (int64_t)row * out_rs;
+            const bool live = row < nrows;
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                const C q = shfl_c(v[R2 - 1 - r], partner);
+                const C pz = j2 == 0 ? v[(R2 - r) % R2] : q;
+                const int k = j2 + r * R1;
+                const C E = cmk<C>(h * (v[r].x + pz.x), h * (v[r].y - pz.y));
+                const C O = cmk<C>(h * (v[r].y + pz.y), -h * (v[r].x - pz.x));
+                if (live) o[k] = cadd(E, cmul(O, __ldg(&twx[k])));
+            }
+            if (live && j2 == 0) o[L] = cmk<C>(v[0].x - v[0].y, (T)0);
+        }
+        __syncthreads();  // exchange rows read before the next tile rewrites them
+    }
+}
+
+// Inverse C2R rows with the XOut epilogue (energy partials per tile into
+// partials[t]); input rows of in_rs complex (even) stored back to back.
+// P1 as in k_x_inv2 (one output pair beyond the half length).
+template <typename T, int L, bool P1>
+__global__ void __launch_bounds__(Tile2<T>::NT)
+k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows, int nvalid, XOut<T> o,
+            const typename Cplx<T>::type *__restrict__ twx, int ntiles)
+{
+    using C = typename Cplx<T>::type;
+    using S = XShape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TR = S::TR, RS = S::RS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const size_t inb = ((size_t)TR * in_rs * sizeof(C) + 15) / 16 * 16;
+    C *buf[2] = {reinterpret_cast<C *>(smraw + (size_t)TR * RS * sizeof(C)),
+                 reinterpret_cast<C *>(smraw + (size_t)TR * RS * sizeof(C) + inb)};
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + (size_t)TR * RS * sizeof(C) + 2 * inb);
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int step = gridDim.x;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 2; ++i) {
+            const int t = blockIdx.x + i * step;
+            if (t < ntiles) xpipe_issue(in, in_rs, nrows, TR, t, buf[i], &bars[i]);
+        }
+    const T g = o.gdev ? (T)(*o.gdev) : (T)1;
+    const T oscale = o.oscale * g;
+    for (int i = 0;; ++i) {
+        const int t = blockIdx.x + i * step;
+        if (t >= ntiles) break;
+        const int b = i & 1;
+        if (!mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1), kPipeWaitCycles)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) {
+            xpipe_abort(bars, i + 1, step, ntiles);
+            return;
+        }
+        const int row0 = t * TR;
+        if (threadIdx.x < TR * R2) {
+            const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
+            C u[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+            if (row < nrows) {
+                const C *p = buf[b] + rr * in_rs;
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    const int k = j1 + r * R2;
+                    const C a = p[k];
+                    const C bb = p[L - k];
+                    const C E2 = cmk<C>(a.x + bb.x, a.y - bb.y);
+                    const C D = cmk<C>(a.x - bb.x, a.y + bb.y);
+                    const C O2 = cmulc(D, __ldg(&twx[k]));
+                    u[r] = cmk<C>(E2.x - O2.y, E2.y + O2.x);
+                }
+            }
+            RegDFT<R1, true, C>::run(u);
+            C *s = sm + rr * RS;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int tn = blockIdx.x + (i + 2) * step;
+            if (tn < ntiles) {
+                fence_proxy_async_smem();
+                xpipe_issue(in, in_rs, nrows, TR, tn, buf[b], &bars[b]);
+            }
+        }
+        T acc = 0;
+        if (threadIdx.x < TR * R1) {
+            const int rr = threadIdx.x / R1, j2 = threadIdx.x % R1, row = row0 + rr;
+            const C *s = sm + rr * RS;
+            C v[R2];
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+#pragma unroll
+            for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
+            if constexpr (P1) RegDFTHalfOutP1<R2, true, C>::run(v);
+            else RegDFTHalfOut<R2, true, C>::run(v);
+            if (row < nrows) {
+#pragma unroll
+                for (int r = 0; r < (P1 ? R2 / 2 + 1 : R2 / 2); ++r) {
+                    const int n = j2 + r * R1;
+                    const T hv[2] = {v[r].x * o.scale, v[r].y * o.scale};
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int x = 2 * n + u;
+                        if (x >= nvalid) continue;
+                        const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
+                        const int64_t idx = (int64_t)row * o.out_rs + x;
+                        if (o.out) o.out[idx] = hv[u] * oscale * w;
+                        if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
+                    }
+                }
+            }
+        }
+        if (o.partials) block_partial<NT>((double)acc, o.partials, t);  // has its own barriers
+        __syncthreads();
+    }
+}
+
+}  // namespace demag

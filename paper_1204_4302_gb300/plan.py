@@ -175,8 +175,17 @@ class Plan:
     def variants(self):
         return B.demag_get_variants(self.handle)
 
-    def set_variants(self, z: int, y: int):
+    def set_variants(self, z: int, y: int, x: int | None = None):
         B.demag_set_variants(self.handle, z, y)
+        if x is not None:
+            B.demag_set_x_variant(self.handle, x)
+
+    def x_variant(self) -> int:
+        return B.demag_get_x_variant(self.handle)
+
+    def check_pipeline(self):
+        """Raise DemagError(DEMAG_ERR_TIMEOUT) if a pipelined pass gave up waiting."""
+        B.demag_check_pipeline(self.handle)
 
     # ------------------------------------------------------------------ timing
     def set_timing(self, enable: bool = True):
