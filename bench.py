@@ -230,7 +230,10 @@ def run_ours(args, rank, world, local_rank):
     plan = Plan(n, CELL, prec="f32", device=dev)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
-    tuned_ms = None if args.no_tune else plan.autotune(use_cache=False)
+    if args.variants:
+        z, y, x = (int(v) for v in args.variants.split(","))
+        plan.set_variants(z, y, x)
+    tuned_ms = None if (args.no_tune or args.variants) else plan.autotune(use_cache=False)
     variants = plan.variants()
     info = plan.info()
     P = (info["px"], info["py"], info["pz"])
@@ -416,7 +419,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs and spectra (~2 GB) larger than L2, no flush needed"},
             "gpu_launches": launches,
             "setup_ms": round(setup_ms, 1),
-            "autotune": {"z_variant": variants[0], "y_variant": variants[1],
+            "autotune": {"z_variant": variants[0], "y_variant": variants[1], "x_variant": plan.x_variant(),
                          "ms_per_field": None if tuned_ms is None else round(tuned_ms, 4)},
             "batch": batch,
             "scalar_potential": sp,
@@ -452,7 +455,9 @@ def run_sp(args, dev, M, H_dm, peak):
     cells = n[0] * n[1] * n[2]
     st = torch.cuda.current_stream(dev)
     plan = Plan(n, CELL, prec="f32", device=dev, method="sp")
-    tuned = None if args.no_tune else plan.autotune(use_cache=False)
+    if args.variants:
+        plan.set_variants(0, int(args.variants.split(",")[1]), int(args.variants.split(",")[2]))
+    tuned = None if (args.no_tune or args.variants) else plan.autotune(use_cache=False)
     info = plan.info()
     P = (info["px"], info["py"], info["pz"])
     H = torch.empty_like(M)
@@ -630,6 +635,7 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-sp", action="store_true", help="skip the scalar-potential method leg")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")
+    ap.add_argument("--variants", default="", help="fixed z,y,x kernel variants instead of autotuning")
     ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")
     args = ap.parse_args()
     if args.warmup < 3:

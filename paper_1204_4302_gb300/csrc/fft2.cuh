@@ -52,10 +52,13 @@ template <typename T, int L, int V = 0> struct ColShape {
 // Variant 0: TC = Tile2 threads / R1 columns; when R1 = 2 R2 the CTA has
 // 3 TC R2 threads so both stage-1 passes give each thread one butterfly.
 // Variant 1: half the columns.
+// Variant 4: variant 0's thread layout on half the columns, compiled for two
+// resident CTAs per SM (one CTA's loads overlap the other's arithmetic).
 template <typename T, int L, int V = 0> struct ZShape {
     static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2;
-    static constexpr int TC = (V == 1 ? Tile2<T>::NT / 2 : Tile2<T>::NT) / R1;
-    static constexpr int NT = (V == 0 && R1 == 2 * R2) ? 3 * TC * R2 : TC * R1;
+    static constexpr int TC = ((V == 1 || V == 4) ? Tile2<T>::NT / 2 : Tile2<T>::NT) / R1;
+    static constexpr int NT = ((V == 0 || V == 4) && R1 == 2 * R2) ? 3 * TC * R2 : TC * R1;
+    static constexpr int MIN_CTAS = V == 4 ? 2 : 1;
 };
 
 // v[r] *= W_L^(r * k) (or its conjugate), table W_L^m at tw[m * twstride]
@@ -308,6 +311,36 @@ __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem)
     else cp_async8(smem, gmem);
 }
 
+// Copy the CTA's block of a folded spectral table ([NC][HZ][Py/2+1][Kx]) to
+// shared memory as [kzf][comp][c] with cp.async. Thread (g, c) handles the
+// entries kzf * NC + comp = g, g + G, ... (G = NT / TC); (kzf, comp) and the
+// source offset advance incrementally.
+template <typename T, int TC, int NT, int NC, int HZ>
+__device__ __forceinline__ void tensor_block_prefetch(T *smT, const T *__restrict__ tab, int f0, int ncols, int width,
+                                                      int Py, int Kx, int64_t plane)
+{
+    constexpr int G = NT / TC, GQ = G / NC, GR = G % NC;
+    const int c = threadIdx.x % TC, f = f0 + c, g = threadIdx.x / TC;
+    if (f >= ncols) return;
+    const int i = f / width, kx = f - i * width;
+    const int ky = ky_pair_order(i, Py);
+    const int kyf = ky > Py / 2 ? Py - ky : ky;
+    const int64_t zs = (int64_t)(Py / 2 + 1) * Kx;
+    const T *src = tab + (int64_t)kyf * Kx + kx;
+    int comp = g % NC;
+    int64_t off = comp * plane + (int64_t)(g / NC) * zs;
+    const int64_t step = GQ * zs + GR * plane, wrap = zs - NC * plane;
+    for (int idx = g; idx < HZ * NC; idx += G) {
+        cp_async_elem(&smT[idx * TC + c], src + off);
+        comp += GR;
+        off += step;
+        if (comp >= NC) {
+            comp -= NC;
+            off += wrap;
+        }
+    }
+}
+
 // Fused z pass, two stages (L >= 32): forward stage 1 (radix R1, rows < nrows
 // read, upper half zero) for the three components into shared memory;
 // forward stage 2 (radix R2) into registers, which then hold the three
@@ -336,19 +369,7 @@ __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restric
     const int hy = Py / 2 + 1;
     const int64_t plane = (int64_t)HZ * hy * Kx;
 
-    {
-        const int c = threadIdx.x % TC, f = f0 + c;
-        if (f < ncols) {
-            const int i = f / width, kx = f - i * width;
-            const int ky = ky_pair_order(i, Py);
-            const int kyf = ky > Py / 2 ? Py - ky : ky;
-            const T *src = nhat + (int64_t)kyf * Kx + kx;
-            for (int idx = threadIdx.x / TC; idx < HZ * 6; idx += NT / TC) {
-                const int kzf = idx / 6, comp = idx - kzf * 6;
-                cp_async_elem(&smT[idx * TC + c], src + comp * plane + (int64_t)kzf * hy * Kx);
-            }
-        }
-    }
+    tensor_block_prefetch<T, TC, NT, 6, HZ>(smT, nhat, f0, ncols, width, Py, Kx, plane);
 
     // forward stage 1, three components: rows j1 + r R2 -> rows j1 R1 + r
 #pragma unroll
@@ -465,7 +486,7 @@ __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restric
 }
 
 template <typename T, int L, int V>
-__global__ void __launch_bounds__(ZShape<T, L, V>::NT, 1)
+__global__ void __launch_bounds__(ZShape<T, L, V>::NT, ZShape<T, L, V>::MIN_CTAS)
 k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
           int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
           int twstride)

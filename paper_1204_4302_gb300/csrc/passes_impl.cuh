@@ -379,6 +379,7 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
     case LL:                                                                                   \
         return variant == 1 ? zconv_launch<LL, 1>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
              : variant == 2 ? zconv_launch<LL, 2>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
+             : variant == 4 ? zconv_launch<LL, 4>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
                             : zconv_launch<LL, 0>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
     switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE

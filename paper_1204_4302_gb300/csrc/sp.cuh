@@ -57,19 +57,7 @@ k_sp_z2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss
     const int hy = Py / 2 + 1;
     const int64_t plane = (int64_t)HZ * hy * Kx;
 
-    {
-        const int c = threadIdx.x % TC, f = f0 + c;
-        if (f < ncols) {
-            const int i = f / width, kx = f - i * width;
-            const int ky = ky_pair_order(i, Py);
-            const int kyf = ky > Py / 2 ? Py - ky : ky;
-            const T *src = that + (int64_t)kyf * Kx + kx;
-            for (int idx = threadIdx.x / TC; idx < HZ * 3; idx += NT / TC) {
-                const int kzf = idx / 3, comp = idx - kzf * 3;
-                cp_async_elem(&smT[idx * TC + c], src + comp * plane + (int64_t)kzf * hy * Kx);
-            }
-        }
-    }
+    tensor_block_prefetch<T, TC, NT, 3, HZ>(smT, that, f0, ncols, width, Py, Kx, plane);
 
     // forward stage 1, three components: rows j1 + r R2 -> rows j1 R1 + r
 #pragma unroll
