@@ -320,8 +320,10 @@ demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, v
  *    4 = variant 0's layout on half the columns with two CTAs per SM.
  * y: 0 = two-stage column transform, 1 = swapped radix order (y lengths 32,
  *    128, 512), 2 = three-stage transform with more CTAs per SM (y lengths
- *    512 and 1024). A variant that does not exist for the plan's lengths runs
- *    as variant 0. Out-of-range values: DEMAG_ERR_INVALID_ARG. */
+ *    512 and 1024), 3 = as 2, with the forward pass by persistent CTAs that
+ *    receive their column tiles by TMA tensor copies (two tiles in flight).
+ *    A variant that does not exist for the plan's lengths runs as variant 0.
+ *    Out-of-range values: DEMAG_ERR_INVALID_ARG. */
 demag_status demag_get_variants(demag_plan_t plan, int *z, int *y);
 demag_status demag_set_variants(demag_plan_t plan, int z, int y);
 

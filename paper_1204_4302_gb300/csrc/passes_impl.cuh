@@ -4,6 +4,8 @@
 #pragma once
 #include "fft2.cuh"
 #include "fft_engine.cuh"
+#include <string.h>
+
 #include "plan.h"
 #include "sp.cuh"
 #include "xpipe.cuh"
@@ -107,12 +109,104 @@ cudaError_t x_inv_pipe(const typename Cplx<T>::type *in, int in_rs, int nrows, i
                        const typename Cplx<T>::type *twx, cudaStream_t st)
 {
     using S = XShape<T, L>;
-    const size_t sm = XPipeSmem<T, L, typename Cplx<T>::type>::bytes(S::TR * in_rs);
+    const size_t sm = 2 * xinv_slot_bytes<T, L>(in_rs) + 2 * sizeof(uint64_t);
     cudaError_t e = allow_smem<k_x_inv_tma<T, L, P1>>(sm);
     if (e != cudaSuccess) return e;
     const int ntiles = (nrows + S::TR - 1) / S::TR;
     const int cap = sm_count() * resident_ctas<k_x_inv_tma<T, L, P1>>(S::NT, sm);
     k_x_inv_tma<T, L, P1><<<ntiles < cap ? ntiles : cap, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, ntiles);
+    return cudaGetLastError();
+}
+}  // namespace
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, through the runtime's entry-point lookup
+// (no link against the driver library). nullptr if unavailable.
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Map of the y pass input: nslabs slabs of nin rows of width complex values
+// (row pitch irs, slab pitch iss complex), seen as reals; box 2 TC reals x BR
+// rows x 1 slab. Cached for the last arguments (one per element type and L).
+template <typename T, int L>
+bool y_input_map(CUtensorMap *out, const typename Cplx<T>::type *in, int width, int nin, int nslabs, int64_t irs,
+                 int64_t iss, int BR)
+{
+    static CUtensorMap cache;
+    static const void *k_in = nullptr;
+    static int64_t k_key[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t key[6] = {width, nin, nslabs, irs, iss, BR};
+    if (k_in == in && memcmp(key, k_key, sizeof key) == 0) {
+        *out = cache;
+        return true;
+    }
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    using C = typename Cplx<T>::type;
+    constexpr int TC = Col3Shape<T, L>::TC;
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * width, (cuuint64_t)nin, (cuuint64_t)nslabs};
+    const cuuint64_t strides[2] = {(cuuint64_t)irs * sizeof(C), (cuuint64_t)iss * sizeof(C)};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * TC), (cuuint32_t)BR, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (enc(&cache, dt, 3, const_cast<void *>(static_cast<const void *>(in)), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        k_in = nullptr;
+        return false;
+    }
+    k_in = in;
+    memcpy(k_key, key, sizeof key);
+    *out = cache;
+    return true;
+}
+
+// Pipelined pruned forward column pass (TMA tensor copies); returns
+// cudaErrorNotSupported when the arguments do not allow it (caller falls back).
+template <typename T, int L>
+cudaError_t col_fwd_tma(const typename Cplx<T>::type *in, typename Cplx<T>::type *out, int ncols, int width,
+                        int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, const typename Cplx<T>::type *tw,
+                        int twstride, cudaStream_t st)
+{
+    using C = typename Cplx<T>::type;
+    using S = Col3Shape<T, L>;
+    if (width <= 0 || ncols % width != 0 || nin < 1 || 2 * nin > L) return cudaErrorNotSupported;
+    if (((uintptr_t)in & 15) || (irs * (int64_t)sizeof(C)) % 16 || (iss * (int64_t)sizeof(C)) % 16)
+        return cudaErrorNotSupported;
+    const int nslabs = ncols / width;
+    const int BR = nin <= 256 ? nin : 256;
+    const int nb = (nin + BR - 1) / BR;
+    CUtensorMap map;
+    if (!y_input_map<T, L>(&map, in, width, nin, nslabs, irs, iss, BR)) return cudaErrorNotSupported;
+    const size_t ex = ((size_t)swsize(L * S::TC) * sizeof(C) + 127) / 128 * 128;
+    const size_t inb = ((size_t)nb * BR * S::TC * sizeof(C) + 127) / 128 * 128;
+    const size_t sm = 128 + ex + 2 * inb + 2 * sizeof(uint64_t);
+    if (sm > 227 * 1024) return cudaErrorNotSupported;  // e.g. FP64 at L = 1024 with more than 256 rows
+    cudaError_t e = allow_smem<k_col_tma_fwd<T, L>>(sm);
+    if (e != cudaSuccess) return e;
+    const int ntiles = ((width + S::TC - 1) / S::TC) * nslabs;
+    const int cap = sm_count() * resident_ctas<k_col_tma_fwd<T, L>>(S::NT, sm);
+    k_col_tma_fwd<T, L><<<ntiles < cap ? ntiles : cap, S::NT, sm, st>>>(map, out, width, nslabs, nin, BR, nb, oss,
+                                                                         ors, tw, twstride);
     return cudaGetLastError();
 }
 }  // namespace
@@ -201,7 +295,9 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
     case LL:                                                                                   \
         return p1 ? x_inv_pipe<T, LL, true>(in, (int)in_rs, nrows, nvalid, o, twx, st)         \
                   : x_inv_pipe<T, LL, false>(in, (int)in_rs, nrows, nvalid, o, twx, st);
-        switch (L) { DEMAG_PIPE(64) DEMAG_PIPE(128) DEMAG_PIPE(256) DEMAG_PIPE(512) default: break; }
+        // (L = 512 would hold a whole 32-point stage in registers across the
+        // buffer hand-over: one CTA per SM; the one-tile kernel serves it)
+        switch (L) { DEMAG_PIPE(64) DEMAG_PIPE(128) DEMAG_PIPE(256) default: break; }
 #undef DEMAG_PIPE
     }
     if (L >= 64) {
@@ -273,6 +369,13 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
     }
     // the zero padding halves the input (forward) or the output (inverse)
     const bool pin = 2 * nin <= L, pout = 2 * nout <= L;
+    // variant 3: forward by the TMA pipeline, inverse as variant 2
+    if (variant == 3 && !inv && pin && nout == L && (L == 512 || L == 1024)) {
+        const cudaError_t e = L == 512 ? col_fwd_tma<T, 512>(in, out, ncols, width, iss, irs, nin, oss, ors, tw, twstride, st)
+                                       : col_fwd_tma<T, 1024>(in, out, ncols, width, iss, irs, nin, oss, ors, tw, twstride, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
+    if (variant == 3) variant = 2;
     if (variant == 2 && (L == 512 || L == 1024) && (pin || pout) && !(pin && inv) && !(pout && !inv)) {
 #define DEMAG_C3(LL)                                                                                    \
     if (L == LL) {                                                                                      \

@@ -6,6 +6,8 @@
 // and 16-byte multiples (the field passes of plans with nx % 4 == 0 for the
 // forward pass; always for the inverse pass, whose rows are Kxp complex).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the map is built on the host, see passes_impl.cuh)
+
 #include "fft2.cuh"
 
 namespace demag {
@@ -90,6 +92,17 @@ struct XPipeSmem {
     }
 };
 
+// One buffer of the inverse pass: a tile of TR rows of in_rs complex, or the
+// tile's exchange rows [TR][RS], whichever is larger (16-byte multiple).
+template <typename T, int L>
+__host__ __device__ inline size_t xinv_slot_bytes(int in_rs)
+{
+    using S = XShape<T, L>;
+    const size_t a = (size_t)S::TR * in_rs * sizeof(typename Cplx<T>::type);
+    const size_t b = (size_t)S::TR * S::RS * sizeof(typename Cplx<T>::type);
+    return ((a > b ? a : b) + 15) / 16 * 16;
+}
+
 // Issue the bulk copy of tile t (rows [t TR, min((t+1) TR, nrows)) of
 // rowlen elements, contiguous in global memory) into buffer b.
 template <typename E>
@@ -103,12 +116,13 @@ __device__ __forceinline__ void xpipe_issue(const E *src, int rowlen, int nrows,
     bulk_g2s(buf, src + (int64_t)r0 * rowlen, bytes, bar);
 }
 
-// Error exit: wait (bounded) for copies this CTA still has in flight, flag
-// the failure for the host.
-__device__ __forceinline__ void xpipe_abort(uint64_t *bars, int next_i, int gridstep, int ntiles)
+// Error exit at the wait of iteration first_i: the copies of tiles first_i
+// and first_i + 1 may still be in flight; wait for them (bounded) so that no
+// copy lands after the CTA exits, and flag the failure for the host.
+__device__ __forceinline__ void xpipe_abort(uint64_t *bars, int first_i, int gridstep, int ntiles)
 {
     if (threadIdx.x == 0) {
-        for (int i = next_i; i < next_i + 2; ++i) {
+        for (int i = first_i; i < first_i + 2; ++i) {
             const int t = blockIdx.x + i * gridstep;
             if (t < ntiles) mbar_wait_bounded(&bars[i & 1], (unsigned)((i >> 1) & 1), kPipeWaitCycles);
         }
@@ -153,7 +167,7 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
         if (!mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1), kPipeWaitCycles)) s_fail = 1;
         __syncthreads();
         if (s_fail) {
-            xpipe_abort(bars, i + 1, step, ntiles);
+            xpipe_abort(bars, i, step, ntiles);
             return;
         }
         const int row0 = t * TR;
@@ -219,7 +233,11 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
 
 // Inverse C2R rows with the XOut epilogue (energy partials per tile into
 // partials[t]); input rows of in_rs complex (even) stored back to back.
-// P1 as in k_x_inv2 (one output pair beyond the half length).
+// P1 as in k_x_inv2 (one output pair beyond the half length). Each of the two
+// buffers first receives a tile by bulk copy and then, once stage 1 has read
+// it into registers, serves as that tile's exchange rows, so a CTA needs two
+// buffers in all and three CTAs fit on an SM; the buffer is refilled with the
+// tile after next when stage 2 is done with it.
 template <typename T, int L, bool P1>
 __global__ void __launch_bounds__(Tile2<T>::NT)
 k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows, int nvalid, XOut<T> o,
@@ -229,11 +247,9 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
     using S = XShape<T, L>;
     constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TR = S::TR, RS = S::RS;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C *sm = reinterpret_cast<C *>(smraw);
-    const size_t inb = ((size_t)TR * in_rs * sizeof(C) + 15) / 16 * 16;
-    C *buf[2] = {reinterpret_cast<C *>(smraw + (size_t)TR * RS * sizeof(C)),
-                 reinterpret_cast<C *>(smraw + (size_t)TR * RS * sizeof(C) + inb)};
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + (size_t)TR * RS * sizeof(C) + 2 * inb);
+    const size_t slot = xinv_slot_bytes<T, L>(in_rs);
+    C *buf[2] = {reinterpret_cast<C *>(smraw), reinterpret_cast<C *>(smraw + slot)};
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + 2 * slot);
     __shared__ int s_fail;
     if (threadIdx.x == 0) {
         s_fail = 0;
@@ -257,17 +273,18 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
         if (!mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1), kPipeWaitCycles)) s_fail = 1;
         __syncthreads();
         if (s_fail) {
-            xpipe_abort(bars, i + 1, step, ntiles);
+            xpipe_abort(bars, i, step, ntiles);
             return;
         }
         const int row0 = t * TR;
-        if (threadIdx.x < TR * R2) {
-            const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
-            C u[R1];
+        const bool act1 = threadIdx.x < TR * R2;
+        const int rr1 = threadIdx.x / R2, j1 = threadIdx.x % R2;
+        C u[R1];
+        if (act1) {
 #pragma unroll
             for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
-            if (row < nrows) {
-                const C *p = buf[b] + rr * in_rs;
+            if (row0 + rr1 < nrows) {
+                const C *p = buf[b] + rr1 * in_rs;
 #pragma unroll
                 for (int r = 0; r < R1; ++r) {
                     const int k = j1 + r * R2;
@@ -280,18 +297,15 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
                 }
             }
             RegDFT<R1, true, C>::run(u);
-            C *s = sm + rr * RS;
+        }
+        __syncthreads();  // the tile is in registers: the buffer becomes the exchange rows
+        C *sm = buf[b];
+        if (act1) {
+            C *s = sm + rr1 * RS;
 #pragma unroll
             for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const int tn = blockIdx.x + (i + 2) * step;
-            if (tn < ntiles) {
-                fence_proxy_async_smem();
-                xpipe_issue(in, in_rs, nrows, TR, tn, buf[b], &bars[b]);
-            }
-        }
         T acc = 0;
         if (threadIdx.x < TR * R1) {
             const int rr = threadIdx.x / R1, j2 = threadIdx.x % R1, row = row0 + rr;
@@ -309,19 +323,139 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
                     const int n = j2 + r * R1;
                     const T hv[2] = {v[r].x * o.scale, v[r].y * o.scale};
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int x = 2 * n + u;
+                    for (int uu = 0; uu < 2; ++uu) {
+                        const int x = 2 * n + uu;
                         if (x >= nvalid) continue;
                         const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
                         const int64_t idx = (int64_t)row * o.out_rs + x;
-                        if (o.out) o.out[idx] = hv[u] * oscale * w;
-                        if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
+                        if (o.out) o.out[idx] = hv[uu] * oscale * w;
+                        if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[uu];
                     }
                 }
             }
         }
-        if (o.partials) block_partial<NT>((double)acc, o.partials, t);  // has its own barriers
+        if (o.partials) block_partial<NT>((double)acc, o.partials, t);  // has its own barrier
+        __syncthreads();  // exchange rows read: the buffer can take the tile after next
+        if (threadIdx.x == 0) {
+            const int tn = blockIdx.x + (i + 2) * step;
+            if (tn < ntiles) {
+                fence_proxy_async_smem();
+                xpipe_issue(in, in_rs, nrows, TR, tn, buf[b], &bars[b]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ y forward pass
+// Tiled 3-D tensor copy (TMA) of box `coords` of the map into shared memory,
+// completing as transactions on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Pruned forward column transform (the y pass: nin <= L/2 rows in, all L rows
+// out) by persistent CTAs: each tile of TC columns of one slab arrives by
+// TMA tensor copies (box: 2 TC reals wide, BR rows, one slab; nb boxes stacked
+// in rows) into one of two buffers while the previous tile is transformed in
+// the three-stage layout of k_col3; two tiles in flight per CTA. Columns past
+// the slab's width and rows past nin arrive as zeros (out-of-bounds fill).
+template <typename T, int L>
+__global__ void __launch_bounds__(Col3Shape<T, L>::NT, L >= 1024 ? 2 : 3)
+k_col_tma_fwd(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *__restrict__ out, int width, int nslabs,
+              int nin, int BR, int nb, int64_t oss, int64_t ors, const typename Cplx<T>::type *__restrict__ tw,
+              int twstride)
+{
+    using C = typename Cplx<T>::type;
+    using S = Col3Shape<T, L>;
+    constexpr int R1 = S::R1, R2 = S::R2, R3 = S::R3, NT = S::NT, TC = S::TC;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    // tensor-copy destinations 128-byte aligned (the launch adds 128 bytes of slack)
+    unsigned char *base = smraw + ((128 - (smem_u32(smraw) & 127)) & 127);
+    C *sm = reinterpret_cast<C *>(base);
+    const size_t ex = ((size_t)swsize(L * TC) * sizeof(C) + 127) / 128 * 128;
+    const unsigned tile_bytes = (unsigned)((size_t)nb * BR * TC * sizeof(C));  // whole boxes, fill included
+    const size_t inb = ((size_t)tile_bytes + 127) / 128 * 128;
+    C *buf[2] = {reinterpret_cast<C *>(base + ex), reinterpret_cast<C *>(base + ex + inb)};
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + ex + 2 * inb);
+    __shared__ int s_fail;
+    const int tps = (width + TC - 1) / TC;
+    const int ntiles = tps * nslabs;
+    auto issue = [&](int t, int bsel) {
+        const int slab = t / tps, x = 2 * (t - slab * tps) * TC;
+        mbar_expect_tx(&bars[bsel], tile_bytes);
+        for (int k = 0; k < nb; ++k)
+            tma_load_3d(buf[bsel] + (size_t)k * BR * TC, &map, x, k * BR, slab, &bars[bsel]);
+    };
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int step = gridDim.x;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 2; ++i)
+            if (blockIdx.x + i * step < ntiles) issue(blockIdx.x + i * step, i);
+    for (int i = 0;; ++i) {
+        const int t = blockIdx.x + i * step;
+        if (t >= ntiles) break;
+        const int b = i & 1;
+        if (!mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1), kPipeWaitCycles)) s_fail = 1;
         __syncthreads();
+        if (s_fail) {
+            xpipe_abort(bars, i, step, ntiles);
+            return;
+        }
+        const int slab = t / tps, kx0 = (t - slab * tps) * TC;
+        // stage 1: radix R1 over rows j1 + r L/R1 (r < R1/2 hold data) -> rows j1 R1 + r
+#pragma unroll
+        for (int q = 0; q < (TC * (L / R1) + NT - 1) / NT; ++q) {
+            const int bq = threadIdx.x + q * NT;
+            if (bq < TC * (L / R1)) {
+                const int c = bq % TC, j1 = bq / TC;
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r) {
+                    const int row = j1 + r * (L / R1);
+                    if (row < nin) u[r] = buf[b][row * TC + c];
+                }
+                RegDFTHalfIn<R1, false, C>::run(u);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
+            }
+        }
+        __syncthreads();  // buffer b consumed
+        if (threadIdx.x == 0 && t + 2 * step < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2 * step, b);
+        }
+        fft_stage<C, L, R2, R1, false, NT, TC>(sm, tw, twstride);
+#pragma unroll
+        for (int q = 0; q < (TC * (L / R3) + NT - 1) / NT; ++q) {
+            const int bq = threadIdx.x + q * NT;
+            if (bq < TC * (L / R3)) {
+                const int c = bq % TC, j = bq / TC, kx = kx0 + c;
+                C v[R3];
+#pragma unroll
+                for (int r = 0; r < R3; ++r) v[r] = sm[sw((j + r * (L / R3)) * TC + c)];
+                twiddle_row<R3, L, false>(v, j, tw, twstride);
+                RegDFT<R3, false, C>::run(v);
+                if (kx < width) {
+                    C *col = out + (int64_t)slab * oss + kx;
+#pragma unroll
+                    for (int r = 0; r < R3; ++r) col[(int64_t)(j + r * (L / R3)) * ors] = v[r];
+                }
+            }
+        }
+        __syncthreads();  // exchange rows read before the next tile rewrites them
     }
 }
 
