@@ -317,7 +317,10 @@ demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, v
 /* Current variant choice, and a way to set it by hand.
  * z: 0 = two-stage fused pass, 1 = half-width tile, 2 = 256-thread tile
  *    (z length 512 only), 3 = persistent pipelined pass (z lengths 64..512),
- *    4 = variant 0's layout on half the columns with two CTAs per SM.
+ *    4 = variant 0's layout on half the columns with two CTAs per SM,
+ *    5 = persistent CTAs whose input columns arrive by TMA tensor copies
+ *    while the previous tile is transformed (z lengths 32..512; the
+ *    autotuner tries it up to 256, where it is the fastest).
  * y: 0 = two-stage column transform, 1 = swapped radix order (y lengths 32,
  *    128, 512), 2 = three-stage transform with more CTAs per SM (y lengths
  *    512 and 1024), 3 = as 2, with the forward pass by persistent CTAs that

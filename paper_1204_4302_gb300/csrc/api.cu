@@ -1002,6 +1002,7 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     if (dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
     if (dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
     if (dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(4);   // half tile, two CTAs per SM
+    if (dm && p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input
     if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
     if (p->Py == 512 || p->Py == 1024) ys.push_back(2);  // three-stage, more CTAs per SM
     if (p->Py == 512 || p->Py == 1024) ys.push_back(3);  // forward pass by the TMA pipeline
@@ -1062,7 +1063,7 @@ demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
 
 demag_status demag_set_variants(demag_plan_t p, int z, int y)
 {
-    if (!p || z < 0 || z > 4 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
+    if (!p || z < 0 || z > 5 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->zvariant = z;
     p->yvariant = y;
     return DEMAG_OK;

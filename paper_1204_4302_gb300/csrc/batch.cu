@@ -421,7 +421,21 @@ demag_status build_persistent(demag_batch *b)
     if (cudaMalloc(&b->derror, sizeof(int)) != cudaSuccess) return bfail(DEMAG_ERR_OOM, "batch flag");
     cudaMemset(b->derror, 0, sizeof(int));
     cudaMemcpy(b->dstart, b->hstart.data(), sizeof(int) * b->hstart.size(), cudaMemcpyHostToDevice);
-    e = cudaFuncSetAttribute(demag::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // opt in to the whole per-block shared memory (other batches launch the
+    // same kernel with other sizes; the occupancy follows each launch's size)
+    {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, demag::k_batch);
+        if (e == cudaSuccess && smem + fa.sharedSizeBytes > (size_t)optin) {
+            b->why_not_persistent = "the persistent kernel's shared memory exceeds the per-block limit";
+            return DEMAG_OK;
+        }
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(demag::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+    }
     if (e != cudaSuccess) return bfail(DEMAG_ERR_CUDA, std::string("batch kernel smem: ") + cudaGetErrorString(e));
     int per_sm = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, demag::k_batch, demag::kThreads, smem);

@@ -31,18 +31,28 @@ int sm_count()
 template <auto Kern>
 cudaError_t allow_smem(size_t bytes)
 {
+    // Opt the kernel in to the device's whole per-block shared memory once per
+    // device (launch sizes can differ from call to call); the occupancy still
+    // follows the size each launch asks for.
     const auto kern = Kern;
     static int done_for = -1;
+    static size_t limit = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (done_for == dev) return cudaSuccess;
-    if (bytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
+    if (done_for != dev) {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        const size_t dyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        if (dyn > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
+            return e;
+        limit = dyn > 48 * 1024 ? dyn : 48 * 1024;
+        done_for = dev;
     }
-    done_for = dev;
-    return cudaSuccess;
+    return bytes <= limit ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -207,6 +217,68 @@ cudaError_t col_fwd_tma(const typename Cplx<T>::type *in, typename Cplx<T>::type
     const int cap = sm_count() * resident_ctas<k_col_tma_fwd<T, L>>(S::NT, sm);
     k_col_tma_fwd<T, L><<<ntiles < cap ? ntiles : cap, S::NT, sm, st>>>(map, out, width, nslabs, nin, BR, nb, oss,
                                                                          ors, tw, twstride);
+    return cudaGetLastError();
+}
+}  // namespace
+
+namespace {
+// Map of the z pass input S2 [3][nz][Py][Kxp] complex seen as reals: dims
+// (2 Kx, Py, nz, 3), box (2 TC, 1, nz, 3): one copy per tile. Cached for the
+// last arguments (one per element type and L).
+template <typename T, int L>
+bool z_input_map(CUtensorMap *out, const typename Cplx<T>::type *S, int Kx, int Py, int nz, int64_t ss, int64_t rs,
+                 int64_t cs)
+{
+    static CUtensorMap cache;
+    static const void *k_S = nullptr;
+    static int64_t k_key[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t key[6] = {Kx, Py, nz, ss, rs, cs};
+    if (k_S == S && memcmp(key, k_key, sizeof key) == 0) {
+        *out = cache;
+        return true;
+    }
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    using C = typename Cplx<T>::type;
+    constexpr int TC = ZShape<T, L, ZTmaV<L>::V>::TC;
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * Kx, (cuuint64_t)Py, (cuuint64_t)nz, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)ss * sizeof(C), (cuuint64_t)rs * sizeof(C), (cuuint64_t)cs * sizeof(C)};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * TC), 1, (cuuint32_t)nz, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (enc(&cache, dt, 4, const_cast<void *>(static_cast<const void *>(S)), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        k_S = nullptr;
+        return false;
+    }
+    k_S = S;
+    memcpy(k_key, key, sizeof key);
+    *out = cache;
+    return true;
+}
+
+template <typename T, int L>
+cudaError_t zconv_tma(typename Cplx<T>::type *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                      const T *nhat, int Py, int Kx, const typename Cplx<T>::type *tw, int twstride, cudaStream_t st)
+{
+    using C = typename Cplx<T>::type;
+    using Sh = ZShape<T, L, ZTmaV<L>::V>;
+    if (twstride != 1 || width != Kx || ncols != Py * Kx || nrows < 1 || 2 * nrows > L || cs != (int64_t)nrows * rs ||
+        ((uintptr_t)S & 15) || (ss * (int64_t)sizeof(C)) % 16 || (rs * (int64_t)sizeof(C)) % 16)
+        return cudaErrorNotSupported;
+    CUtensorMap map;
+    if (!z_input_map<T, L>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
+    const size_t stg = ((size_t)3 * nrows * Sh::TC * sizeof(C) + 127) / 128 * 128;
+    const size_t sm = 128 + stg + 3 * swsize(L * Sh::TC) * sizeof(C) + (L / 2 + 1) * 6 * Sh::TC * sizeof(T) + 8;
+    if (sm > 227 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = allow_smem<k_z_conv_tma<T, L>>(sm);
+    if (e != cudaSuccess) return e;
+    const int ntr = (Kx + Sh::TC - 1) / Sh::TC;
+    const int ntiles = ntr * Py;
+    const int cap = sm_count();
+    k_z_conv_tma<T, L><<<ntiles < cap ? ntiles : cap, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, nhat, tw,
+                                                                         ntr, ntiles);
     return cudaGetLastError();
 }
 }  // namespace
@@ -448,6 +520,19 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant)
 {
+    if (variant == 5 && ncols > 0 && 2 * nrows <= L) {
+        cudaError_t e = cudaErrorNotSupported;
+        switch (L) {
+        case 32: e = zconv_tma<T, 32>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st); break;
+        case 64: e = zconv_tma<T, 64>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st); break;
+        case 128: e = zconv_tma<T, 128>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st); break;
+        case 256: e = zconv_tma<T, 256>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st); break;
+        case 512: e = zconv_tma<T, 512>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st); break;
+        default: break;
+        }
+        if (e != cudaErrorNotSupported) return e;
+        variant = 0;
+    }
     if (variant == 3 && ncols > 0 && 2 * nrows <= L) {
         switch (L) {
         case 64: return zconv_pipe<64>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);

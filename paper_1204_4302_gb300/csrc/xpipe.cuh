@@ -459,4 +459,212 @@ k_col_tma_fwd(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *_
     }
 }
 
+// ------------------------------------------------------------ z pass (DM)
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The tensor block of the columns kx0 .. kx0 + TC - 1 of spectral row ky (as
+// tensor_block_prefetch, for row-aligned tiles).
+template <typename T, int TC, int NT, int NC, int HZ>
+__device__ __forceinline__ void tensor_block_prefetch_row(T *smT, const T *__restrict__ tab, int ky, int kx0, int Kx,
+                                                          int Py, int64_t plane, int tid)
+{
+    constexpr int G = NT / TC, GQ = G / NC, GR = G % NC;
+    const int c = tid % TC, g = tid / TC, kx = kx0 + c;
+    if (kx >= Kx) return;
+    const int kyf = ky > Py / 2 ? Py - ky : ky;
+    const int64_t zs = (int64_t)(Py / 2 + 1) * Kx;
+    const T *src = tab + (int64_t)kyf * Kx + kx;
+    int comp = g % NC;
+    int64_t off = comp * plane + (int64_t)(g / NC) * zs;
+    const int64_t step = GQ * zs + GR * plane, wrap = zs - NC * plane;
+    for (int idx = g; idx < HZ * NC; idx += G) {
+        cp_async_elem(&smT[idx * TC + c], src + off);
+        comp += GR;
+        off += step;
+        if (comp >= NC) {
+            comp -= NC;
+            off += wrap;
+        }
+    }
+}
+
+// Fused z pass by persistent CTAs with the input columns staged by TMA:
+// tiles are TC consecutive kx of one spectral row ky (rows taken in fold-pair
+// order); a tile's three components (nrows z-rows each) arrive in one 4-D
+// tensor copy while the previous tile's forward stage 2, product and inverse
+// run, and its tensor block is copied (cp.async) during the previous tile's
+// inverse stage. Arithmetic as k_z_conv2.
+// Thread layout of the TMA z pass: as k_z_conv2 variant 0, except at L = 512
+// where the 256-thread layout (variant 2) leaves the persistent loop enough
+// registers.
+template <int L> struct ZTmaV { static constexpr int V = 0; };
+
+template <typename T, int L>
+__global__ void __launch_bounds__(ZShape<T, L, ZTmaV<L>::V>::NT, 1)
+k_z_conv_tma(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *__restrict__ S, int Kx, int Py,
+             int64_t ss, int64_t rs, int64_t cs, int nrows, const T *__restrict__ nhat,
+             const typename Cplx<T>::type *__restrict__ tw, int ntr, int ntiles)
+{
+    using C = typename Cplx<T>::type;
+    using Sh = ZShape<T, L, ZTmaV<L>::V>;
+    constexpr int R1 = Sh::R1, R2 = Sh::R2, NT = Sh::NT, TC = Sh::TC;
+    constexpr int TS = swsize(L * TC);
+    constexpr int NB1 = TC * R2;
+    constexpr int HZ = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned char *base = smraw + ((128 - (smem_u32(smraw) & 127)) & 127);
+    const unsigned in_bytes = (unsigned)(3u * nrows * TC * sizeof(C));
+    const size_t stg_bytes = ((size_t)in_bytes + 127) / 128 * 128;
+    C *stg = reinterpret_cast<C *>(base);               // [3][nrows][TC]
+    C *sm = reinterpret_cast<C *>(base + stg_bytes);    // exchange [3][TS]
+    T *smT = reinterpret_cast<T *>(sm + 3 * TS);        // tensor block [HZ][6][TC]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smT + HZ * 6 * TC);
+    __shared__ int s_fail;
+    const int hy = Py / 2 + 1;
+    const int64_t plane = (int64_t)HZ * hy * Kx;
+    auto tile_ky = [&](int t) { return ky_pair_order(t / ntr, Py); };
+    auto tile_kx0 = [&](int t) { return (t % ntr) * TC; };
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int t = blockIdx.x;
+    if (t < ntiles) {
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(bar, in_bytes);
+            tma_load_4d(stg, &map, 2 * tile_kx0(t), tile_ky(t), 0, 0, bar);
+        }
+        tensor_block_prefetch_row<T, TC, NT, 6, HZ>(smT, nhat, tile_ky(t), tile_kx0(t), Kx, Py, plane, threadIdx.x);
+    }
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int next = t + gridDim.x;
+        const int ky = tile_ky(t), kx0 = tile_kx0(t);
+        if (!mbar_wait_bounded(bar, (unsigned)(k & 1), kPipeWaitCycles)) s_fail = 1;
+        cp_async_wait_all();
+        __syncthreads();
+        if (s_fail) {
+            if (threadIdx.x == 0) atomicExch(&g_xpipe_error, 1);
+            return;  // only this tile's copy was in flight, and it gave up
+        }
+        // forward stage 1 from the staged rows: rows j1 + r R2 -> rows j1 R1 + r
+#pragma unroll
+        for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+            const int b = threadIdx.x + q * NT;
+            if (b < 3 * NB1) {
+                const int comp = b / NB1, bb = b - comp * NB1;
+                const int c = bb % TC, j1 = bb / TC;
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+                const C *col = stg + ((size_t)comp * nrows + j1) * TC + c;
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r)
+                    if (j1 + r * R2 < nrows) u[r] = col[r * R2 * TC];
+                RegDFTHalfIn<R1, false, C>::run(u);
+                C *s = sm + comp * TS + sw(j1 * R1 * TC + c);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
+            }
+        }
+        __syncthreads();  // staging buffer consumed
+        if (threadIdx.x == 0 && next < ntiles) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, in_bytes);
+            tma_load_4d(stg, &map, 2 * tile_kx0(next), tile_ky(next), 0, 0, bar);
+        }
+        const bool act2 = threadIdx.x < TC * R1;
+        const int c2 = threadIdx.x % TC, j2 = threadIdx.x / TC;
+        C v0[R2], v1[R2], v2[R2];
+        if (act2) {
+            const C *s = sm + sw(j2 * TC + c2);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                constexpr int step = R1 * TC + (R1 * TC) / 32;
+                v0[r] = s[r * step];
+                v1[r] = s[TS + r * step];
+                v2[r] = s[2 * TS + r * step];
+            }
+#pragma unroll
+            for (int r = 1; r < R2; ++r) {
+                const C w = __ldg(&tw[r * j2]);
+                v0[r] = cmul(v0[r], w);
+                v1[r] = cmul(v1[r], w);
+                v2[r] = cmul(v2[r], w);
+            }
+            RegDFT<R2, false, C>::run(v0);
+            RegDFT<R2, false, C>::run(v1);
+            RegDFT<R2, false, C>::run(v2);
+            const T sy = ky > Py / 2 ? (T)-1 : (T)1;
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                const int kz = j2 + r * R1;
+                const bool up = kz > L / 2;
+                const int kzf = up ? L - kz : kz;
+                const T sz = up ? (T)-1 : (T)1;
+                const T *tt = smT + kzf * 6 * TC + c2;
+                const T nxx = tt[0], nyy = tt[TC], nzz = tt[2 * TC];
+                const T nxy = sy * tt[3 * TC], nxz = sz * tt[4 * TC], nyz = sy * sz * tt[5 * TC];
+                const C mx = v0[r], my = v1[r], mz = v2[r];
+                v0[r] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+                v1[r] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+                v2[r] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+            }
+            RegDFT<R2, true, C>::run(v0);
+            RegDFT<R2, true, C>::run(v1);
+            RegDFT<R2, true, C>::run(v2);
+        }
+        __syncthreads();  // exchange and tensor block read
+        if (next < ntiles)
+            tensor_block_prefetch_row<T, TC, NT, 6, HZ>(smT, nhat, tile_ky(next), tile_kx0(next), Kx, Py, plane,
+                                                        threadIdx.x);
+        if (act2) {
+            C *s = sm + sw(j2 * R2 * TC + c2);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                const int o = r * TC + (r * TC) / 32;
+                s[o] = v0[r];
+                s[TS + o] = v1[r];
+                s[2 * TS + o] = v2[r];
+            }
+        }
+        __syncthreads();
+        // inverse stage 2: radix R1 over rows j1 + r R2, rows < nrows stored
+#pragma unroll
+        for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+            const int b = threadIdx.x + q * NT;
+            if (b < 3 * NB1) {
+                const int comp = b / NB1, bb = b - comp * NB1;
+                const int c = bb % TC, j1 = bb / TC, kx = kx0 + c;
+                const C *s = sm + comp * TS + sw(j1 * TC + c);
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    constexpr int step = R2 * TC + (R2 * TC) / 32;
+                    u[r] = s[r * step];
+                }
+#pragma unroll
+                for (int r = 1; r < R1; ++r) u[r] = cmulc(u[r], __ldg(&tw[r * j1]));
+                RegDFTHalfOut<R1, true, C>::run(u);
+                if (kx < Kx) {
+                    C *col = S + (int64_t)ky * ss + kx + comp * cs + j1 * rs;
+#pragma unroll
+                    for (int r = 0; r < R1 / 2; ++r)
+                        if (j1 + r * R2 < nrows) col[(int64_t)r * R2 * rs] = u[r];
+                }
+            }
+        }
+        __syncthreads();  // exchange rows read before the next tile writes them
+    }
+}
+
 }  // namespace demag
