@@ -306,7 +306,7 @@ demag_status run_field_sp(demag_plan *p, const FieldJob &job, cudaStream_t st)
     p->launches++;
     tm.mark();
     e = Passes<T>::sp_zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nz + 1, that, Py,
-                            Kx, twz, phx, phy, phz, st);
+                            Kx, twz, phx, phy, phz, st, p->zvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("SP z pass: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -1002,7 +1002,7 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     if (dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
     if (dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
     if (dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(4);   // half tile, two CTAs per SM
-    if (dm && p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input
+    if (p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input (DM and SP)
     if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
     if (p->Py == 512 || p->Py == 1024) ys.push_back(2);  // three-stage, more CTAs per SM
     if (p->Py == 512 || p->Py == 1024) ys.push_back(3);  // forward pass by the TMA pipeline

@@ -281,6 +281,38 @@ cudaError_t zconv_tma(typename Cplx<T>::type *S, int ncols, int width, int64_t s
                                                                          ntr, ntiles);
     return cudaGetLastError();
 }
+template <typename T, int L>
+cudaError_t sp_zconv_tma(typename Cplx<T>::type *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+                         int nrows, int nout, const T *that, int Py, int Kx, const typename Cplx<T>::type *tw,
+                         const typename Cplx<T>::type *phx, const typename Cplx<T>::type *phy,
+                         const typename Cplx<T>::type *phz, cudaStream_t st)
+{
+    using C = typename Cplx<T>::type;
+    using Sh = ZShape<T, L, 0>;
+    if (width != Kx || ncols != Py * Kx || nrows < 1 || 2 * nrows > L || cs != (int64_t)nrows * rs ||
+        ((uintptr_t)S & 15) || (ss * (int64_t)sizeof(C)) % 16 || (rs * (int64_t)sizeof(C)) % 16)
+        return cudaErrorNotSupported;
+    CUtensorMap map;
+    if (!z_input_map<T, L>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
+    const size_t stg = ((size_t)3 * nrows * Sh::TC * sizeof(C) + 127) / 128 * 128;
+    const size_t sm = 128 + stg + 3 * swsize(L * Sh::TC) * sizeof(C) +
+                      (size_t)(((L / 2 + 1) * 3 * Sh::TC + 1) / 2 * 2) * sizeof(T) + 8;
+    if (sm > 227 * 1024) return cudaErrorNotSupported;
+    const int ntr = (Kx + Sh::TC - 1) / Sh::TC;
+    const int ntiles = ntr * Py;
+    const int grid = ntiles < sm_count() ? ntiles : sm_count();
+    cudaError_t e;
+    if (2 * nout <= L) {
+        if ((e = allow_smem<k_sp_z_tma<T, L, true>>(sm)) != cudaSuccess) return e;
+        k_sp_z_tma<T, L, true><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, nout, that, tw, phx, phy,
+                                                          phz, ntr, ntiles);
+    } else {
+        if ((e = allow_smem<k_sp_z_tma<T, L, false>>(sm)) != cudaSuccess) return e;
+        k_sp_z_tma<T, L, false><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, nout, that, tw, phx, phy,
+                                                           phz, ntr, ntiles);
+    }
+    return cudaGetLastError();
+}
 }  // namespace
 
 template <typename T>
@@ -576,11 +608,22 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
 template <typename T>
 cudaError_t Passes<T>::sp_zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
                                 int nout, const T *that, int Py, int Kx, const C *tw, const C *phx, const C *phy,
-                                const C *phz, cudaStream_t st)
+                                const C *phz, cudaStream_t st, int variant)
 {
     if (ncols <= 0) return cudaSuccess;
     // zero padding: nz + 1 node rows out of L >= 2 nz
     if (L < 2 || 2 * nrows > L || nout != nrows + 1 || cs != (int64_t)nrows * rs) return cudaErrorInvalidValue;
+    if (variant == 5) {
+        cudaError_t e = cudaErrorNotSupported;
+        switch (L) {
+        case 32: e = sp_zconv_tma<T, 32>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz, st); break;
+        case 64: e = sp_zconv_tma<T, 64>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz, st); break;
+        case 128: e = sp_zconv_tma<T, 128>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz, st); break;
+        case 256: e = sp_zconv_tma<T, 256>(S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz, st); break;
+        default: break;
+        }
+        if (e != cudaErrorNotSupported) return e;
+    }
     if (L <= 16) {
         const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
 #define DEMAG_CASE(LL)                                                                         \

@@ -82,7 +82,7 @@ template <typename T> struct Passes {
     // spectrum out, nout = nz + 1 node rows) and the finite-difference field
     static cudaError_t sp_zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                                 int nrows, int nout, const T *that, int Py, int Kx, const C *tw,
-                                const C *phx, const C *phy, const C *phz, cudaStream_t st);
+                                const C *phx, const C *phy, const C *phz, cudaStream_t st, int variant = 0);
     static cudaError_t sp_grad(const T *phi, int nx, int ny, int nz, double dx, double dy, double dz, T *H,
                                const T *Mref, double *partials, cudaStream_t st);
     static int sp_grad_blocks(int nx, int ny, int nz);

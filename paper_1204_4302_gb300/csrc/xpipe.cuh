@@ -667,4 +667,164 @@ k_z_conv_tma(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *__
     }
 }
 
+// ------------------------------------------------------------ z pass (SP)
+// Persistent SP z pass with TMA-staged input columns: as k_z_conv_tma for
+// the three forward transforms; the product forms the potential spectrum
+// (sp_product with the half-cell phase) and one inverse transform writes the
+// nout = nz + 1 node planes over component 0 of the tile's own columns (the
+// last plane lands in component 1's first plane, which only this tile reads,
+// and it has been read). POUT: nout <= L/2.
+template <typename T, int L, bool POUT>
+__global__ void __launch_bounds__(ZShape<T, L, 0>::NT, 1)
+k_sp_z_tma(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *__restrict__ S, int Kx, int Py,
+           int64_t ss, int64_t rs, int64_t cs, int nrows, int nout, const T *__restrict__ that,
+           const typename Cplx<T>::type *__restrict__ tw, const typename Cplx<T>::type *__restrict__ phx,
+           const typename Cplx<T>::type *__restrict__ phy, const typename Cplx<T>::type *__restrict__ phz, int ntr,
+           int ntiles)
+{
+    using C = typename Cplx<T>::type;
+    using Sh = ZShape<T, L, 0>;
+    constexpr int R1 = Sh::R1, R2 = Sh::R2, NT = Sh::NT, TC = Sh::TC;
+    constexpr int TS = swsize(L * TC);
+    constexpr int NB1 = TC * R2;
+    constexpr int HZ = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned char *base = smraw + ((128 - (smem_u32(smraw) & 127)) & 127);
+    const unsigned in_bytes = (unsigned)(3u * nrows * TC * sizeof(C));
+    const size_t stg_bytes = ((size_t)in_bytes + 127) / 128 * 128;
+    C *stg = reinterpret_cast<C *>(base);
+    C *sm = reinterpret_cast<C *>(base + stg_bytes);
+    T *smT = reinterpret_cast<T *>(sm + 3 * TS);  // [kzf][3][TC]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smT + ((HZ * 3 * TC + 1) / 2) * 2);
+    __shared__ int s_fail;
+    const int hy = Py / 2 + 1;
+    const int64_t plane = (int64_t)HZ * hy * Kx;
+    auto tile_ky = [&](int t) { return ky_pair_order(t / ntr, Py); };
+    auto tile_kx0 = [&](int t) { return (t % ntr) * TC; };
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int t = blockIdx.x;
+    if (t < ntiles) {
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(bar, in_bytes);
+            tma_load_4d(stg, &map, 2 * tile_kx0(t), tile_ky(t), 0, 0, bar);
+        }
+        tensor_block_prefetch_row<T, TC, NT, 3, HZ>(smT, that, tile_ky(t), tile_kx0(t), Kx, Py, plane, threadIdx.x);
+    }
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int next = t + gridDim.x;
+        const int ky = tile_ky(t), kx0 = tile_kx0(t);
+        if (!mbar_wait_bounded(bar, (unsigned)(k & 1), kPipeWaitCycles)) s_fail = 1;
+        cp_async_wait_all();
+        __syncthreads();
+        if (s_fail) {
+            if (threadIdx.x == 0) atomicExch(&g_xpipe_error, 1);
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < (3 * NB1 + NT - 1) / NT; ++q) {
+            const int b = threadIdx.x + q * NT;
+            if (b < 3 * NB1) {
+                const int comp = b / NB1, bb = b - comp * NB1;
+                const int c = bb % TC, j1 = bb / TC;
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) u[r] = cmk<C>(0, 0);
+                const C *col = stg + ((size_t)comp * nrows + j1) * TC + c;
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r)
+                    if (j1 + r * R2 < nrows) u[r] = col[r * R2 * TC];
+                RegDFTHalfIn<R1, false, C>::run(u);
+                C *s = sm + comp * TS + sw(j1 * R1 * TC + c);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && next < ntiles) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, in_bytes);
+            tma_load_4d(stg, &map, 2 * tile_kx0(next), tile_ky(next), 0, 0, bar);
+        }
+        const bool act2 = threadIdx.x < TC * R1;
+        const int c2 = threadIdx.x % TC, j2 = threadIdx.x / TC;
+        C p[R2];
+        if (act2) {
+            C v0[R2], v1[R2], v2[R2];
+            const C *s = sm + sw(j2 * TC + c2);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                constexpr int step = R1 * TC + (R1 * TC) / 32;
+                v0[r] = s[r * step];
+                v1[r] = s[TS + r * step];
+                v2[r] = s[2 * TS + r * step];
+            }
+#pragma unroll
+            for (int r = 1; r < R2; ++r) {
+                const C w = __ldg(&tw[r * j2]);
+                v0[r] = cmul(v0[r], w);
+                v1[r] = cmul(v1[r], w);
+                v2[r] = cmul(v2[r], w);
+            }
+            RegDFT<R2, false, C>::run(v0);
+            RegDFT<R2, false, C>::run(v1);
+            RegDFT<R2, false, C>::run(v2);
+            const int kx = kx0 + c2;
+            const T sy = ky > Py / 2 ? (T)-1 : (T)1;
+            const C pxy = cmul(__ldg(&phx[kx < Kx ? kx : 0]), __ldg(&phy[ky]));
+            const C cxy = cmk<C>(pxy.y, -pxy.x);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                const int kz = j2 + r * R1;
+                const bool up = kz > L / 2;
+                const int kzf = up ? L - kz : kz;
+                const T sz = up ? (T)-1 : (T)1;
+                const T *tt = smT + kzf * 3 * TC + c2;
+                p[r] = sp_product<T, C>(sy * sz * tt[0], sz * tt[TC], sy * tt[2 * TC], v0[r], v1[r], v2[r],
+                                        cmul(cxy, __ldg(&phz[kz])));
+            }
+            RegDFT<R2, true, C>::run(p);
+        }
+        __syncthreads();
+        if (next < ntiles)
+            tensor_block_prefetch_row<T, TC, NT, 3, HZ>(smT, that, tile_ky(next), tile_kx0(next), Kx, Py, plane,
+                                                        threadIdx.x);
+        if (act2) {
+            C *s = sm + sw(j2 * R2 * TC + c2);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) s[r * TC + (r * TC) / 32] = p[r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < (NB1 + NT - 1) / NT; ++q) {
+            const int b = threadIdx.x + q * NT;
+            if (b < NB1) {
+                const int c = b % TC, j1 = b / TC, kx = kx0 + c;
+                const C *s = sm + sw(j1 * TC + c);
+                C u[R1];
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    constexpr int step = R2 * TC + (R2 * TC) / 32;
+                    u[r] = s[r * step];
+                }
+#pragma unroll
+                for (int r = 1; r < R1; ++r) u[r] = cmulc(u[r], __ldg(&tw[r * j1]));
+                if constexpr (POUT) RegDFTHalfOut<R1, true, C>::run(u);
+                else RegDFT<R1, true, C>::run(u);
+                if (kx < Kx) {
+                    C *col = S + (int64_t)ky * ss + kx + j1 * rs;
+#pragma unroll
+                    for (int r = 0; r < (POUT ? R1 / 2 : R1); ++r)
+                        if (j1 + r * R2 < nout) col[(int64_t)r * R2 * rs] = u[r];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace demag

@@ -215,3 +215,28 @@ def test_sp_full_size_point_sources(n, d):
         p.close()
         del M, H
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [(17, 9, 20), (33, 64, 17), (40, 33, 64), (24, 20, 128), (9, 5, 100)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_sp_tma_z_pass_variant(n, prec):
+    """The persistent SP z pass with TMA-staged columns (z variant 5) gives the
+    one-tile form's field and the oracle's, node rows reaching P/2 included."""
+    from paper_1204_4302_gb300.plan import Plan
+    d = (2e-9, 1.5e-9, 2.5e-9)
+    M = MS * inputs.random_unit(n, seed=3 + sum(n))
+    phi_ref = oracle.sp_potential_fft(M, d)
+    H_ref = oracle.sp_field_from_potential(phi_ref, d)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    p = Plan(n, d, prec=prec, method="sp")
+    Mt = torch.tensor(M, dtype=dt, device="cuda")
+    out = []
+    for z in (0, 5):
+        p.set_variants(z, 0)
+        out.append(p.field(Mt).double().cpu().numpy())
+    p.check_pipeline()
+    tol = 1e-12 if prec == "f64" else _fp32_bound(n, d, phi_ref, H_ref)
+    for H in out:
+        assert _relmax(H, H_ref) <= tol
+    assert np.array_equal(out[0], out[1])
+    p.close()
