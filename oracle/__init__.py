@@ -29,6 +29,12 @@ kernel S of one homogeneously magnetized cell, by direct sum or by zero-padded
 FFT convolution, and the field of each cell from the node potentials by
 finite differences (the cell average of minus the gradient of the trilinear
 interpolant). Potentials have shape (nz+1, ny+1, nx+1).
+
+The tensor-grid method (TG, Sec. 3.2) has its oracle in ``tensor_grid.py``
+(``oracle.tensor_grid``): sinc quadrature of the Gaussian representation of
+1/r^3, closed-form Gaussian matrices, mode products for dense and CP
+magnetization, the exact cell-centre potential for comparison, and the
+second-order finite-difference field.
 """
 from __future__ import annotations
 
@@ -453,3 +459,6 @@ def sp_field_from_potential(phi: np.ndarray, d) -> np.ndarray:
 def sp_field(M: np.ndarray, d, P=None) -> np.ndarray:
     """SP stray field: FFT node potential, then the finite-difference field."""
     return sp_field_from_potential(sp_potential_fft(M, d, P), d)
+
+
+from . import tensor_grid  # noqa: E402  (TG oracle, numpy only)
