@@ -394,6 +394,10 @@ def run_ours(args, rank, world, local_rank):
         sp = run_sp(args, dev, M, H, peak)
         sp["speedup_over_dm"] = round(ms_per_step / sp["ms_per_step"], 3)
 
+    tgr = None
+    if not args.skip_tg:
+        tgr = run_tg(args, dev, peak)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cpu = cpu_baseline(args.cpu_sample)
@@ -423,6 +427,7 @@ def run_ours(args, rank, world, local_rank):
                          "ms_per_field": None if tuned_ms is None else round(tuned_ms, 4)},
             "batch": batch,
             "scalar_potential": sp,
+            "tensor_grid": tgr,
             "energy_J": E_val,
             "passes": per_pass,
             "roofline": roof,
@@ -500,6 +505,65 @@ def run_sp(args, dev, M, H_dm, peak):
         del H64
     del H
     torch.cuda.empty_cache()
+    return out
+
+
+def run_tg(args, dev, peak):
+    """The tensor-grid method (paper Sec. 3.2) on the same grid for CP
+    magnetizations of rank 1 (a uniform body, exact) and rank 8 (seeded random
+    factors): field + energy per step, and the FP32 error of the rank-8 field
+    against the FP64 TG path."""
+    import numpy as np
+    import torch
+
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300.tg import TGPlan
+
+    n = N_GRID
+    cells = n[0] * n[1] * n[2]
+    st = torch.cuda.current_stream(dev)
+    out = {}
+    rng = np.random.default_rng(SEED)
+    for r in (1, 8):
+        if r == 1:
+            lam = np.array([[0.3], [-0.5], [0.8]]) * MS
+            U = [np.ones((3, 1, v)) for v in n]
+        else:
+            lam = MS * rng.standard_normal((3, r)) / r
+            U = [rng.standard_normal((3, r, v)) for v in n]
+        f32 = [torch.tensor(a, dtype=torch.float32, device=dev) for a in [lam] + U]
+        plan = TGPlan(n, CELL, r, prec="f32", device=dev)
+        H = torch.empty((3, n[2], n[1], n[0]), dtype=torch.float32, device=dev)
+        E = torch.empty((), dtype=torch.float64, device=dev)
+
+        def step():
+            B.demag_tg_field_cp(plan.handle, *(t.data_ptr() for t in f32), H.data_ptr(), E.data_ptr(),
+                                st.cuda_stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        k = max(5, args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(k):
+            step()
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        ent = {"rank": r, "ms_per_step": round(ms, 4), "cells_per_s": cells / (ms / 1e3),
+               "sinc_terms": plan.info()["sinc_terms"], "energy_J": float(E.item())}
+        plan.close()
+        if r == 8 and not args.skip_f64:
+            p64 = TGPlan(n, CELL, r, prec="f64", device=dev)
+            H64 = p64.field(*[torch.tensor(a, dtype=torch.float64, device=dev) for a in [lam] + U])
+            ent["f32_rel_max_err_vs_f64"] = float((H.double() - H64).abs().max() / H64.abs().max())
+            p64.close()
+            del H64
+        out[f"rank{r}"] = ent
+        del H, f32
+        torch.cuda.empty_cache()
     return out
 
 
@@ -634,6 +698,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-sp", action="store_true", help="skip the scalar-potential method leg")
+    ap.add_argument("--skip-tg", action="store_true", help="skip the tensor-grid method leg")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")
     ap.add_argument("--variants", default="", help="fixed z,y,x kernel variants instead of autotuning")
     ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")

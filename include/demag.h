@@ -347,6 +347,44 @@ demag_status demag_set_x_variant(demag_plan_t plan, int x);
  * else DEMAG_OK. */
 demag_status demag_check_pipeline(demag_plan_t plan);
 
+/* ------------------------------------------------------------------------
+ * Tensor-grid method (TG, paper Sec. 3.2) for magnetization in CP format
+ * (App. A): M^(p)[k][j][i] = sum_m lam[p][m] Ux[p][m][i] Uy[p][m][j] Uz[p][m][k].
+ * The potential at the cell centres is the block sum of mode products of
+ * Eq. "sumpot": 1/|r|^3 written as a Gaussian integral (Eq. "transform") and
+ * integrated by a sinc rule in t (tau = e^t; rule error ~1e-15 for FP64
+ * plans, ~2e-9 for FP32 plans), with the Gaussian matrices of Eqs. "Dmat"
+ * and "gs" in closed form (FP64 setup). The field is H = -grad Phi by
+ * second-order differences (central inside, one-sided at the first and last
+ * cell of each axis), and the energy is E = -(mu0/2) V sum M.H with M rebuilt
+ * from its factors. Cost per call: O(R r (nx^2 + ny^2 + nz^2)) for the
+ * factors and O(R r nx ny nz) for the dense potential (R sinc terms), instead
+ * of a convolution over the padded grid. */
+typedef struct demag_tg_plan *demag_tg_plan_t;
+
+/* Plan for an nx x ny x nz grid (3..512 per axis: the differences need three
+ * cells) of edges dx, dy, dz and CP rank 1..64. Computes the sinc rule and
+ * the Gaussian tables on the device (FP64, stored in the plan's precision)
+ * and synchronises. Errors as demag_plan_create. */
+demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, int rank,
+                                  demag_prec prec, demag_tg_plan_t *out);
+
+/* Field and/or energy of a CP magnetization. lam: device [3][rank]; Ux:
+ * device [3][rank][nx]; Uy: [3][rank][ny]; Uz: [3][rank][nz] (plan element
+ * type, A/m carried by lam). H: device [3][nz][ny][nx] or NULL; E_dev: device
+ * double or NULL (not both NULL). Asynchronous on stream. */
+demag_status demag_tg_field_cp(demag_tg_plan_t plan, const void *lam, const void *Ux, const void *Uy,
+                               const void *Uz, void *H, double *E_dev, void *stream);
+
+/* The cell-centre potential phi [nz][ny][nx] (device) of a CP magnetization. */
+demag_status demag_tg_potential_cp(demag_tg_plan_t plan, const void *lam, const void *Ux, const void *Uy,
+                                   const void *Uz, void *phi, void *stream);
+
+/* Sinc terms R, device memory held, kernels launched so far (any may be NULL). */
+demag_status demag_tg_plan_info(demag_tg_plan_t plan, int *sinc_terms, size_t *device_bytes, long *launches);
+
+void demag_tg_plan_destroy(demag_tg_plan_t plan);
+
 /* Destroy a plan and free its device memory (NULL is ignored). */
 void demag_plan_destroy(demag_plan_t plan);
 

@@ -42,6 +42,8 @@ EXPORTS = [
     "demag_field_host_async", "demag_host_wait",
     "demag_plan_create_sp", "demag_sp_potential",
     "demag_get_x_variant", "demag_set_x_variant", "demag_check_pipeline",
+    "demag_tg_plan_create", "demag_tg_field_cp", "demag_tg_potential_cp", "demag_tg_plan_info",
+    "demag_tg_plan_destroy",
 ]
 
 
@@ -124,6 +126,11 @@ def load(path: str | Path | None = None):
         "demag_get_x_variant": (S, [P, POINTER(c_int)]),
         "demag_set_x_variant": (S, [P, I]),
         "demag_check_pipeline": (S, [P]),
+        "demag_tg_plan_create": (S, [I, I, I, D, D, D, I, I, POINTER(c_void_p)]),
+        "demag_tg_field_cp": (S, [P, P, P, P, P, P, P, P]),
+        "demag_tg_potential_cp": (S, [P, P, P, P, P, P, P]),
+        "demag_tg_plan_info": (S, [P, POINTER(c_int), POINTER(c_size_t), POINTER(c_long)]),
+        "demag_tg_plan_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -186,6 +193,37 @@ def demag_set_x_variant(plan, x):
 
 def demag_check_pipeline(plan):
     _check(load().demag_check_pipeline(_p(plan)), "demag_check_pipeline")
+
+
+def demag_tg_plan_create(nx, ny, nz, dx, dy, dz, rank, prec=DEMAG_F32):
+    h = c_void_p()
+    _check(load().demag_tg_plan_create(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), int(rank),
+                                       int(prec), ctypes.byref(h)), "demag_tg_plan_create")
+    return h.value
+
+
+def demag_tg_field_cp(plan, lam, Ux, Uy, Uz, H, E_dev, stream=0):
+    _check(load().demag_tg_field_cp(_p(plan), _p(lam), _p(Ux), _p(Uy), _p(Uz), _p(H), _p(E_dev), _p(stream)),
+           "demag_tg_field_cp")
+
+
+def demag_tg_potential_cp(plan, lam, Ux, Uy, Uz, phi, stream=0):
+    _check(load().demag_tg_potential_cp(_p(plan), _p(lam), _p(Ux), _p(Uy), _p(Uz), _p(phi), _p(stream)),
+           "demag_tg_potential_cp")
+
+
+def demag_tg_plan_info(plan) -> dict:
+    r = c_int()
+    b = c_size_t()
+    n = c_long()
+    _check(load().demag_tg_plan_info(_p(plan), ctypes.byref(r), ctypes.byref(b), ctypes.byref(n)),
+           "demag_tg_plan_info")
+    return {"sinc_terms": r.value, "device_bytes": b.value, "launches": n.value}
+
+
+def demag_tg_plan_destroy(plan):
+    if plan:
+        load().demag_tg_plan_destroy(_p(plan))
 
 
 def demag_tensor_setup(plan, stream=0):

@@ -18,7 +18,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libdemag.so"
 
-SOURCES = ["api.cu", "tensor.cu", "passes_f32.cu", "passes_f64.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "tensor.cu", "passes_f32.cu", "passes_f64.cu", "noalloc.cu", "batch.cu", "tg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -79,6 +79,21 @@ def test_sp_plan_arguments_are_checked_before_any_device_call(lib):
         assert e.value.name == status, (args, pad)
 
 
+def test_tg_plan_arguments_are_checked_before_any_device_call(lib):
+    """Tensor-grid plans: at least 3 cells per axis (second-order one-sided
+    differences), at most 512, CP rank 1..64, positive edges."""
+    from paper_1204_4302_gb300 import binding
+    cases = [((2, 8, 8, 1.0, 1.0, 1.0, 1), "DEMAG_ERR_INVALID_ARG"),
+             ((8, 8, 8, 1.0, -1.0, 1.0, 1), "DEMAG_ERR_INVALID_ARG"),
+             ((8, 8, 8, 1.0, 1.0, 1.0, 0), "DEMAG_ERR_INVALID_ARG"),
+             ((8, 8, 8, 1.0, 1.0, 1.0, 65), "DEMAG_ERR_INVALID_ARG"),
+             ((513, 8, 8, 1.0, 1.0, 1.0, 1), "DEMAG_ERR_UNSUPPORTED")]
+    for args, status in cases:
+        with pytest.raises(binding.DemagError) as e:
+            binding.demag_tg_plan_create(*args)
+        assert e.value.name == status, args
+
+
 def test_no_device_gives_a_cuda_status():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
