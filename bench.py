@@ -109,9 +109,16 @@ def whole_job_rate(cells_per_rank: int, world: int, steps: int, ms_max: float) -
     return world * cells_per_rank * steps / (ms_max / 1e3)
 
 
+# The sources that define the field-step kernels of the DM and SP pipelines
+# and their launch shapes (the per-kernel DRAM traffic in profiles/traffic.json
+# is valid while these are unchanged).
+STEP_KERNEL_SOURCES = ("fft_engine.cuh", "fft2.cuh", "xpipe.cuh", "sp.cuh", "passes_impl.cuh", "passes_f32.cu",
+                       "passes_f64.cu", "plan.h")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1204_4302_gb300", "csrc"))):
+    for f in STEP_KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1204_4302_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
