@@ -327,6 +327,22 @@ demag_status tg_job(demag_tg_plan *p, const void *lam, const void *Ux, const voi
         return s;
     if (H && (s = tg_check_ptr(p, H, "H")) != DEMAG_OK) return s;
     if (phi && (s = tg_check_ptr(p, phi, "phi")) != DEMAG_OK) return s;
+    {
+        // outputs must not overlap the factors (the kernels read them throughout)
+        const size_t es = p->prec == DEMAG_F32 ? 4 : 8, r = (size_t)p->rank;
+        const size_t ncell = (size_t)p->nx * p->ny * p->nz;
+        const void *in[4] = {lam, Ux, Uy, Uz};
+        const size_t inb[4] = {3 * r * es, 3 * r * p->nx * es, 3 * r * p->ny * es, 3 * r * p->nz * es};
+        auto hits = [&](const void *o, size_t ob) {
+            for (int q = 0; q < 4; ++q) {
+                const uintptr_t a = (uintptr_t)o, b = (uintptr_t)in[q];
+                if (a < b + inb[q] && b < a + ob) return true;
+            }
+            return false;
+        };
+        if (H && hits(H, 3 * ncell * es)) return tg_fail(DEMAG_ERR_INVALID_ARG, "H overlaps a factor");
+        if (phi && hits(phi, ncell * es)) return tg_fail(DEMAG_ERR_INVALID_ARG, "phi overlaps a factor");
+    }
     if (E_dev) {
         if (((uintptr_t)E_dev & 7u) != 0) return tg_fail(DEMAG_ERR_INVALID_ARG, "E_dev is not 8-byte aligned");
         cudaPointerAttributes a;

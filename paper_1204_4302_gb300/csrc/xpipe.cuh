@@ -553,8 +553,13 @@ k_z_conv_tma(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *__
         cp_async_wait_all();
         __syncthreads();
         if (s_fail) {
-            if (threadIdx.x == 0) atomicExch(&g_xpipe_error, 1);
-            return;  // only this tile's copy was in flight, and it gave up
+            // only this tile's copy is in flight: give it one more bounded wait
+            // so that it does not land after the CTA has exited, then flag
+            if (threadIdx.x == 0) {
+                mbar_wait_bounded(bar, (unsigned)(k & 1), kPipeWaitCycles);
+                atomicExch(&g_xpipe_error, 1);
+            }
+            return;
         }
         // forward stage 1 from the staged rows: rows j1 + r R2 -> rows j1 R1 + r
 #pragma unroll
@@ -722,7 +727,10 @@ k_sp_z_tma(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *__re
         cp_async_wait_all();
         __syncthreads();
         if (s_fail) {
-            if (threadIdx.x == 0) atomicExch(&g_xpipe_error, 1);
+            if (threadIdx.x == 0) {  // as in k_z_conv_tma
+                mbar_wait_bounded(bar, (unsigned)(k & 1), kPipeWaitCycles);
+                atomicExch(&g_xpipe_error, 1);
+            }
             return;
         }
 #pragma unroll
