@@ -182,6 +182,8 @@ template <typename T, int L> struct Col3Shape {
     static constexpr int R1 = Col3Radix<L>::R1, R2 = Col3Radix<L>::R2, R3 = Col3Radix<L>::R3;
     static constexpr int NT = 2 * Tile2<T>::NT;
     static constexpr int TC = 8;
+    static_assert((R1 * TC) % 32 == 0 && ((L / R3) * TC) % 32 == 0 && 32 % TC == 0,
+                  "constant swizzled steps need 32-aligned row groups");
 };
 
 template <typename T, int L, bool INV, bool PIN, bool POUT>
@@ -216,8 +218,10 @@ k_col3(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__
             }
             if constexpr (PIN) RegDFTHalfIn<R1, INV, C>::run(u);
             else RegDFT<R1, INV, C>::run(u);
+            // R1 TC is a multiple of 32 and TC divides 32: constant swizzled steps
+            C *s = sm + sw(j1 * R1 * TC + c);
 #pragma unroll
-            for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
+            for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
         }
     }
     __syncthreads();
@@ -230,8 +234,9 @@ k_col3(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__
         if (b < TC * (L / R3)) {
             const int c = b % TC, j = b / TC, f = f0 + c;
             C v[R3];
+            const C *s = sm + sw(j * TC + c);
 #pragma unroll
-            for (int r = 0; r < R3; ++r) v[r] = sm[sw((j + r * (L / R3)) * TC + c)];
+            for (int r = 0; r < R3; ++r) v[r] = s[r * ((L / R3) * TC + (L / R3) * TC / 32)];
             twiddle_row<R3, L, INV>(v, j, tw, twstride);
             if constexpr (POUT) RegDFTHalfOut<R3, INV, C>::run(v);
             else RegDFT<R3, INV, C>::run(v);
@@ -753,6 +758,7 @@ template <> struct XRadix<512> { static constexpr int R1 = 32, R2 = 16; };
 
 template <typename T, int L> struct XShape {
     static constexpr int R1 = XRadix<L>::R1, R2 = XRadix<L>::R2;
+    static_assert(R1 <= 32 && 32 % R1 == 0, "the exchange indexing assumes R1 divides 32");
     static constexpr int NT = Tile2<T>::NT;
     static constexpr int TR = NT / (R1 > R2 ? R1 : R2);  // rows per CTA
     static constexpr int RS = swsize(L);                 // padded row in shared memory
@@ -814,7 +820,7 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
         else RegDFT<R1, false, C>::run(u);
         C *s = sm + rr * RS;
 #pragma unroll
-        for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+        for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
     }
     __syncthreads();
     // stage 2 + split: thread (row, j2) computes X[k], k = j2 + r R1
@@ -823,7 +829,7 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
         const C *s = sm + rr * RS;
         C v[R2];
 #pragma unroll
-        for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+        for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
 #pragma unroll
         for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], __ldg(&twx[2 * r * j2]));
         RegDFT<R2, false, C>::run(v);
@@ -887,7 +893,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         RegDFT<R1, true, C>::run(u);
         C *s = sm + rr * RS;
 #pragma unroll
-        for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+        for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
     }
     __syncthreads();
     T acc = 0;  // per-thread sum of a few dozen terms; blocks reduce in FP64
@@ -896,7 +902,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         const C *s = sm + rr * RS;
         C v[R2];
 #pragma unroll
-        for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+        for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
 #pragma unroll
         for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
         if constexpr (P1) RegDFTHalfOutP1<R2, true, C>::run(v);

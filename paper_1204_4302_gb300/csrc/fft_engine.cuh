@@ -174,8 +174,15 @@ __device__ __forceinline__ void fft_stage(C *sm, const C *__restrict__ tw, int t
     for (int q = 0; q < BPT; ++q) {
         const int b = threadIdx.x + q * NT;
         const int col = b % TC, j = b / TC;
+        if constexpr ((NB * TC) % 32 == 0) {
+            // sw() is additive across multiples of 32: one swizzled base, constant steps
+            const C *s = sm + sw(j * TC + col);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = sm[sw((j + r * NB) * TC + col)];
+            for (int r = 0; r < R; ++r) v[q][r] = s[r * (NB * TC + (NB * TC) / 32)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = sm[sw((j + r * NB) * TC + col)];
+        }
         if (NS > 1) {
             const int k = j % NS;
 #pragma unroll
@@ -193,8 +200,14 @@ __device__ __forceinline__ void fft_stage(C *sm, const C *__restrict__ tw, int t
         const int col = b % TC, j = b / TC;
         const int k = j % NS;
         const int d = (j / NS) * NS * R + k;
+        if constexpr ((NS * TC) % 32 == 0) {
+            C *s = sm + sw(d * TC + col);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[sw((d + r * NS) * TC + col)] = v[q][r];
+            for (int r = 0; r < R; ++r) s[r * (NS * TC + (NS * TC) / 32)] = v[q][r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[sw((d + r * NS) * TC + col)] = v[q][r];
+        }
     }
     __syncthreads();
 }

@@ -191,7 +191,7 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
             RegDFTHalfIn<R1, false, C>::run(u);
             C *s = sm + rr * RS;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+            for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
         }
         __syncthreads();  // buffer b consumed, exchange rows written
         if (threadIdx.x == 0) {
@@ -207,7 +207,7 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
             const C *s = sm + rr * RS;
             C v[R2];
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+            for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
 #pragma unroll
             for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], __ldg(&twx[2 * r * j2]));
             RegDFT<R2, false, C>::run(v);
@@ -303,7 +303,7 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
         if (act1) {
             C *s = sm + rr1 * RS;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) s[sw(j1 * R1 + r)] = u[r];
+            for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
         }
         __syncthreads();
         T acc = 0;
@@ -312,7 +312,7 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
             const C *s = sm + rr * RS;
             C v[R2];
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[r] = s[sw(j2 + r * R1)];
+            for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
 #pragma unroll
             for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
             if constexpr (P1) RegDFTHalfOutP1<R2, true, C>::run(v);
@@ -428,8 +428,9 @@ k_col_tma_fwd(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *_
                     if (row < nin) u[r] = buf[b][row * TC + c];
                 }
                 RegDFTHalfIn<R1, false, C>::run(u);
+                C *s = sm + sw(j1 * R1 * TC + c);
 #pragma unroll
-                for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
+                for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
             }
         }
         __syncthreads();  // buffer b consumed
@@ -444,8 +445,9 @@ k_col_tma_fwd(const __grid_constant__ CUtensorMap map, typename Cplx<T>::type *_
             if (bq < TC * (L / R3)) {
                 const int c = bq % TC, j = bq / TC, kx = kx0 + c;
                 C v[R3];
+                const C *s = sm + sw(j * TC + c);
 #pragma unroll
-                for (int r = 0; r < R3; ++r) v[r] = sm[sw((j + r * (L / R3)) * TC + c)];
+                for (int r = 0; r < R3; ++r) v[r] = s[r * ((L / R3) * TC + (L / R3) * TC / 32)];
                 twiddle_row<R3, L, false>(v, j, tw, twstride);
                 RegDFT<R3, false, C>::run(v);
                 if (kx < width) {
