@@ -46,6 +46,8 @@ template <typename T, int L, int V = 0> struct ColShape {
     static constexpr int R1 = ColRadix<L, V>::R1, R2 = ColRadix<L, V>::R2;
     static constexpr int NT = Tile2<T>::NT;
     static constexpr int TC = NT / (R1 < R2 ? R1 : R2);
+    static_assert((R1 * TC) % 32 == 0 && (TC % 32 == 0 || 32 % TC == 0),
+                  "constant swizzled steps need 32-aligned row groups");
 };
 // z pass: every thread owns one stage-2 butterfly (three components); the
 // CTA size NT is a tuning choice (variant 0: Tile2 threads, 1: half).
@@ -129,8 +131,10 @@ __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__rest
             }
             if constexpr (PIN) RegDFTHalfIn<R1, INV, C>::run(u);
             else RegDFT<R1, INV, C>::run(u);
+            // R1 TC is a multiple of 32 and TC a power of two: constant swizzled steps
+            C *s = sm + sw(j1 * R1 * TC + c);
 #pragma unroll
-            for (int r = 0; r < R1; ++r) sm[sw((j1 * R1 + r) * TC + c)] = u[r];
+            for (int r = 0; r < R1; ++r) s[r * TC + (r * TC) / 32] = u[r];
         }
     }
     __syncthreads();
@@ -141,8 +145,9 @@ __device__ __forceinline__ void k_col2_tile(const typename Cplx<T>::type *__rest
         if (b < TC * R1) {
             const int c = b % TC, j2 = b / TC, f = f0 + c;
             C v[R2];
+            const C *s = sm + sw(j2 * TC + c);
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[r] = sm[sw((j2 + r * R1) * TC + c)];
+            for (int r = 0; r < R2; ++r) v[r] = s[r * (R1 * TC + (R1 * TC) / 32)];
             twiddle_row<R2, L, INV>(v, j2, tw, twstride);
             if constexpr (POUT) RegDFTHalfOut<R2, INV, C>::run(v);
             else RegDFT<R2, INV, C>::run(v);
