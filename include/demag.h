@@ -61,12 +61,23 @@ typedef enum { DEMAG_F32 = 0, DEMAG_F64 = 1 } demag_prec;
  * difference gradient (SP). */
 typedef enum { DEMAG_METHOD_DM = 0, DEMAG_METHOD_SP = 1 } demag_method;
 
+/* Choice of padded lengths where demag_options leaves one at 0. */
+typedef enum {
+    DEMAG_PAD_POW2 = 0,   /* smallest power of two >= 2n - 1 */
+    DEMAG_PAD_SMOOTH = 1  /* smallest even length >= 2n - 1 whose prime factors
+                             are 2, 3, 5 and 7 (mixed-radix passes; DM only) */
+} demag_pad_mode;
+
 /* Optional plan settings; zero-initialise and set what you need. */
 typedef struct {
-    /* Padded FFT lengths per axis. 0 selects the smallest power of two
-     * >= 2n - 1 (1 when n == 1). Any power of two >= 2n - 1 gives the same
-     * field up to rounding (the convolution is exact for every such period). */
+    /* Padded FFT lengths per axis. 0 selects one by pad_mode (1 when n == 1).
+     * An explicit length must be >= 2n - 1 and at most 1024: for DM plans a
+     * power of two or an even product of 2, 3, 5 and 7; for SP plans a power
+     * of two >= 2n. Every such period gives the same field up to rounding
+     * (the zero-padded convolution is exact for each). Lengths that are not
+     * powers of two run the mixed-radix passes. */
     int px, py, pz;
+    int pad_mode; /* demag_pad_mode */
 } demag_options;
 
 /* Sizes of a plan, as chosen at creation. */

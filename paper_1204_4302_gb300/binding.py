@@ -18,6 +18,8 @@ DEMAG_F64 = 1
 
 DEMAG_METHOD_DM = 0
 DEMAG_METHOD_SP = 1
+DEMAG_PAD_POW2 = 0
+DEMAG_PAD_SMOOTH = 1
 
 STATUS = {
     0: "DEMAG_OK",
@@ -55,7 +57,7 @@ class DemagError(RuntimeError):
 
 
 class demag_options(ctypes.Structure):
-    _fields_ = [("px", c_int), ("py", c_int), ("pz", c_int)]
+    _fields_ = [("px", c_int), ("py", c_int), ("pz", c_int), ("pad_mode", c_int)]
 
 
 class demag_info(ctypes.Structure):
@@ -159,18 +161,18 @@ def demag_plan_create(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32):
     return h.value
 
 
-def demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=0):
+def demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=0, pad_mode=0):
     h = c_void_p()
-    opt = demag_options(int(px), int(py), int(pz))
+    opt = demag_options(int(px), int(py), int(pz), int(pad_mode))
     _check(load().demag_plan_create_ex(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
                                        int(prec), ctypes.byref(opt), ctypes.byref(h)),
            "demag_plan_create_ex")
     return h.value
 
 
-def demag_plan_create_sp(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=0):
+def demag_plan_create_sp(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, px=0, py=0, pz=0, pad_mode=0):
     h = c_void_p()
-    opt = demag_options(int(px), int(py), int(pz))
+    opt = demag_options(int(px), int(py), int(pz), int(pad_mode))
     _check(load().demag_plan_create_sp(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
                                        int(prec), ctypes.byref(opt), ctypes.byref(h)),
            "demag_plan_create_sp")

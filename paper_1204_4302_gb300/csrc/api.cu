@@ -54,6 +54,23 @@ int default_pad(int n)
     return p;
 }
 
+// even, with no prime factor above 7 (the mixed-radix passes' lengths)
+bool is_smooth_even(int v)
+{
+    if (v < 2 || v % 2) return false;
+    for (int f : {2, 3, 5, 7})
+        while (v % f == 0) v /= f;
+    return v == 1;
+}
+
+int smooth_pad(int n)
+{
+    if (n == 1) return 1;
+    int p = 2 * n - 1;
+    while (!is_smooth_even(p)) ++p;
+    return p;
+}
+
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
     int prev = -1;
@@ -618,14 +635,19 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
     if (prec != DEMAG_F32 && prec != DEMAG_F64) return fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
     if (nx > kMaxN || ny > kMaxN || nz > kMaxN)
         return fail(DEMAG_ERR_UNSUPPORTED, "grid sizes above 512 per axis are not built");
-    int P[3] = {default_pad(nx), default_pad(ny), default_pad(nz)};
     const int n[3] = {nx, ny, nz};
+    if (opt && opt->pad_mode != DEMAG_PAD_POW2 && opt->pad_mode != DEMAG_PAD_SMOOTH)
+        return fail(DEMAG_ERR_INVALID_ARG, "unknown pad_mode");
+    const bool smooth = opt && opt->pad_mode == DEMAG_PAD_SMOOTH;
+    int P[3];
+    for (int a = 0; a < 3; ++a) P[a] = smooth ? smooth_pad(n[a]) : default_pad(n[a]);
     if (opt) {
         const int req[3] = {opt->px, opt->py, opt->pz};
         for (int a = 0; a < 3; ++a) {
             if (req[a] == 0) continue;
-            if (!is_pow2(req[a]) || req[a] < 2 * n[a] - 1)
-                return fail(DEMAG_ERR_INVALID_ARG, "padded lengths must be powers of two >= 2n - 1");
+            if (!(is_pow2(req[a]) || is_smooth_even(req[a])) || req[a] < 2 * n[a] - 1)
+                return fail(DEMAG_ERR_INVALID_ARG,
+                            "padded lengths must be >= 2n - 1 and powers of two or even products of 2, 3, 5, 7");
             if (req[a] > kMaxP) return fail(DEMAG_ERR_UNSUPPORTED, "padded lengths above 1024 are not built");
             P[a] = req[a];
         }
@@ -646,6 +668,8 @@ demag_status demag_plan_create_sp(int nx, int ny, int nz, double dx, double dy, 
         return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential grids are built up to 512 x 512 x 256");
     int P[3] = {sp_pad(nx), sp_pad(ny), sp_pad(nz)};
     const int n[3] = {nx, ny, nz};
+    if (opt && opt->pad_mode != DEMAG_PAD_POW2)
+        return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential plans use power-of-two padding");
     if (opt) {
         const int req[3] = {opt->px, opt->py, opt->pz};
         for (int a = 0; a < 3; ++a) {
@@ -998,11 +1022,14 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     // radix order where the two radices differ
     std::vector<int> zs = {0}, ys = {0}, xs = {0, 1, 2};
     const bool dm = p->method == DEMAG_METHOD_DM;  // the SP z pass has one form
-    if (dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
-    if (dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
-    if (dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
-    if (dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(4);   // half tile, two CTAs per SM
-    if (p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input (DM and SP)
+    // (lengths that are not powers of two have the one mixed-radix form)
+    const bool z2 = is_pow2(p->Pz);
+    if (!is_pow2(p->Px)) xs = {0};
+    if (z2 && dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(1);
+    if (z2 && dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
+    if (z2 && dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
+    if (z2 && dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(4);   // half tile, two CTAs per SM
+    if (z2 && p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input (DM and SP)
     if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
     if (p->Py == 512 || p->Py == 1024) ys.push_back(2);  // three-stage, more CTAs per SM
     if (p->Py == 512 || p->Py == 1024) ys.push_back(3);  // forward pass by the TMA pipeline

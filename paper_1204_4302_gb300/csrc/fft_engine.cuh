@@ -384,41 +384,6 @@ k_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows,
     k_x_inv_tile<T, L, false>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
 }
 
-// ---------------------------------------------------------------- columns
-// Length-L transform of ncols strided columns. Column f maps to slab f / width
-// and offset f % width; element r of the column sits at slab * ss + r * rs +
-// offset. Rows >= nin read as zero; rows >= nout are not written.
-template <typename T, int L, bool INV>
-__global__ void __launch_bounds__(Tile<T>::NT)
-k_col_fft(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out,
-          int ncols, int width, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
-          const typename Cplx<T>::type *__restrict__ tw, int twstride)
-{
-    using C = typename Cplx<T>::type;
-    using S = TileShape<T, L>;
-    constexpr int NT = S::NT, TC = S::TC;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *sm = reinterpret_cast<C *>(smraw);
-    const int f0 = blockIdx.x * TC;
-    for (int e = threadIdx.x; e < L * TC; e += NT) {
-        const int c = e % TC, r = e / TC, f = f0 + c;
-        C v = cmk<C>(0, 0);
-        if (f < ncols && r < nin) {
-            const int slab = f / width, off = f - slab * width;
-            v = in[(int64_t)slab * iss + (int64_t)r * irs + off];
-        }
-        sm[sw(e)] = v;
-    }
-    __syncthreads();
-    tile_fft<C, L, INV, NT, TC>(sm, tw, twstride);
-    for (int e = threadIdx.x; e < L * TC; e += NT) {
-        const int c = e % TC, r = e / TC, f = f0 + c;
-        if (f < ncols && r < nout) {
-            const int slab = f / width, off = f - slab * width;
-            out[(int64_t)slab * oss + (int64_t)r * ors + off] = sm[sw(e)];
-        }
-    }
-}
 
 // ---------------------------------------------------------------- z pass
 // Forward z transform of the three components, the spectral product

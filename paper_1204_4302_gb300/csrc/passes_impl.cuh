@@ -6,6 +6,7 @@
 #include "fft_engine.cuh"
 #include <string.h>
 
+#include "mixed.cuh"
 #include "plan.h"
 #include "sp.cuh"
 #include "xpipe.cuh"
@@ -53,6 +54,30 @@ cudaError_t allow_smem(size_t bytes)
         done_for = dev;
     }
     return bytes <= limit ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Mixed-radix plan of a length that is not a power of two (factors 2, 3, 5, 7).
+bool gen_radix(int L, GenRadix &g)
+{
+    g.L = L;
+    g.n = 0;
+    int m = L;
+    while (m % 8 == 0 && g.n < 16) { g.r[g.n++] = 8; m /= 8; }
+    if (m % 4 == 0 && g.n < 16) { g.r[g.n++] = 4; m /= 4; }
+    if (m % 2 == 0 && g.n < 16) { g.r[g.n++] = 2; m /= 2; }
+    while (m % 3 == 0 && g.n < 16) { g.r[g.n++] = 3; m /= 3; }
+    while (m % 5 == 0 && g.n < 16) { g.r[g.n++] = 5; m /= 5; }
+    while (m % 7 == 0 && g.n < 16) { g.r[g.n++] = 7; m /= 7; }
+    return m == 1;
+}
+
+bool pow2_len(int L) { return L > 0 && (L & (L - 1)) == 0; }
+
+// transforms per CTA of the mixed-radix kernels (L x tile <= kGenTileElems)
+int gen_tile(int L)
+{
+    const int t = kGenTileElems / L;
+    return t < 1 ? 1 : t;
 }
 
 template <typename T>
@@ -329,6 +354,16 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
                              const C *twx, cudaStream_t st, int variant)
 {
     if (nrows <= 0) return cudaSuccess;
+    if (!pow2_len(L)) {
+        GenRadix g;
+        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
+        const int TR = gen_tile(L);
+        const size_t sm = 2 * swsize(L * TR) * sizeof(C);
+        cudaError_t e = allow_smem<k_gen_x_fwd<T>>(sm);
+        if (e != cudaSuccess) return e;
+        k_gen_x_fwd<T><<<(nrows + TR - 1) / TR, kGenThreads, sm, st>>>(a, nrows, nvalid, out, out_rs, twx, g, TR);
+        return cudaGetLastError();
+    }
     // pipelined form: rows of the plain field (no per-cell weight) stored back
     // to back, 16-byte multiples, zero-padded half
     if (variant >= 1 && L >= 64 && nvalid <= L && !a.wcell && a.in_rs == nvalid && nvalid % 4 == 0 &&
@@ -377,6 +412,7 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
 template <typename T>
 int Passes<T>::x_blocks(int L, int nrows)
 {
+    if (!pow2_len(L)) return (nrows + gen_tile(L) - 1) / gen_tile(L);
     int rows_per_cta;
     switch (L) {
     case 64: rows_per_cta = XShape<T, 64>::TR; break;
@@ -393,6 +429,16 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
                              const C *twx, cudaStream_t st, int variant)
 {
     if (nrows <= 0) return cudaSuccess;
+    if (!pow2_len(L)) {
+        GenRadix g;
+        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
+        const int TR = gen_tile(L);
+        const size_t sm = 2 * swsize(L * TR) * sizeof(C);
+        cudaError_t e = allow_smem<k_gen_x_inv<T>>(sm);
+        if (e != cudaSuccess) return e;
+        k_gen_x_inv<T><<<(nrows + TR - 1) / TR, kGenThreads, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, g, TR);
+        return cudaGetLastError();
+    }
     if (variant == 2 && L >= 64 && in_rs % 2 == 0 && in_rs <= 2 * L && nvalid <= L + 1 && ((uintptr_t)in & 15) == 0) {
         const bool p1 = nvalid > L;
 #define DEMAG_PIPE(LL)                                                                         \
@@ -458,6 +504,23 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
                            int twstride, cudaStream_t st, int variant)
 {
     if (ncols <= 0) return cudaSuccess;
+    if (!pow2_len(L)) {
+        GenRadix g;
+        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
+        const int TC = gen_tile(L);
+        const size_t sm = 2 * swsize(L * TC) * sizeof(C);
+        cudaError_t e;
+        if (inv) {
+            if ((e = allow_smem<k_gen_col<T, true>>(sm)) != cudaSuccess) return e;
+            k_gen_col<T, true><<<(ncols + TC - 1) / TC, kGenThreads, sm, st>>>(in, out, ncols, width, iss, irs, nin, oss,
+                                                                               ors, nout, tw, twstride, g, TC);
+        } else {
+            if ((e = allow_smem<k_gen_col<T, false>>(sm)) != cudaSuccess) return e;
+            k_gen_col<T, false><<<(ncols + TC - 1) / TC, kGenThreads, sm, st>>>(in, out, ncols, width, iss, irs, nin,
+                                                                                oss, ors, nout, tw, twstride, g, TC);
+        }
+        return cudaGetLastError();
+    }
     if (L <= 16) {
         // one thread per column
         const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
@@ -552,6 +615,18 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant)
 {
+    if (ncols > 0 && !pow2_len(L)) {
+        if (nrows > L) return cudaErrorInvalidValue;
+        GenRadix g;
+        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
+        const int TC = gen_tile(L);
+        const size_t sm = 6 * swsize(L * TC) * sizeof(C);
+        cudaError_t e = allow_smem<k_gen_zconv<T>>(sm);
+        if (e != cudaSuccess) return e;
+        k_gen_zconv<T><<<(ncols + TC - 1) / TC, kGenThreads, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx,
+                                                                       tw, twstride, g, TC);
+        return cudaGetLastError();
+    }
     if (variant == 5 && ncols > 0 && 2 * nrows <= L) {
         cudaError_t e = cudaErrorNotSupported;
         switch (L) {

@@ -17,7 +17,11 @@ class Plan:
 
     method="dm": the demagnetization-tensor convolution (paper Sec. 3.1, Eq.
     "demag"); method="sp": the scalar-potential convolution at the grid nodes
-    with the finite-difference field (Eqs. "scpot" and "field")."""
+    with the finite-difference field (Eqs. "scpot" and "field").
+
+    pad: None or "pow2" pads each axis to the smallest power of two >= 2n - 1;
+    "smooth" to the smallest even length >= 2n - 1 with prime factors 2, 3, 5
+    and 7 (mixed-radix passes, DM only); or explicit (px, py, pz)."""
 
     def __init__(self, n, d, prec: str = "f32", pad=None, device=None, setup: bool = True,
                  method: str = "dm"):
@@ -40,8 +44,10 @@ class Plan:
         with torch.cuda.device(self.device):
             if method == "sp":
                 self.handle = B.demag_plan_create_sp(nx, ny, nz, *self.d, code, *(pad or (0, 0, 0)))
-            elif pad is None:
+            elif pad is None or pad == "pow2":
                 self.handle = B.demag_plan_create(nx, ny, nz, *self.d, code)
+            elif pad == "smooth":
+                self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, pad_mode=B.DEMAG_PAD_SMOOTH)
             else:
                 self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, *pad)
         self.shape = (3, nz, ny, nx)

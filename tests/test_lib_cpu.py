@@ -49,7 +49,7 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
         binding.demag_plan_create(513, 4, 4, 1.0, 1.0, 1.0)
     assert e.value.name == "DEMAG_ERR_UNSUPPORTED"
     with pytest.raises(binding.DemagError) as e:
-        binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, 12, 0, 0)  # not a power of two
+        binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, 22, 0, 0)  # prime factor 11
     assert e.value.name == "DEMAG_ERR_INVALID_ARG"
     with pytest.raises(binding.DemagError) as e:
         binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, 8, 0, 0)  # below 2n - 1
@@ -61,6 +61,33 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
         binding.demag_energy(None, None)
     binding.demag_plan_destroy(None)
     assert binding.demag_launch_count(None) == 0
+
+
+def test_padding_options_are_checked_before_any_device_call(lib):
+    """Padded lengths: powers of two or even products of 2, 3, 5, 7, at least
+    2n - 1 and at most 1024; pad_mode 0 (powers of two) or 1 (smooth)."""
+    from paper_1204_4302_gb300 import binding
+    bad = [({"px": 26}, "DEMAG_ERR_INVALID_ARG"),        # 2 x 13
+           ({"px": 21}, "DEMAG_ERR_INVALID_ARG"),        # odd
+           ({"py": 14}, "DEMAG_ERR_INVALID_ARG"),        # below 2n - 1
+           ({"pz": 1050}, "DEMAG_ERR_UNSUPPORTED"),      # 2 3 5^2 7 > 1024
+           ({"pad_mode": 2}, "DEMAG_ERR_INVALID_ARG"),
+           ({"pad_mode": -1}, "DEMAG_ERR_INVALID_ARG")]
+    for kw, status in bad:
+        with pytest.raises(binding.DemagError) as e:
+            binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, **kw)
+        assert e.value.name == status, kw
+    # accepted by the argument checks (then the device decides)
+    for kw in [{"px": 18}, {"py": 42, "pz": 30}, {"pad_mode": 1}, {"px": 1000, "pad_mode": 1}]:
+        try:
+            h = binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, **kw)
+        except binding.DemagError as e:
+            assert e.name not in ("DEMAG_ERR_INVALID_ARG", "DEMAG_ERR_UNSUPPORTED"), kw
+        else:
+            binding.demag_plan_destroy(h)
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create_sp(8, 8, 8, 1.0, 1.0, 1.0, 0, pad_mode=1)
+    assert e.value.name == "DEMAG_ERR_UNSUPPORTED"
 
 
 def test_sp_plan_arguments_are_checked_before_any_device_call(lib):
