@@ -64,8 +64,11 @@ typedef enum { DEMAG_METHOD_DM = 0, DEMAG_METHOD_SP = 1 } demag_method;
 /* Choice of padded lengths where demag_options leaves one at 0. */
 typedef enum {
     DEMAG_PAD_POW2 = 0,   /* smallest power of two >= 2n - 1 */
-    DEMAG_PAD_SMOOTH = 1  /* smallest even length >= 2n - 1 whose prime factors
+    DEMAG_PAD_SMOOTH = 1, /* smallest even length >= 2n - 1 whose prime factors
                              are 2, 3, 5 and 7 (mixed-radix passes; DM only) */
+    DEMAG_PAD_TUNED = 2   /* the lengths demag_tune_padding picks (DM only; the
+                             plan creation then launches kernels and
+                             synchronises, unless the choice is cached) */
 } demag_pad_mode;
 
 /* Optional plan settings; zero-initialise and set what you need. */
@@ -267,6 +270,13 @@ typedef struct demag_batch *demag_batch_t;
 demag_status demag_batch_create(int n, const int *dims, const double *cells, demag_prec prec,
                                 demag_batch_t *out);
 
+/* Same, with the padding of every state chosen by opt->pad_mode (px, py, pz
+ * must be 0; NULL = powers of two). States whose lengths are not all powers
+ * of two run in branch mode. DEMAG_PAD_TUNED runs demag_tune_padding (cached)
+ * per state. */
+demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, demag_prec prec,
+                                   const demag_options *opt, demag_batch_t *out);
+
 /* Fields and energies of all states. M, H: arrays of n device pointers
  * ([3][nz][ny][nx] per state, 16-byte aligned, H[i] not overlapping M[i]).
  * E_dev: optional device array of n doubles receiving each state's energy.
@@ -324,6 +334,20 @@ long demag_launch_count(demag_plan_t plan);
  * field call with the chosen variants. Allocates and frees two temporary
  * fields; synchronises. */
 demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, void *stream);
+
+/* Padding autotuner for DM plans of an nx x ny x nz grid. Every axis can be
+ * padded to the smallest power of two >= 2n - 1 or to the smallest even
+ * length >= 2n - 1 with prime factors 2, 3, 5, 7 (mixed-radix passes); the
+ * field is the same up to rounding. Each distinct combination (at most 8)
+ * is created, set up, autotuned (demag_autotune) and timed on the current
+ * device; the fastest lengths are written to best->px, py, pz (pad_mode 0).
+ * ms_best / ms_pow2 (may be NULL) receive the time per field call of the
+ * chosen and of the all-power-of-two lengths. use_cache != 0 reuses and
+ * appends results in the autotuner's cache file, keyed by GPU, precision and
+ * sizes. Errors as demag_plan_create_ex and demag_tensor_setup. Synchronises. */
+demag_status demag_tune_padding(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
+                                int use_cache, demag_options *best, double *ms_best, double *ms_pow2,
+                                void *stream);
 
 /* Current variant choice, and a way to set it by hand.
  * z: 0 = two-stage fused pass, 1 = half-width tile, 2 = 256-thread tile

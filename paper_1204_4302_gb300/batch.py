@@ -11,14 +11,19 @@ class Batch:
     PERSISTENT = 0
     BRANCHES = 1
 
-    def __init__(self, dims, cells, prec: str = "f32"):
+    PAD = {None: None, "pow2": 0, "smooth": 1, "tuned": 2}
+
+    def __init__(self, dims, cells, prec: str = "f32", pad=None):
         if not torch.cuda.is_available():
             raise RuntimeError("libdemag needs a CUDA device; there is no CPU path")
         self.dims = [tuple(int(v) for v in t) for t in dims]
         self.cells = [tuple(float(v) for v in t) for t in cells]
         self.dtype = torch.float32 if prec == "f32" else torch.float64
         self.device = torch.device("cuda", torch.cuda.current_device())
-        self.handle = B.demag_batch_create(self.dims, self.cells, B.DEMAG_F32 if prec == "f32" else B.DEMAG_F64)
+        if pad not in self.PAD:
+            raise ValueError("pad must be None, 'pow2', 'smooth' or 'tuned'")
+        self.handle = B.demag_batch_create(self.dims, self.cells, B.DEMAG_F32 if prec == "f32" else B.DEMAG_F64,
+                                           self.PAD[pad])
         self.n = len(self.dims)
 
     def shapes(self):

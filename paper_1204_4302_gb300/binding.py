@@ -20,6 +20,7 @@ DEMAG_METHOD_DM = 0
 DEMAG_METHOD_SP = 1
 DEMAG_PAD_POW2 = 0
 DEMAG_PAD_SMOOTH = 1
+DEMAG_PAD_TUNED = 2
 
 STATUS = {
     0: "DEMAG_OK",
@@ -38,7 +39,8 @@ EXPORTS = [
     "demag_field_host", "demag_plan_info", "demag_set_timing", "demag_get_timing",
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
     "demag_energy_noalloc",
-    "demag_batch_create", "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
+    "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding",
+    "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
     "demag_field_host_async", "demag_host_wait",
@@ -109,6 +111,9 @@ def load(path: str | Path | None = None):
         "demag_status_string": (ctypes.c_char_p, [I]),
         "demag_energy_noalloc": (S, [I, I, I, D, D, D, I, P, P, P, P]),
         "demag_batch_create": (S, [I, P, P, I, POINTER(c_void_p)]),
+        "demag_batch_create_ex": (S, [I, P, P, I, POINTER(demag_options), POINTER(c_void_p)]),
+        "demag_tune_padding": (S, [I, I, I, D, D, D, I, I, POINTER(demag_options), POINTER(c_double),
+                                   POINTER(c_double), P]),
         "demag_batch_field": (S, [P, P, P, P, P]),
         "demag_batch_set_mode": (S, [P, I]),
         "demag_batch_set_timeout": (S, [P, D, I]),
@@ -306,14 +311,30 @@ def demag_energy_noalloc(nx, ny, nz, dx, dy, dz, prec, M, H, E_dev, stream=0):
         raise DemagError(status, "demag_energy_noalloc", "see include/demag.h for the conditions")
 
 
-def demag_batch_create(dims, cells, prec=DEMAG_F32):
-    """dims: [(nx, ny, nz), ...]; cells: [(dx, dy, dz), ...]."""
+def demag_batch_create(dims, cells, prec=DEMAG_F32, pad_mode=None):
+    """dims: [(nx, ny, nz), ...]; cells: [(dx, dy, dz), ...]; pad_mode None
+    (powers of two) or a DEMAG_PAD_* value (demag_batch_create_ex)."""
     n = len(dims)
     d = (c_int * (3 * n))(*[int(v) for t in dims for v in t])
     c = (c_double * (3 * n))(*[float(v) for t in cells for v in t])
     h = c_void_p()
-    _check(load().demag_batch_create(n, d, c, int(prec), ctypes.byref(h)), "demag_batch_create")
+    if pad_mode is None:
+        _check(load().demag_batch_create(n, d, c, int(prec), ctypes.byref(h)), "demag_batch_create")
+    else:
+        opt = demag_options(0, 0, 0, int(pad_mode))
+        _check(load().demag_batch_create_ex(n, d, c, int(prec), ctypes.byref(opt), ctypes.byref(h)),
+               "demag_batch_create_ex")
     return h.value
+
+
+def demag_tune_padding(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, use_cache=True, stream=0):
+    """Fastest padded lengths of a DM plan: ((px, py, pz), ms_best, ms_pow2)."""
+    opt = demag_options()
+    mb, mp = c_double(), c_double()
+    _check(load().demag_tune_padding(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), int(prec),
+                                     1 if use_cache else 0, ctypes.byref(opt), ctypes.byref(mb), ctypes.byref(mp),
+                                     _p(stream)), "demag_tune_padding")
+    return (opt.px, opt.py, opt.pz), mb.value, mp.value
 
 
 def demag_batch_field(batch, M_ptrs, H_ptrs, E_dev=None, stream=0):

@@ -636,11 +636,22 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
     if (nx > kMaxN || ny > kMaxN || nz > kMaxN)
         return fail(DEMAG_ERR_UNSUPPORTED, "grid sizes above 512 per axis are not built");
     const int n[3] = {nx, ny, nz};
-    if (opt && opt->pad_mode != DEMAG_PAD_POW2 && opt->pad_mode != DEMAG_PAD_SMOOTH)
+    if (opt && opt->pad_mode != DEMAG_PAD_POW2 && opt->pad_mode != DEMAG_PAD_SMOOTH &&
+        opt->pad_mode != DEMAG_PAD_TUNED)
         return fail(DEMAG_ERR_INVALID_ARG, "unknown pad_mode");
     const bool smooth = opt && opt->pad_mode == DEMAG_PAD_SMOOTH;
     int P[3];
     for (int a = 0; a < 3; ++a) P[a] = smooth ? smooth_pad(n[a]) : default_pad(n[a]);
+    if (opt && opt->pad_mode == DEMAG_PAD_TUNED) {
+        if (opt->px || opt->py || opt->pz)
+            return fail(DEMAG_ERR_INVALID_ARG, "DEMAG_PAD_TUNED takes no explicit padded lengths");
+        demag_options t;
+        memset(&t, 0, sizeof t);
+        demag_status s = demag_tune_padding(nx, ny, nz, dx, dy, dz, prec, 1, &t, nullptr, nullptr, nullptr);
+        if (s != DEMAG_OK) return s;
+        P[0] = t.px; P[1] = t.py; P[2] = t.pz;
+        return create_plan(nx, ny, nz, dx, dy, dz, prec, P, DEMAG_METHOD_DM, out);
+    }
     if (opt) {
         const int req[3] = {opt->px, opt->py, opt->pz};
         for (int a = 0; a < 3; ++a) {
@@ -1077,6 +1088,74 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     p->tuned = true;
     if (best_ms) *best_ms = best;
     if (use_cache) tune_store(key, bz, by, bx, best);
+    return DEMAG_OK;
+}
+
+demag_status demag_tune_padding(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
+                                int use_cache, demag_options *best, double *ms_best, double *ms_pow2, void *stream)
+{
+    if (!best) return fail(DEMAG_ERR_INVALID_ARG, "best is NULL");
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a)
+        if (n[a] < 1) return fail(DEMAG_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DEMAG_ERR_CUDA, "no CUDA device");
+    }
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (auto &c : name)
+        if (c == ' ') c = '_';
+    char key[256];
+    snprintf(key, sizeof key, "pad1|%s|%s|%dx%dx%d", name.c_str(), prec == DEMAG_F32 ? "f32" : "f64", nx, ny, nz);
+    const std::string kbest = std::string(key) + "|best", kpow2 = std::string(key) + "|pow2";
+    int c0, c1, c2, q0, q1, q2;
+    double mb = 0, mp = 0;
+    if (use_cache && tune_lookup(kbest, c0, c1, c2, mb) && tune_lookup(kpow2, q0, q1, q2, mp)) {
+        memset(best, 0, sizeof *best);
+        best->px = c0; best->py = c1; best->pz = c2;
+        if (ms_best) *ms_best = mb;
+        if (ms_pow2) *ms_pow2 = mp;
+        return DEMAG_OK;
+    }
+    // candidate lengths per axis: the power of two first
+    std::vector<int> cand[3];
+    for (int a = 0; a < 3; ++a) {
+        cand[a].push_back(default_pad(n[a]));
+        if (smooth_pad(n[a]) != cand[a][0]) cand[a].push_back(smooth_pad(n[a]));
+    }
+    double tbest = 1e30, tpow2 = -1;
+    int bP[3] = {0, 0, 0};
+    for (int i : cand[0])
+        for (int j : cand[1])
+            for (int k : cand[2]) {
+                demag_options o;
+                memset(&o, 0, sizeof o);
+                o.px = i; o.py = j; o.pz = k;
+                demag_plan_t p = nullptr;
+                demag_status s = demag_plan_create_ex(nx, ny, nz, dx, dy, dz, prec, &o, &p);
+                double ms = 0;
+                if (s == DEMAG_OK) s = demag_tensor_setup(p, stream);
+                if (s == DEMAG_OK) s = demag_autotune(p, use_cache, &ms, stream);
+                demag_plan_destroy(p);
+                if (s != DEMAG_OK) return s;
+                if (i == cand[0][0] && j == cand[1][0] && k == cand[2][0]) tpow2 = ms;
+                if (ms < tbest) {
+                    tbest = ms;
+                    bP[0] = i; bP[1] = j; bP[2] = k;
+                }
+            }
+    memset(best, 0, sizeof *best);
+    best->px = bP[0]; best->py = bP[1]; best->pz = bP[2];
+    if (ms_best) *ms_best = tbest;
+    if (ms_pow2) *ms_pow2 = tpow2;
+    if (use_cache) {
+        tune_store(kbest, bP[0], bP[1], bP[2], tbest);
+        tune_store(kpow2, cand[0][0], cand[1][0], cand[2][0], tpow2);
+    }
+    g_err.clear();
     return DEMAG_OK;
 }
 

@@ -558,8 +558,16 @@ extern "C" {
 
 demag_status demag_batch_create(int n, const int *dims, const double *cells, demag_prec prec, demag_batch_t *out)
 {
+    return demag_batch_create_ex(n, dims, cells, prec, nullptr, out);
+}
+
+demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, demag_prec prec,
+                                   const demag_options *opt, demag_batch_t *out)
+{
     if (!out) return bfail(DEMAG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    if (opt && (opt->px || opt->py || opt->pz))
+        return bfail(DEMAG_ERR_INVALID_ARG, "batch options take a pad_mode only (no explicit lengths)");
     if (n < 1 || !dims || !cells) return bfail(DEMAG_ERR_INVALID_ARG, "need n >= 1 and the size arrays");
     demag_batch *b = new demag_batch();
     b->n = n;
@@ -572,8 +580,8 @@ demag_status demag_batch_create(int n, const int *dims, const double *cells, dem
     }
     b->plans.assign(n, nullptr);
     for (int i = 0; i < n; ++i) {
-        demag_status s = demag_plan_create(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], cells[3 * i],
-                                           cells[3 * i + 1], cells[3 * i + 2], prec, &b->plans[i]);
+        demag_status s = demag_plan_create_ex(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], cells[3 * i],
+                                              cells[3 * i + 1], cells[3 * i + 2], prec, opt, &b->plans[i]);
         if (s == DEMAG_OK) s = demag_tensor_setup(b->plans[i], nullptr);
         if (s != DEMAG_OK) {
             demag::set_last_error(std::string("state ") + std::to_string(i) + ": " + demag_last_error());

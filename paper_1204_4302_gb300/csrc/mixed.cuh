@@ -4,131 +4,148 @@
 // next power of two (e.g. n = 80: 160 instead of 256 per axis). These kernels
 // trade the compile-time register schedules of the power-of-two passes for
 // one generic form: a tile of transforms in shared memory, Stockham stages of
-// radix 8, 4, 2, 3, 5 or 7 run with a runtime radix list, ping-ponging between
-// two buffers. Same inputs, outputs and epilogues as the power-of-two passes.
+// radix 2, 4, 8, 16, 3, 5, 7 or 9 run from a runtime radix list, ping-ponging
+// between two buffers. Same inputs, outputs and epilogues as the power-of-two
+// passes.
 #pragma once
 #include "fft_engine.cuh"
 
 namespace demag {
 
-// Radices of one transform, in stage order (product L).
+// Stage plan of one transform of length L (product of the radices), with
+// the multipliers that replace the runtime divisions of the index
+// arithmetic: q = umulhi(n, m) with m = ceil(2^32 / d) equals n / d for every
+// n d < 2^32 (here n < 2^13, d < 2^11), and d == 1 is taken apart.
+constexpr int kGenMaxStages = 12;
 struct GenRadix {
-    int L;
-    int n;
-    int r[16];
+    int L, n, TC;                  // length, stages, transforms per tile
+    int r[kGenMaxStages];          // radices in stage order
+    int NS[kGenMaxStages];         // product of the earlier radices
+    unsigned mNS[kGenMaxStages];   // division by NS
+    unsigned mPer[kGenMaxStages];  // division by (L / r) TC
+    unsigned mTC, mL, mL1;         // division by TC, L, L + 1
 };
 
 constexpr int kGenThreads = 256;
-constexpr int kGenTileElems = 2048;  // transform elements per buffer (L x columns)
 
-// DFT of 3 points: y_k = sum_j x_j w^{jk}, w = exp(-+2 pi i / 3).
-template <bool INV, typename C>
-__device__ __forceinline__ void dft3(C *v)
+__device__ __forceinline__ int udiv(int n, int d, unsigned m)
 {
-    using T = decltype(C::x);
-    const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
-    const C t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-    const C y0 = cadd(v[0], t1);
-    const C m = cmk<C>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
-    // forward: y1 = m - i h t2, y2 = m + i h t2 (inverse: signs swapped)
-    const C s = INV ? cmk<C>(-h * t2.y, h * t2.x) : cmk<C>(h * t2.y, -h * t2.x);
-    v[0] = y0;
-    v[1] = cadd(m, s);
-    v[2] = csub(m, s);
+    return d == 1 ? n : (int)__umulhi((unsigned)n, m);
 }
 
-// DFT of 5 points with the angles 2 pi / 5 and 4 pi / 5.
-template <bool INV, typename C>
-__device__ __forceinline__ void dft5(C *v)
+// cos and sin of 2 pi q / R for the odd radices (q = 1 .. (R - 1) / 2).
+template <int R> __device__ __forceinline__ double cos_tab(int q);
+template <int R> __device__ __forceinline__ double sin_tab(int q);
+template <> __device__ __forceinline__ double cos_tab<3>(int) { return -0.5; }
+template <> __device__ __forceinline__ double sin_tab<3>(int) { return 0.866025403784438646764; }
+template <> __device__ __forceinline__ double cos_tab<5>(int q)
 {
-    using T = decltype(C::x);
-    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
-    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
-    const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-    const C y0 = cadd(v[0], cadd(t1, t2));
-    const C a1 = cmk<C>(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
-    const C a2 = cmk<C>(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
-    const C b1 = cmk<C>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
-    const C b2 = cmk<C>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
-    // forward: y1 = a1 - i b1, y4 = a1 + i b1, y2 = a2 - i b2, y3 = a2 + i b2
-    const C ib1 = INV ? cmk<C>(-b1.y, b1.x) : cmk<C>(b1.y, -b1.x);
-    const C ib2 = INV ? cmk<C>(-b2.y, b2.x) : cmk<C>(b2.y, -b2.x);
-    v[0] = y0;
-    v[1] = cadd(a1, ib1);
-    v[4] = csub(a1, ib1);
-    v[2] = cadd(a2, ib2);
-    v[3] = csub(a2, ib2);
+    return q == 1 ? 0.309016994374947424102 : -0.809016994374947424102;
+}
+template <> __device__ __forceinline__ double sin_tab<5>(int q)
+{
+    return q == 1 ? 0.951056516295153572116 : 0.587785252292473129169;
+}
+template <> __device__ __forceinline__ double cos_tab<7>(int q)
+{
+    return q == 1 ? 0.623489801858733530525 : q == 2 ? -0.222520933956314404289 : -0.900968867902419126236;
+}
+template <> __device__ __forceinline__ double sin_tab<7>(int q)
+{
+    return q == 1 ? 0.781831482468029808708 : q == 2 ? 0.974927912181823607018 : 0.433883739117558120476;
+}
+template <> __device__ __forceinline__ double cos_tab<9>(int q)
+{
+    return q == 1 ? 0.766044443118978035202
+         : q == 2 ? 0.173648177666930348852
+         : q == 3 ? -0.5
+                  : -0.939692620785908384054;
+}
+template <> __device__ __forceinline__ double sin_tab<9>(int q)
+{
+    return q == 1 ? 0.642787609686539326323
+         : q == 2 ? 0.984807753012208059367
+         : q == 3 ? 0.866025403784438646764
+                  : 0.342020143325668733044;
 }
 
-// DFT of 7 points: pairs x_k +- x_{7-k}, k = 1..3, against cos and sin of
-// 2 pi k m / 7 (y_m = a_m - i b_m, y_{7-m} = a_m + i b_m in the forward sense).
-template <bool INV, typename C>
-__device__ __forceinline__ void dft7(C *v)
+// DFT of an odd number R of points, y_m = sum_j x_j w^{jm}, w = exp(-+2 pi i / R):
+// with t_k = x_k + x_{R-k} and u_k = x_k - x_{R-k} (k = 1 .. H, H = (R-1)/2),
+// a_m = x_0 + sum_k cos(2 pi k m / R) t_k and b_m = sum_k sin(2 pi k m / R) u_k,
+// y_m = a_m -+ i b_m and y_{R-m} = a_m +- i b_m.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dft_odd(C *v)
 {
     using T = decltype(C::x);
-    const T c[3] = {(T)0.623489801858733530525, (T)-0.222520933956314404289, (T)-0.900968867902419126236};
-    const T s[3] = {(T)0.781831482468029808708, (T)0.974927912181823607018, (T)0.433883739117558120476};
-    C t[3], u[3];
+    constexpr int H = (R - 1) / 2;
+    C t[H], u[H];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        t[k] = cadd(v[k + 1], v[6 - k]);
-        u[k] = csub(v[k + 1], v[6 - k]);
+    for (int k = 0; k < H; ++k) {
+        t[k] = cadd(v[k + 1], v[R - 1 - k]);
+        u[k] = csub(v[k + 1], v[R - 1 - k]);
     }
     const C x0 = v[0];
-    v[0] = cadd(x0, cadd(t[0], cadd(t[1], t[2])));
+    C y0 = x0;
 #pragma unroll
-    for (int m = 1; m <= 3; ++m) {
+    for (int k = 0; k < H; ++k) y0 = cadd(y0, t[k]);
+    v[0] = y0;
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
         C a = x0, b = cmk<C>(0, 0);
 #pragma unroll
-        for (int k = 1; k <= 3; ++k) {
-            const int q = (k * m) % 7;  // angle index of 2 pi k m / 7
-            const T cq = q <= 3 ? c[q - 1] : c[7 - q - 1];
-            const T sq = q <= 3 ? s[q - 1] : -s[7 - q - 1];
+        for (int k = 1; k <= H; ++k) {
+            const int q = (k * m) % R;  // angle 2 pi q / R (q = 0 only for R = 9)
+            const T cq = (T)(q == 0 ? 1.0 : q <= H ? cos_tab<R>(q) : cos_tab<R>(R - q));
+            const T sq = (T)(q == 0 ? 0.0 : q <= H ? sin_tab<R>(q) : -sin_tab<R>(R - q));
             a = cmk<C>(a.x + cq * t[k - 1].x, a.y + cq * t[k - 1].y);
             b = cmk<C>(b.x + sq * u[k - 1].x, b.y + sq * u[k - 1].y);
         }
         const C ib = INV ? cmk<C>(-b.y, b.x) : cmk<C>(b.y, -b.x);
         v[m] = cadd(a, ib);
-        v[7 - m] = csub(a, ib);
+        v[R - m] = csub(a, ib);
     }
 }
 
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void small_dft(C *v)
 {
-    if constexpr (R == 3) dft3<INV, C>(v);
-    else if constexpr (R == 5) dft5<INV, C>(v);
-    else if constexpr (R == 7) dft7<INV, C>(v);
+    if constexpr (R % 2 == 1) dft_odd<R, INV, C>(v);
     else RegDFT<R, INV, C>::run(v);
 }
 
-// One Stockham stage of radix R from src to dst, ncomp tiles [L][TC] each
-// (component stride cstride, swizzled as everywhere). NS = product of the
-// earlier radices; tw: table W_P^m of the axis with P = L twstride.
+// One Stockham stage s of radix R from src to dst, ncomp tiles of [L][TC]
+// (component stride cstride, swizzled as everywhere). Butterfly b of a
+// component: j = b / TC (0 <= j < L / R), column b % TC; it reads rows
+// j + r L / R, applies W^{r k} (k = j mod NS, W the root of order NS R) and
+// writes rows (j / NS) NS R + k + r NS. tw: W_P^m with P = L twstride.
 template <typename C, int R, bool INV>
-__device__ __forceinline__ void gen_stage(const C *src, C *dst, int ncomp, int cstride, int L, int NS, int TC,
+__device__ __forceinline__ void gen_stage(const C *src, C *dst, int ncomp, int cstride, const GenRadix &g, int s,
                                           const C *__restrict__ tw, int twstride)
 {
+    const int L = g.L, TC = g.TC, NS = g.NS[s];
     const int NB = L / R, per = NB * TC, total = ncomp * per;
     const int tws = (L / (NS * R)) * twstride;
+    const unsigned mPer = g.mPer[s], mNS = g.mNS[s], mTC = g.mTC;
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int comp = b / per, bb = b - comp * per;
-        const int col = bb % TC, j = bb / TC;
-        const C *s = src + comp * cstride;
+        const int comp = ncomp == 1 ? 0 : udiv(b, per, mPer);
+        const int bb = b - comp * per;
+        const int j = udiv(bb, TC, mTC), col = bb - j * TC;
+        const C *sp = src + comp * cstride;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[sw((j + r * NB) * TC + col)];
-        const int k = j % NS;
-        if (NS > 1) {
+        for (int r = 0; r < R; ++r) v[r] = sp[sw((j + r * NB) * TC + col)];
+        const int q = udiv(j, NS, mNS), k = j - q * NS;
+        if (k > 0) {
+            const int kt = k * tws;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const C w = __ldg(&tw[r * k * tws]);
+                const C w = __ldg(&tw[r * kt]);
                 v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
             }
         }
         small_dft<R, INV, C>(v);
-        const int d = (j / NS) * NS * R + k;
         C *o = dst + comp * cstride;
+        const int d = q * NS * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) o[sw((d + r * NS) * TC + col)] = v[r];
     }
@@ -137,23 +154,22 @@ __device__ __forceinline__ void gen_stage(const C *src, C *dst, int ncomp, int c
 // Whole transform of the tiles in a (b is the second buffer); returns the
 // buffer that holds the result.
 template <typename C, bool INV>
-__device__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const GenRadix &g, int TC, const C *__restrict__ tw,
-                      int twstride)
+__device__ __forceinline__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const GenRadix &g, const C *__restrict__ tw,
+                                      int twstride)
 {
     C *src = a, *dst = b;
-    int NS = 1;
     for (int s = 0; s < g.n; ++s) {
-        const int R = g.r[s];
-        switch (R) {
-        case 2: gen_stage<C, 2, INV>(src, dst, ncomp, cstride, g.L, NS, TC, tw, twstride); break;
-        case 3: gen_stage<C, 3, INV>(src, dst, ncomp, cstride, g.L, NS, TC, tw, twstride); break;
-        case 4: gen_stage<C, 4, INV>(src, dst, ncomp, cstride, g.L, NS, TC, tw, twstride); break;
-        case 5: gen_stage<C, 5, INV>(src, dst, ncomp, cstride, g.L, NS, TC, tw, twstride); break;
-        case 7: gen_stage<C, 7, INV>(src, dst, ncomp, cstride, g.L, NS, TC, tw, twstride); break;
-        default: gen_stage<C, 8, INV>(src, dst, ncomp, cstride, g.L, NS, TC, tw, twstride); break;
+        switch (g.r[s]) {
+        case 2: gen_stage<C, 2, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 3: gen_stage<C, 3, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 4: gen_stage<C, 4, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 5: gen_stage<C, 5, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 7: gen_stage<C, 7, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 8: gen_stage<C, 8, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 9: gen_stage<C, 9, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        default: gen_stage<C, 16, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
         }
         __syncthreads();
-        NS *= R;
         C *t = src;
         src = dst;
         dst = t;
@@ -161,68 +177,69 @@ __device__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const GenRadix &g, int
     return src;
 }
 
-// Column transforms (as k_col2): TC columns per CTA, rows < nin read, rows
-// < nout written.
+// Column transforms (as k_col2): g.TC columns per CTA, rows < nin read,
+// rows < nout written; column f = slab * width + (f mod width), mw the
+// multiplier of width.
 template <typename T, bool INV>
 __global__ void __launch_bounds__(kGenThreads)
 k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols, int width,
-          int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
-          const typename Cplx<T>::type *__restrict__ tw, int twstride, GenRadix g, int TC)
+          unsigned mw, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
+          const typename Cplx<T>::type *__restrict__ tw, int twstride, const __grid_constant__ GenRadix g)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int L = g.L, TS = swsize(L * TC);
+    const int L = g.L, TC = g.TC, TS = swsize(L * TC);
     C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
     const int f0 = blockIdx.x * TC;
     for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int c = e % TC, r = e / TC, f = f0 + c;
+        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
         C v = cmk<C>(0, 0);
         if (f < ncols && r < nin) {
-            const int slab = f / width;
+            const int slab = udiv(f, width, mw);
             v = in[(int64_t)slab * iss + (int64_t)r * irs + (f - slab * width)];
         }
         A[sw(e)] = v;
     }
     __syncthreads();
-    const C *res = gen_fft<C, INV>(A, B, 1, 0, g, TC, tw, twstride);
-    for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int c = e % TC, r = e / TC, f = f0 + c;
-        if (f < ncols && r < nout) {
-            const int slab = f / width;
+    const C *res = gen_fft<C, INV>(A, B, 1, 0, g, tw, twstride);
+    for (int e = threadIdx.x; e < nout * TC; e += blockDim.x) {
+        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
+        if (f < ncols) {
+            const int slab = udiv(f, width, mw);
             out[(int64_t)slab * oss + (int64_t)r * ors + (f - slab * width)] = res[sw(e)];
         }
     }
 }
 
 // Real-to-complex rows (as k_x_fwd): pack pairs of reals, transform of
-// L = Px/2 points, split into X[k], k = 0..L. TR rows per CTA.
+// L = Px/2 points, split into X[k], k = 0..L. g.TC rows per CTA.
 template <typename T>
 __global__ void __launch_bounds__(kGenThreads)
 k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
-            const typename Cplx<T>::type *__restrict__ twx, GenRadix g, int TR)
+            const typename Cplx<T>::type *__restrict__ twx, const __grid_constant__ GenRadix g)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int L = g.L, TS = swsize(L * TR);
+    const int L = g.L, TR = g.TC, TS = swsize(L * TR);
     C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
     const int row0 = blockIdx.x * TR;
     for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
-        const int n = e % L, rr = e / L, row = row0 + rr;
+        const int rr = udiv(e, L, g.mL), n = e - rr * L, row = row0 + rr;
         C z = cmk<C>(0, 0);
-        if (row < nrows) {
+        const int x0 = 2 * n;
+        if (row < nrows && x0 < nvalid) {
             const T *p = a.in + (int64_t)row * a.in_rs;
-            const int x0 = 2 * n;
-            if (x0 < nvalid) z.x = p[x0] * a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
+            z.x = p[x0] * a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
             if (x0 + 1 < nvalid)
                 z.y = p[x0 + 1] * a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0 + 1);
         }
         A[sw(n * TR + rr)] = z;
     }
     __syncthreads();
-    const C *Z = gen_fft<C, false>(A, B, 1, 0, g, TR, twx, 2);
+    const C *Z = gen_fft<C, false>(A, B, 1, 0, g, twx, 2);
     const T h = (T)0.5;
     for (int e = threadIdx.x; e < (L + 1) * TR; e += blockDim.x) {
-        const int k = e % (L + 1), rr = e / (L + 1), row = row0 + rr;
+        const int rr = udiv(e, L + 1, g.mL1), k = e - rr * (L + 1), row = row0 + rr;
         if (row >= nrows) continue;
         const C p = Z[sw((k == L ? 0 : k) * TR + rr)];
         const C q = Z[sw((k == 0 ? 0 : L - k) * TR + rr)];
@@ -237,15 +254,15 @@ k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict_
 template <typename T>
 __global__ void __launch_bounds__(kGenThreads)
 k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
-            const typename Cplx<T>::type *__restrict__ twx, GenRadix g, int TR)
+            const typename Cplx<T>::type *__restrict__ twx, const __grid_constant__ GenRadix g)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int L = g.L, TS = swsize(L * TR);
+    const int L = g.L, TR = g.TC, TS = swsize(L * TR);
     C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
     const int row0 = blockIdx.x * TR;
     for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
-        const int k = e % L, rr = e / L, row = row0 + rr;
+        const int rr = udiv(e, L, g.mL), k = e - rr * L, row = row0 + rr;
         C z = cmk<C>(0, 0);
         if (row < nrows) {
             const C *p = in + (int64_t)row * in_rs;
@@ -258,13 +275,15 @@ k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nr
         A[sw(k * TR + rr)] = z;
     }
     __syncthreads();
-    const C *Z = gen_fft<C, true>(A, B, 1, 0, g, TR, twx, 2);
+    const C *Z = gen_fft<C, true>(A, B, 1, 0, g, twx, 2);
     const T gsc = o.gdev ? (T)(*o.gdev) : (T)1;
     const T oscale = o.oscale * gsc;
     T acc = 0;
+    // outputs x < nvalid only: n < (nvalid + 1) / 2 of each row
+    const int nh = (nvalid + 1) / 2 < L ? (nvalid + 1) / 2 : L;
     for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
-        const int n = e % L, rr = e / L, row = row0 + rr;
-        if (row >= nrows) continue;
+        const int rr = udiv(e, L, g.mL), n = e - rr * L, row = row0 + rr;
+        if (row >= nrows || n >= nh) continue;
         const C z = Z[sw(n * TR + rr)];
         const T hv[2] = {z.x * o.scale, z.y * o.scale};
 #pragma unroll
@@ -285,34 +304,34 @@ k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nr
 // transforms, rows < nrows stored. Column f = ky * width + kx.
 template <typename T>
 __global__ void __launch_bounds__(kGenThreads)
-k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
-            int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
-            int twstride, GenRadix g, int TC)
+k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsigned mw, int64_t ss, int64_t rs,
+            int64_t cs, int nrows, const T *__restrict__ nhat, int Py, int Kx,
+            const typename Cplx<T>::type *__restrict__ tw, int twstride, const __grid_constant__ GenRadix g)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int L = g.L, TS = swsize(L * TC);
+    const int L = g.L, TC = g.TC, TS = swsize(L * TC);
     C *A = reinterpret_cast<C *>(smraw), *B = A + 3 * TS;
     const int f0 = blockIdx.x * TC;
     for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int c = e % TC, r = e / TC, f = f0 + c;
+        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
         C v0 = cmk<C>(0, 0), v1 = v0, v2 = v0;
         if (f < ncols && r < nrows) {
-            const int slab = f / width;
+            const int slab = udiv(f, width, mw);
             const int64_t q = (int64_t)slab * ss + (int64_t)r * rs + (f - slab * width);
             v0 = S[q]; v1 = S[q + cs]; v2 = S[q + 2 * cs];
         }
         A[sw(e)] = v0; A[TS + sw(e)] = v1; A[2 * TS + sw(e)] = v2;
     }
     __syncthreads();
-    C *F = gen_fft<C, false>(A, B, 3, TS, g, TC, tw, twstride);
+    C *F = gen_fft<C, false>(A, B, 3, TS, g, tw, twstride);
     C *G = F == A ? B : A;
     const int hy = Py / 2 + 1, hz = L / 2 + 1;
     const int64_t plane = (int64_t)hz * hy * Kx;
     for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int c = e % TC, kz = e / TC, f = f0 + c;
+        const int kz = udiv(e, TC, g.mTC), f = f0 + e - kz * TC;
         if (f >= ncols) continue;
-        const int ky = f / width, kx = f - ky * width;
+        const int ky = udiv(f, width, mw), kx = f - ky * width;
         const bool fy = ky > Py / 2, fz = kz > L / 2;
         const int kyf = fy ? Py - ky : ky, kzf = fz ? L - kz : kz;
         const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
@@ -327,11 +346,11 @@ k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_
         F[2 * TS + sw(e)] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
     }
     __syncthreads();
-    const C *res = gen_fft<C, true>(F, G, 3, TS, g, TC, tw, twstride);
-    for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int c = e % TC, r = e / TC, f = f0 + c;
-        if (f < ncols && r < nrows) {
-            const int slab = f / width;
+    const C *res = gen_fft<C, true>(F, G, 3, TS, g, tw, twstride);
+    for (int e = threadIdx.x; e < nrows * TC; e += blockDim.x) {
+        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
+        if (f < ncols) {
+            const int slab = udiv(f, width, mw);
             const int64_t q = (int64_t)slab * ss + (int64_t)r * rs + (f - slab * width);
             S[q] = res[sw(e)]; S[q + cs] = res[TS + sw(e)]; S[q + 2 * cs] = res[2 * TS + sw(e)];
         }

@@ -56,28 +56,54 @@ cudaError_t allow_smem(size_t bytes)
     return bytes <= limit ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Mixed-radix plan of a length that is not a power of two (factors 2, 3, 5, 7).
-bool gen_radix(int L, GenRadix &g)
-{
-    g.L = L;
-    g.n = 0;
-    int m = L;
-    while (m % 8 == 0 && g.n < 16) { g.r[g.n++] = 8; m /= 8; }
-    if (m % 4 == 0 && g.n < 16) { g.r[g.n++] = 4; m /= 4; }
-    if (m % 2 == 0 && g.n < 16) { g.r[g.n++] = 2; m /= 2; }
-    while (m % 3 == 0 && g.n < 16) { g.r[g.n++] = 3; m /= 3; }
-    while (m % 5 == 0 && g.n < 16) { g.r[g.n++] = 5; m /= 5; }
-    while (m % 7 == 0 && g.n < 16) { g.r[g.n++] = 7; m /= 7; }
-    return m == 1;
-}
-
 bool pow2_len(int L) { return L > 0 && (L & (L - 1)) == 0; }
 
-// transforms per CTA of the mixed-radix kernels (L x tile <= kGenTileElems)
-int gen_tile(int L)
+// ceil(2^32 / d): n / d == umulhi(n, magic) for n d < 2^32 (d == 1 apart)
+unsigned magic_of(int d) { return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d); }
+
+// Elements per tile of the mixed-radix kernels: the column and row passes
+// hold two buffers, the z pass six (three components, ping-pong).
+template <typename T> constexpr int gen_tile_elems(bool zpass)
 {
-    const int t = kGenTileElems / L;
-    return t < 1 ? 1 : t;
+    return sizeof(T) == 4 ? (zpass ? 2048 : 4096) : (zpass ? 1024 : 2048);
+}
+
+// Stage plan of a mixed-radix transform of length L (a product of 2, 3, 5
+// and 7, L < 2048) over tiles of about `tile` elements: the power of two in
+// L as even stages of radix <= 16, then radix 9 for pairs of threes, 3, 5, 7.
+bool gen_plan(int L, int tile, GenRadix &g)
+{
+    memset(&g, 0, sizeof g);
+    if (L < 2 || L >= 2048) return false;
+    g.L = L;
+    g.TC = tile / L > 1 ? tile / L : 1;
+    int m = L, a = 0, f3 = 0, f5 = 0, f7 = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++f3; }
+    while (m % 5 == 0) { m /= 5; ++f5; }
+    while (m % 7 == 0) { m /= 7; ++f7; }
+    if (m != 1) return false;
+    int r[32], n = 0;
+    const int n2 = (a + 3) / 4;
+    for (int s = 0; s < n2; ++s) r[n++] = 1 << (a / n2 + (s < a % n2 ? 1 : 0));
+    for (int i = 0; i < f3 / 2; ++i) r[n++] = 9;
+    if (f3 % 2) r[n++] = 3;
+    for (int i = 0; i < f5; ++i) r[n++] = 5;
+    for (int i = 0; i < f7; ++i) r[n++] = 7;
+    if (n > kGenMaxStages) return false;
+    int NS = 1;
+    for (int s = 0; s < n; ++s) {
+        g.r[s] = r[s];
+        g.NS[s] = NS;
+        g.mNS[s] = magic_of(NS);
+        g.mPer[s] = magic_of(L / r[s] * g.TC);
+        NS *= r[s];
+    }
+    g.n = n;
+    g.mTC = magic_of(g.TC);
+    g.mL = magic_of(L);
+    g.mL1 = magic_of(L + 1);
+    return true;
 }
 
 template <typename T>
@@ -356,12 +382,11 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
     if (nrows <= 0) return cudaSuccess;
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
-        const int TR = gen_tile(L);
-        const size_t sm = 2 * swsize(L * TR) * sizeof(C);
+        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return cudaErrorInvalidValue;
+        const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
         cudaError_t e = allow_smem<k_gen_x_fwd<T>>(sm);
         if (e != cudaSuccess) return e;
-        k_gen_x_fwd<T><<<(nrows + TR - 1) / TR, kGenThreads, sm, st>>>(a, nrows, nvalid, out, out_rs, twx, g, TR);
+        k_gen_x_fwd<T><<<(nrows + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(a, nrows, nvalid, out, out_rs, twx, g);
         return cudaGetLastError();
     }
     // pipelined form: rows of the plain field (no per-cell weight) stored back
@@ -412,7 +437,11 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
 template <typename T>
 int Passes<T>::x_blocks(int L, int nrows)
 {
-    if (!pow2_len(L)) return (nrows + gen_tile(L) - 1) / gen_tile(L);
+    if (!pow2_len(L)) {
+        GenRadix g;
+        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return 1;
+        return (nrows + g.TC - 1) / g.TC;
+    }
     int rows_per_cta;
     switch (L) {
     case 64: rows_per_cta = XShape<T, 64>::TR; break;
@@ -431,12 +460,11 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
     if (nrows <= 0) return cudaSuccess;
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
-        const int TR = gen_tile(L);
-        const size_t sm = 2 * swsize(L * TR) * sizeof(C);
+        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return cudaErrorInvalidValue;
+        const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
         cudaError_t e = allow_smem<k_gen_x_inv<T>>(sm);
         if (e != cudaSuccess) return e;
-        k_gen_x_inv<T><<<(nrows + TR - 1) / TR, kGenThreads, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, g, TR);
+        k_gen_x_inv<T><<<(nrows + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, g);
         return cudaGetLastError();
     }
     if (variant == 2 && L >= 64 && in_rs % 2 == 0 && in_rs <= 2 * L && nvalid <= L + 1 && ((uintptr_t)in & 15) == 0) {
@@ -506,18 +534,19 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
     if (ncols <= 0) return cudaSuccess;
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
-        const int TC = gen_tile(L);
-        const size_t sm = 2 * swsize(L * TC) * sizeof(C);
+        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return cudaErrorInvalidValue;
+        const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
+        const unsigned mw = magic_of(width);
+        const int grid = (ncols + g.TC - 1) / g.TC;
         cudaError_t e;
         if (inv) {
             if ((e = allow_smem<k_gen_col<T, true>>(sm)) != cudaSuccess) return e;
-            k_gen_col<T, true><<<(ncols + TC - 1) / TC, kGenThreads, sm, st>>>(in, out, ncols, width, iss, irs, nin, oss,
-                                                                               ors, nout, tw, twstride, g, TC);
+            k_gen_col<T, true><<<grid, kGenThreads, sm, st>>>(in, out, ncols, width, mw, iss, irs, nin, oss, ors, nout,
+                                                              tw, twstride, g);
         } else {
             if ((e = allow_smem<k_gen_col<T, false>>(sm)) != cudaSuccess) return e;
-            k_gen_col<T, false><<<(ncols + TC - 1) / TC, kGenThreads, sm, st>>>(in, out, ncols, width, iss, irs, nin,
-                                                                                oss, ors, nout, tw, twstride, g, TC);
+            k_gen_col<T, false><<<grid, kGenThreads, sm, st>>>(in, out, ncols, width, mw, iss, irs, nin, oss, ors,
+                                                               nout, tw, twstride, g);
         }
         return cudaGetLastError();
     }
@@ -618,13 +647,12 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
     if (ncols > 0 && !pow2_len(L)) {
         if (nrows > L) return cudaErrorInvalidValue;
         GenRadix g;
-        if (!gen_radix(L, g)) return cudaErrorInvalidValue;
-        const int TC = gen_tile(L);
-        const size_t sm = 6 * swsize(L * TC) * sizeof(C);
+        if (!gen_plan(L, gen_tile_elems<T>(true), g)) return cudaErrorInvalidValue;
+        const size_t sm = 6 * swsize(L * g.TC) * sizeof(C);
         cudaError_t e = allow_smem<k_gen_zconv<T>>(sm);
         if (e != cudaSuccess) return e;
-        k_gen_zconv<T><<<(ncols + TC - 1) / TC, kGenThreads, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx,
-                                                                       tw, twstride, g, TC);
+        k_gen_zconv<T><<<(ncols + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(S, ncols, width, magic_of(width), ss, rs, cs,
+                                                                           nrows, nhat, Py, Kx, tw, twstride, g);
         return cudaGetLastError();
     }
     if (variant == 5 && ncols > 0 && 2 * nrows <= L) {

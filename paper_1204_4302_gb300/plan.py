@@ -21,7 +21,9 @@ class Plan:
 
     pad: None or "pow2" pads each axis to the smallest power of two >= 2n - 1;
     "smooth" to the smallest even length >= 2n - 1 with prime factors 2, 3, 5
-    and 7 (mixed-radix passes, DM only); or explicit (px, py, pz)."""
+    and 7 (mixed-radix passes, DM only); "tuned" to the per-axis choice of the
+    two that the padding autotuner finds fastest (timed once, then cached);
+    or explicit (px, py, pz)."""
 
     def __init__(self, n, d, prec: str = "f32", pad=None, device=None, setup: bool = True,
                  method: str = "dm"):
@@ -48,6 +50,8 @@ class Plan:
                 self.handle = B.demag_plan_create(nx, ny, nz, *self.d, code)
             elif pad == "smooth":
                 self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, pad_mode=B.DEMAG_PAD_SMOOTH)
+            elif pad == "tuned":
+                self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, pad_mode=B.DEMAG_PAD_TUNED)
             else:
                 self.handle = B.demag_plan_create_ex(nx, ny, nz, *self.d, code, *pad)
         self.shape = (3, nz, ny, nx)

@@ -166,3 +166,45 @@ def test_mixed_radix_large_point_sources(n, d, P):
         plan.close()
         del M, H
         torch.cuda.empty_cache()
+
+
+def test_padding_autotuner_and_tuned_plan(tmp_path, monkeypatch):
+    """The padding autotuner times every per-axis choice of power-of-two or
+    smooth length; a plan created with pad="tuned" takes its choice (from the
+    cache) and its field matches the oracle."""
+    from paper_1204_4302_gb300 import binding as B
+    monkeypatch.setenv("DEMAG_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    n, d = (70, 40, 20), (1e-9, 1e-9, 1e-9)
+    P, ms_best, ms_pow2 = B.demag_tune_padding(*n, *d, B.DEMAG_F32, use_cache=True)
+    assert P[0] in (256, 140) and P[1] in (128, 80) and P[2] in (64, 40)
+    assert 0 < ms_best <= ms_pow2
+    P2, mb2, mp2 = B.demag_tune_padding(*n, *d, B.DEMAG_F32, use_cache=True)  # from the cache file
+    assert P2 == P and mb2 == pytest.approx(ms_best, abs=1e-6) and mp2 == pytest.approx(ms_pow2, abs=1e-6)
+    plan = _plan(n, d, "f32", "tuned")
+    assert (plan.info()["px"], plan.info()["py"], plan.info()["pz"]) == P
+    M = 8e5 * inputs.random_unit(n, seed=77)
+    H = plan.field(torch.tensor(M, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert _relmax(H, oracle.field_fft(M, d)) <= TOL["f32"]
+    plan.close()
+
+
+@pytest.mark.parametrize("pad", ["smooth", "tuned"])
+def test_batch_with_mixed_radix_padding(pad, tmp_path, monkeypatch):
+    """A batch of uneven grids padded to smooth lengths runs as a graph of
+    per-state branches; every state's field and energy against the oracle."""
+    from paper_1204_4302_gb300.batch import Batch
+    monkeypatch.setenv("DEMAG_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    dims = [(33, 20, 9), (40, 36, 12), (17, 65, 5), (24, 24, 24)]
+    cells = [(3e-9, 3e-9, 3e-9)] * len(dims)
+    b = Batch(dims, cells, pad=pad)
+    Ms = [8e5 * inputs.random_unit(n, seed=i) for i, n in enumerate(dims)]
+    Hs, E = b.field([torch.tensor(m, dtype=torch.float32, device="cuda") for m in Ms], energies=True)
+    torch.cuda.synchronize()
+    if pad == "smooth":
+        assert b.info()["mode"] == b.BRANCHES
+    for m, h, e, d in zip(Ms, Hs, E.cpu().numpy(), cells):
+        Href = oracle.field_fft(m, d)
+        assert _relmax(h.double().cpu().numpy(), Href) <= TOL["f32"]
+        Eref = oracle.energy(m, Href, d)
+        assert abs(e - Eref) <= 10 * TOL["f32"] * abs(Eref)
+    b.close()

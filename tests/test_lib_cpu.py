@@ -65,14 +65,16 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
 
 def test_padding_options_are_checked_before_any_device_call(lib):
     """Padded lengths: powers of two or even products of 2, 3, 5, 7, at least
-    2n - 1 and at most 1024; pad_mode 0 (powers of two) or 1 (smooth)."""
+    2n - 1 and at most 1024; pad_mode 0 (powers of two), 1 (smooth) or 2
+    (tuned, without explicit lengths); batches take a pad_mode only."""
     from paper_1204_4302_gb300 import binding
     bad = [({"px": 26}, "DEMAG_ERR_INVALID_ARG"),        # 2 x 13
            ({"px": 21}, "DEMAG_ERR_INVALID_ARG"),        # odd
            ({"py": 14}, "DEMAG_ERR_INVALID_ARG"),        # below 2n - 1
            ({"pz": 1050}, "DEMAG_ERR_UNSUPPORTED"),      # 2 3 5^2 7 > 1024
-           ({"pad_mode": 2}, "DEMAG_ERR_INVALID_ARG"),
-           ({"pad_mode": -1}, "DEMAG_ERR_INVALID_ARG")]
+           ({"pad_mode": 3}, "DEMAG_ERR_INVALID_ARG"),
+           ({"pad_mode": -1}, "DEMAG_ERR_INVALID_ARG"),
+           ({"pad_mode": 2, "px": 16}, "DEMAG_ERR_INVALID_ARG")]  # tuned: no explicit lengths
     for kw, status in bad:
         with pytest.raises(binding.DemagError) as e:
             binding.demag_plan_create_ex(8, 8, 8, 1.0, 1.0, 1.0, 0, **kw)
@@ -88,6 +90,18 @@ def test_padding_options_are_checked_before_any_device_call(lib):
     with pytest.raises(binding.DemagError) as e:
         binding.demag_plan_create_sp(8, 8, 8, 1.0, 1.0, 1.0, 0, pad_mode=1)
     assert e.value.name == "DEMAG_ERR_UNSUPPORTED"
+    import ctypes
+    lib_ = binding.load()
+    d = (ctypes.c_int * 3)(8, 8, 8)
+    c = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    h = ctypes.c_void_p()
+    opt = binding.demag_options(16, 0, 0, 0)
+    assert lib_.demag_batch_create_ex(1, d, c, 0, ctypes.byref(opt), ctypes.byref(h)) == 1
+    best = binding.demag_options()
+    assert lib_.demag_tune_padding(8, 8, 8, 1.0, 1.0, 1.0, 0, 0, None, None, None, None) == \
+        1  # DEMAG_ERR_INVALID_ARG
+    assert lib_.demag_tune_padding(0, 8, 8, 1.0, 1.0, 1.0, 0, 0, ctypes.byref(best), None, None, None) == \
+        1  # DEMAG_ERR_INVALID_ARG
 
 
 def test_sp_plan_arguments_are_checked_before_any_device_call(lib):
