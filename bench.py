@@ -405,6 +405,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.skip_tg:
         tgr = run_tg(args, dev, peak)
 
+    padding = None
+    if not args.skip_padding:
+        padding = run_padding(args, dev)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cpu = cpu_baseline(args.cpu_sample)
@@ -435,6 +439,7 @@ def run_ours(args, rank, world, local_rank):
             "batch": batch,
             "scalar_potential": sp,
             "tensor_grid": tgr,
+            "padding": padding,
             "energy_J": E_val,
             "passes": per_pass,
             "roofline": roof,
@@ -609,13 +614,70 @@ def run_batch(args, dev, rank):
     ms_call = e0.elapsed_time(e1) / k
     cells_total = sum(a * bb * c for a, bb, c in dims)
     info = b.info()
+    # the same states with every axis padded to the smallest even 2,3,5,7-smooth length
+    bs = Batch(dims, cells, pad="smooth")
+    bs.autotune(use_cache=False)
+    for _ in range(3):
+        B.demag_batch_field(bs.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+    e0.record(st)
+    for _ in range(k):
+        B.demag_batch_field(bs.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+    e1.record(st)
+    e1.synchronize()
+    bs.status()
+    ms_smooth = e0.elapsed_time(e1) / k
+    bs.close()
     out = {"workload": "64 states, 32..128 x 32..128 x 8..32 cells of 3 nm, FP32, field + energy",
            "cells": cells_total, "mode": "persistent" if info["mode"] == 0 else "graph branches",
            "ms_per_call": round(ms_call, 4), "cells_per_s": cells_total / (ms_call / 1e3),
            "ms_persistent": round(t_p, 4), "ms_branches": round(t_b, 4),
+           "ms_per_call_smooth_padding": round(ms_smooth, 4),
            "graph_launches_per_call": (b.launch_count() - l0) / k,
            "persistent_items": info["items"], "persistent_grid": info["grid"]}
     b.close()
+    return out
+
+
+def run_padding(args, dev):
+    """Padded lengths that are not powers of two (mixed-radix passes): grids
+    just above a power of two, FP32 field + energy per call with each plan
+    autotuned, padded to powers of two and to the smallest even 2,3,5,7-smooth
+    lengths; plus the padding autotuner's choice."""
+    import torch
+
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300 import inputs
+    from paper_1204_4302_gb300.plan import Plan
+    st = torch.cuda.current_stream(dev)
+    out = []
+    for n in ((130, 130, 130), (300, 260, 100), (100, 100, 100)):
+        M = torch.tensor(MS * inputs.random_unit(n, seed=SEED), dtype=torch.float32, device=dev)
+        H = torch.empty_like(M)
+        E = torch.empty((), dtype=torch.float64, device=dev)
+        row = {"grid": list(n)}
+        for pad in ("pow2", "smooth"):
+            plan = Plan(n, CELL, pad=pad, device=dev)
+            plan.autotune(use_cache=False)
+            for _ in range(max(3, args.warmup)):
+                B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
+            torch.cuda.synchronize()
+            k = max(10, args.steps)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(k):
+                B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
+            e1.record(st)
+            e1.synchronize()
+            info = plan.info()
+            row[pad] = {"padded": [info["px"], info["py"], info["pz"]], "ms_per_call": round(e0.elapsed_time(e1) / k, 4)}
+            plan.close()
+        P, mb, mp = B.demag_tune_padding(*n, *CELL, B.DEMAG_F32, use_cache=False, stream=st.cuda_stream)
+        row["tuned"] = {"padded": list(P), "ms_per_call": round(mb, 4)}
+        row["speedup_tuned_over_pow2"] = round(row["pow2"]["ms_per_call"] / row["tuned"]["ms_per_call"], 3)
+        out.append(row)
+        del M, H
+        torch.cuda.empty_cache()
     return out
 
 
@@ -704,6 +766,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-padding", action="store_true")
     ap.add_argument("--skip-sp", action="store_true", help="skip the scalar-potential method leg")
     ap.add_argument("--skip-tg", action="store_true", help="skip the tensor-grid method leg")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")
