@@ -3,11 +3,14 @@
 // and a smooth P just above 2n - 1 can hold far fewer padded cells than the
 // next power of two (e.g. n = 80: 160 instead of 256 per axis). These kernels
 // trade the compile-time register schedules of the power-of-two passes for
-// one generic form: a tile of transforms in shared memory, Stockham stages of
-// radix 2, 4, 8, 16, 3, 5, 7 or 9 run from a runtime radix list, ping-ponging
-// between two buffers. Same inputs, outputs and epilogues as the power-of-two
-// passes.
+// one generic form: a tile of transforms in shared memory, Stockham stages
+// of any radix R <= 32 with prime factors 2, 3, 5, 7 (in-register DFTs with
+// compile-time twiddles) run from a runtime radix list, ping-ponging between
+// two buffers; most lengths take two stages, like the power-of-two passes.
+// Same inputs, outputs and epilogues as the power-of-two passes.
 #pragma once
+#include <type_traits>
+
 #include "fft_engine.cuh"
 
 namespace demag {
@@ -33,7 +36,7 @@ __device__ __forceinline__ int udiv(int n, int d, unsigned m)
     return d == 1 ? n : (int)__umulhi((unsigned)n, m);
 }
 
-// cos and sin of 2 pi q / R for the odd radices (q = 1 .. (R - 1) / 2).
+// cos and sin of 2 pi q / R for the odd prime radices (q = 1 .. (R - 1) / 2).
 template <int R> __device__ __forceinline__ double cos_tab(int q);
 template <int R> __device__ __forceinline__ double sin_tab(int q);
 template <> __device__ __forceinline__ double cos_tab<3>(int) { return -0.5; }
@@ -54,21 +57,6 @@ template <> __device__ __forceinline__ double sin_tab<7>(int q)
 {
     return q == 1 ? 0.781831482468029808708 : q == 2 ? 0.974927912181823607018 : 0.433883739117558120476;
 }
-template <> __device__ __forceinline__ double cos_tab<9>(int q)
-{
-    return q == 1 ? 0.766044443118978035202
-         : q == 2 ? 0.173648177666930348852
-         : q == 3 ? -0.5
-                  : -0.939692620785908384054;
-}
-template <> __device__ __forceinline__ double sin_tab<9>(int q)
-{
-    return q == 1 ? 0.642787609686539326323
-         : q == 2 ? 0.984807753012208059367
-         : q == 3 ? 0.866025403784438646764
-                  : 0.342020143325668733044;
-}
-
 // DFT of an odd number R of points, y_m = sum_j x_j w^{jm}, w = exp(-+2 pi i / R):
 // with t_k = x_k + x_{R-k} and u_k = x_k - x_{R-k} (k = 1 .. H, H = (R-1)/2),
 // a_m = x_0 + sum_k cos(2 pi k m / R) t_k and b_m = sum_k sin(2 pi k m / R) u_k,
@@ -94,9 +82,9 @@ __device__ __forceinline__ void dft_odd(C *v)
         C a = x0, b = cmk<C>(0, 0);
 #pragma unroll
         for (int k = 1; k <= H; ++k) {
-            const int q = (k * m) % R;  // angle 2 pi q / R (q = 0 only for R = 9)
-            const T cq = (T)(q == 0 ? 1.0 : q <= H ? cos_tab<R>(q) : cos_tab<R>(R - q));
-            const T sq = (T)(q == 0 ? 0.0 : q <= H ? sin_tab<R>(q) : -sin_tab<R>(R - q));
+            const int q = (k * m) % R;  // angle 2 pi q / R, q != 0 for prime R
+            const T cq = (T)(q <= H ? cos_tab<R>(q) : cos_tab<R>(R - q));
+            const T sq = (T)(q <= H ? sin_tab<R>(q) : -sin_tab<R>(R - q));
             a = cmk<C>(a.x + cq * t[k - 1].x, a.y + cq * t[k - 1].y);
             b = cmk<C>(b.x + sq * u[k - 1].x, b.y + sq * u[k - 1].y);
         }
@@ -106,12 +94,121 @@ __device__ __forceinline__ void dft_odd(C *v)
     }
 }
 
-template <int R, bool INV, typename C>
-__device__ __forceinline__ void small_dft(C *v)
+// Compile-time cos and sin of 2 pi e / n (e, n integers, 0 <= e < n) in
+// double: reduction to [0, pi/4] by the symmetries of the circle, then the
+// Taylor series (12 terms: remainder below 1e-28 on that interval).
+__host__ __device__ constexpr double ct_sin_poly(double x)
 {
-    if constexpr (R % 2 == 1) dft_odd<R, INV, C>(v);
-    else RegDFT<R, INV, C>::run(v);
+    double term = x, sum = x;
+    for (int k = 1; k < 12; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
 }
+__host__ __device__ constexpr double ct_cos_poly(double x)
+{
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 12; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double kCtPi = 3.14159265358979323846264338327950288;
+__host__ __device__ constexpr double ct_cos2pi(int e, int n)
+{
+    if (2 * e > n) e = n - e;  // cos(2 pi - x) = cos x; angle now in [0, pi]
+    double x = 2.0 * kCtPi * e / n, sg = 1.0;
+    if (x > kCtPi / 2) {  // cos(pi - x) = -cos x
+        x = kCtPi - x;
+        sg = -1.0;
+    }
+    return sg * (x > kCtPi / 4 ? ct_sin_poly(kCtPi / 2 - x) : ct_cos_poly(x));
+}
+__host__ __device__ constexpr double ct_sin2pi(int e, int n)
+{
+    double sg = 1.0;
+    if (2 * e > n) {  // sin(2 pi - x) = -sin x
+        e = n - e;
+        sg = -1.0;
+    }
+    double x = 2.0 * kCtPi * e / n;
+    if (x > kCtPi / 2) x = kCtPi - x;  // sin(pi - x) = sin x
+    return sg * (x > kCtPi / 4 ? ct_cos_poly(kCtPi / 2 - x) : ct_sin_poly(x));
+}
+
+// x W_R^E (forward, W_R = exp(-2 pi i / R)) or x conj(W_R^E) (inverse), the
+// constants folded at compile time.
+template <int R, int E, bool INV, typename C>
+__device__ __forceinline__ C twmul(C x)
+{
+    using T = decltype(C::x);
+    constexpr int e = E % R;
+    if constexpr (e == 0) {
+        return x;
+    } else if constexpr (4 * e == R) {
+        return INV ? cmk<C>(-x.y, x.x) : cmk<C>(x.y, -x.x);
+    } else if constexpr (2 * e == R) {
+        return cmk<C>(-x.x, -x.y);
+    } else if constexpr (4 * e == 3 * R) {
+        return INV ? cmk<C>(x.y, -x.x) : cmk<C>(-x.y, x.x);
+    } else {
+        constexpr double c = ct_cos2pi(e, R), s = ct_sin2pi(e, R);
+        if (INV) return cmk<C>(x.x * (T)c - x.y * (T)s, x.x * (T)s + x.y * (T)c);
+        return cmk<C>(x.x * (T)c + x.y * (T)s, x.y * (T)c - x.x * (T)s);
+    }
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1.
+template <int B, int E> struct SFor {
+    template <typename F> __device__ __forceinline__ static void run(F &&f)
+    {
+        if constexpr (B < E) {
+            f(std::integral_constant<int, B>{});
+            SFor<B + 1, E>::run(f);
+        }
+    }
+};
+
+__host__ __device__ constexpr int small_prime_factor(int n) { return n % 2 == 0 ? 2 : n % 3 == 0 ? 3 : n % 5 == 0 ? 5 : n % 7 == 0 ? 7 : n; }
+__host__ __device__ constexpr bool pow2_const(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// In-register DFT of R points (R a product of 2, 3, 5, 7), natural order in
+// and out: powers of two by RegDFT, primes by the pair form, composites by
+// decimation in time R = P Q (P the smallest prime factor): Q-point DFTs of
+// the P subsequences x[m P + q], twiddles W_R^{q k}, P-point DFTs across q:
+// X[k + Q s] = sum_q W_P^{q s} W_R^{q k} Y_q[k].
+template <int R, bool INV, typename C> struct MixDFT {
+    static __device__ __forceinline__ void run(C *v)
+    {
+        if constexpr (pow2_const(R)) {
+            RegDFT<R, INV, C>::run(v);
+        } else if constexpr (small_prime_factor(R) == R) {
+            dft_odd<R, INV, C>(v);
+        } else {
+            constexpr int P = small_prime_factor(R), Q = R / P;
+            C sub[P][Q];
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int m = 0; m < Q; ++m) sub[q][m] = v[m * P + q];
+#pragma unroll
+            for (int q = 0; q < P; ++q) MixDFT<Q, INV, C>::run(sub[q]);
+            SFor<0, Q>::run([&](auto kk) {
+                constexpr int k = decltype(kk)::value;
+                C t[P];
+                SFor<0, P>::run([&](auto qq) {
+                    constexpr int q = decltype(qq)::value;
+                    t[q] = twmul<R, q * k, INV>(sub[q][k]);
+                });
+                MixDFT<P, INV, C>::run(t);
+#pragma unroll
+                for (int s2 = 0; s2 < P; ++s2) v[k + Q * s2] = t[s2];
+            });
+        }
+    }
+};
 
 // One Stockham stage s of radix R from src to dst, ncomp tiles of [L][TC]
 // (component stride cstride, swizzled as everywhere). Butterfly b of a
@@ -143,7 +240,7 @@ __device__ __forceinline__ void gen_stage(const C *src, C *dst, int ncomp, int c
                 v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
             }
         }
-        small_dft<R, INV, C>(v);
+        MixDFT<R, INV, C>::run(v);
         C *o = dst + comp * cstride;
         const int d = q * NS * R + k;
 #pragma unroll
@@ -152,8 +249,10 @@ __device__ __forceinline__ void gen_stage(const C *src, C *dst, int ncomp, int c
 }
 
 // Whole transform of the tiles in a (b is the second buffer); returns the
-// buffer that holds the result.
-template <typename C, bool INV>
+// buffer that holds the result. Stage radices up to MAXR are instantiated
+// (the plan never uses more): the row and column passes, memory bound, keep
+// MAXR = 16 and fewer registers; the fused z pass takes up to 32.
+template <typename C, bool INV, int MAXR>
 __device__ __forceinline__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const GenRadix &g, const C *__restrict__ tw,
                                       int twstride)
 {
@@ -164,10 +263,25 @@ __device__ __forceinline__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const 
         case 3: gen_stage<C, 3, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
         case 4: gen_stage<C, 4, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
         case 5: gen_stage<C, 5, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 6: gen_stage<C, 6, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
         case 7: gen_stage<C, 7, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
         case 8: gen_stage<C, 8, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
         case 9: gen_stage<C, 9, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        default: gen_stage<C, 16, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 10: gen_stage<C, 10, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 12: gen_stage<C, 12, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 14: gen_stage<C, 14, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 15: gen_stage<C, 15, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 16: gen_stage<C, 16, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 18: if constexpr (MAXR >= 18) gen_stage<C, 18, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 20: if constexpr (MAXR >= 20) gen_stage<C, 20, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 21: if constexpr (MAXR >= 21) gen_stage<C, 21, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 24: if constexpr (MAXR >= 24) gen_stage<C, 24, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 25: if constexpr (MAXR >= 25) gen_stage<C, 25, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 27: if constexpr (MAXR >= 27) gen_stage<C, 27, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 28: if constexpr (MAXR >= 28) gen_stage<C, 28, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 30: if constexpr (MAXR >= 30) gen_stage<C, 30, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        case 32: if constexpr (MAXR >= 32) gen_stage<C, 32, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
+        default: break;
         }
         __syncthreads();
         C *t = src;
@@ -177,11 +291,13 @@ __device__ __forceinline__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const 
     return src;
 }
 
+constexpr int kGenMaxRadixRows = 16, kGenMaxRadixZ = 32;
+
 // Column transforms (as k_col2): g.TC columns per CTA, rows < nin read,
 // rows < nout written; column f = slab * width + (f mod width), mw the
 // multiplier of width.
 template <typename T, bool INV>
-__global__ void __launch_bounds__(kGenThreads)
+__global__ void __launch_bounds__(kGenThreads, sizeof(T) == 4 ? 3 : 1)
 k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols, int width,
           unsigned mw, int64_t iss, int64_t irs, int nin, int64_t oss, int64_t ors, int nout,
           const typename Cplx<T>::type *__restrict__ tw, int twstride, const __grid_constant__ GenRadix g)
@@ -201,7 +317,7 @@ k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type 
         A[sw(e)] = v;
     }
     __syncthreads();
-    const C *res = gen_fft<C, INV>(A, B, 1, 0, g, tw, twstride);
+    const C *res = gen_fft<C, INV, kGenMaxRadixRows>(A, B, 1, 0, g, tw, twstride);
     for (int e = threadIdx.x; e < nout * TC; e += blockDim.x) {
         const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
         if (f < ncols) {
@@ -214,7 +330,7 @@ k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type 
 // Real-to-complex rows (as k_x_fwd): pack pairs of reals, transform of
 // L = Px/2 points, split into X[k], k = 0..L. g.TC rows per CTA.
 template <typename T>
-__global__ void __launch_bounds__(kGenThreads)
+__global__ void __launch_bounds__(kGenThreads, sizeof(T) == 4 ? 3 : 1)
 k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
             const typename Cplx<T>::type *__restrict__ twx, const __grid_constant__ GenRadix g)
 {
@@ -236,7 +352,7 @@ k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict_
         A[sw(n * TR + rr)] = z;
     }
     __syncthreads();
-    const C *Z = gen_fft<C, false>(A, B, 1, 0, g, twx, 2);
+    const C *Z = gen_fft<C, false, kGenMaxRadixRows>(A, B, 1, 0, g, twx, 2);
     const T h = (T)0.5;
     for (int e = threadIdx.x; e < (L + 1) * TR; e += blockDim.x) {
         const int rr = udiv(e, L + 1, g.mL1), k = e - rr * (L + 1), row = row0 + rr;
@@ -252,7 +368,7 @@ k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict_
 // Complex-to-real rows (as k_x_inv) with the XOut epilogue; energy partials
 // one per CTA.
 template <typename T>
-__global__ void __launch_bounds__(kGenThreads)
+__global__ void __launch_bounds__(kGenThreads, sizeof(T) == 4 ? 3 : 1)
 k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
             const typename Cplx<T>::type *__restrict__ twx, const __grid_constant__ GenRadix g)
 {
@@ -275,7 +391,7 @@ k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nr
         A[sw(k * TR + rr)] = z;
     }
     __syncthreads();
-    const C *Z = gen_fft<C, true>(A, B, 1, 0, g, twx, 2);
+    const C *Z = gen_fft<C, true, kGenMaxRadixRows>(A, B, 1, 0, g, twx, 2);
     const T gsc = o.gdev ? (T)(*o.gdev) : (T)1;
     const T oscale = o.oscale * gsc;
     T acc = 0;
@@ -324,7 +440,7 @@ k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsign
         A[sw(e)] = v0; A[TS + sw(e)] = v1; A[2 * TS + sw(e)] = v2;
     }
     __syncthreads();
-    C *F = gen_fft<C, false>(A, B, 3, TS, g, tw, twstride);
+    C *F = gen_fft<C, false, kGenMaxRadixZ>(A, B, 3, TS, g, tw, twstride);
     C *G = F == A ? B : A;
     const int hy = Py / 2 + 1, hz = L / 2 + 1;
     const int64_t plane = (int64_t)hz * hy * Kx;
@@ -346,7 +462,7 @@ k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsign
         F[2 * TS + sw(e)] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
     }
     __syncthreads();
-    const C *res = gen_fft<C, true>(F, G, 3, TS, g, tw, twstride);
+    const C *res = gen_fft<C, true, kGenMaxRadixZ>(F, G, 3, TS, g, tw, twstride);
     for (int e = threadIdx.x; e < nrows * TC; e += blockDim.x) {
         const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
         if (f < ncols) {

@@ -68,29 +68,50 @@ template <typename T> constexpr int gen_tile_elems(bool zpass)
     return sizeof(T) == 4 ? (zpass ? 2048 : 4096) : (zpass ? 1024 : 2048);
 }
 
+// Stage radices of the mixed-radix passes: every length <= 32 with prime
+// factors 2, 3, 5, 7 (the in-register DFTs that mixed.cuh instantiates).
+bool gen_stage_radix(int r)
+{
+    if (r < 2 || r > 32) return false;
+    for (int f : {2, 3, 5, 7})
+        while (r % f == 0) r /= f;
+    return r == 1;
+}
+
+// Fewest stages (at most `depth`), then the smallest largest radix, radices
+// in non-increasing order; false if L has no such split.
+bool gen_split(int m, int maxr, int depth, int *cur, int n, int *best, int &bn, int &bmax)
+{
+    if (m == 1) {
+        int mx = 0;
+        for (int i = 0; i < n; ++i) mx = cur[i] > mx ? cur[i] : mx;
+        if (bn == 0 || n < bn || (n == bn && mx < bmax)) {
+            for (int i = 0; i < n; ++i) best[i] = cur[i];
+            bn = n;
+            bmax = mx;
+        }
+        return true;
+    }
+    if (depth == 0) return false;
+    bool any = false;
+    for (int r = maxr; r >= 2; --r)
+        if (m % r == 0 && gen_stage_radix(r)) {
+            cur[n] = r;
+            any |= gen_split(m / r, r, depth - 1, cur, n + 1, best, bn, bmax);
+        }
+    return any;
+}
+
 // Stage plan of a mixed-radix transform of length L (a product of 2, 3, 5
-// and 7, L < 2048) over tiles of about `tile` elements: the power of two in
-// L as even stages of radix <= 16, then radix 9 for pairs of threes, 3, 5, 7.
-bool gen_plan(int L, int tile, GenRadix &g)
+// and 7, L < 2048) over tiles of about `tile` elements, radices <= maxr.
+bool gen_plan(int L, int tile, GenRadix &g, int maxr)
 {
     memset(&g, 0, sizeof g);
     if (L < 2 || L >= 2048) return false;
     g.L = L;
     g.TC = tile / L > 1 ? tile / L : 1;
-    int m = L, a = 0, f3 = 0, f5 = 0, f7 = 0;
-    while (m % 2 == 0) { m /= 2; ++a; }
-    while (m % 3 == 0) { m /= 3; ++f3; }
-    while (m % 5 == 0) { m /= 5; ++f5; }
-    while (m % 7 == 0) { m /= 7; ++f7; }
-    if (m != 1) return false;
-    int r[32], n = 0;
-    const int n2 = (a + 3) / 4;
-    for (int s = 0; s < n2; ++s) r[n++] = 1 << (a / n2 + (s < a % n2 ? 1 : 0));
-    for (int i = 0; i < f3 / 2; ++i) r[n++] = 9;
-    if (f3 % 2) r[n++] = 3;
-    for (int i = 0; i < f5; ++i) r[n++] = 5;
-    for (int i = 0; i < f7; ++i) r[n++] = 7;
-    if (n > kGenMaxStages) return false;
+    int cur[4], r[4], n = 0, mx = 0;
+    if (!gen_split(L, maxr, 4, cur, 0, r, n, mx) || n == 0) return false;
     int NS = 1;
     for (int s = 0; s < n; ++s) {
         g.r[s] = r[s];
@@ -382,7 +403,7 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
     if (nrows <= 0) return cudaSuccess;
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return cudaErrorInvalidValue;
+        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
         const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
         cudaError_t e = allow_smem<k_gen_x_fwd<T>>(sm);
         if (e != cudaSuccess) return e;
@@ -439,7 +460,7 @@ int Passes<T>::x_blocks(int L, int nrows)
 {
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return 1;
+        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return 1;
         return (nrows + g.TC - 1) / g.TC;
     }
     int rows_per_cta;
@@ -460,7 +481,7 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
     if (nrows <= 0) return cudaSuccess;
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return cudaErrorInvalidValue;
+        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
         const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
         cudaError_t e = allow_smem<k_gen_x_inv<T>>(sm);
         if (e != cudaSuccess) return e;
@@ -534,7 +555,7 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
     if (ncols <= 0) return cudaSuccess;
     if (!pow2_len(L)) {
         GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g)) return cudaErrorInvalidValue;
+        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
         const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
         const unsigned mw = magic_of(width);
         const int grid = (ncols + g.TC - 1) / g.TC;
@@ -647,7 +668,7 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
     if (ncols > 0 && !pow2_len(L)) {
         if (nrows > L) return cudaErrorInvalidValue;
         GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(true), g)) return cudaErrorInvalidValue;
+        if (!gen_plan(L, gen_tile_elems<T>(true), g, kGenMaxRadixZ)) return cudaErrorInvalidValue;
         const size_t sm = 6 * swsize(L * g.TC) * sizeof(C);
         cudaError_t e = allow_smem<k_gen_zconv<T>>(sm);
         if (e != cudaSuccess) return e;
