@@ -339,8 +339,9 @@ demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, v
  * padded to the smallest power of two >= 2n - 1 or to the smallest even
  * length >= 2n - 1 with prime factors 2, 3, 5, 7 (mixed-radix passes); the
  * field is the same up to rounding. Each distinct combination (at most 8)
- * is created, set up, autotuned (demag_autotune) and timed on the current
- * device; the fastest lengths are written to best->px, py, pz (pad_mode 0).
+ * is created, autotuned (demag_autotune) and timed on the current device
+ * (with a zero tensor spectrum: the passes do the same work whatever it
+ * holds, and no FP64 tensor setup is spent on plans that are only timed); the fastest lengths are written to best->px, py, pz (pad_mode 0).
  * ms_best / ms_pow2 (may be NULL) receive the time per field call of the
  * chosen and of the all-power-of-two lengths. use_cache != 0 reuses and
  * appends results in the autotuner's cache file, keyed by GPU, precision and
