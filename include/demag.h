@@ -109,6 +109,12 @@ typedef struct {
 demag_status demag_plan_create(int nx, int ny, int nz, double dx, double dy, double dz,
                                demag_prec prec, demag_plan_t *out);
 
+/* Padded lengths a DM plan of an nx x ny x nz grid takes with these options
+ * (NULL: powers of two), written to P[0..2]; no device is touched. The same
+ * argument checks as demag_plan_create_ex; DEMAG_PAD_TUNED returns
+ * DEMAG_ERR_UNSUPPORTED (its lengths come from timing: demag_tune_padding). */
+demag_status demag_padded_lengths(int nx, int ny, int nz, const demag_options *opt, int *P);
+
 /* Same, with options (may be NULL). */
 demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, double dz,
                                   demag_prec prec, const demag_options *opt,

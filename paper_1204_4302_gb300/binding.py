@@ -39,7 +39,7 @@ EXPORTS = [
     "demag_field_host", "demag_plan_info", "demag_set_timing", "demag_get_timing",
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
     "demag_energy_noalloc",
-    "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding",
+    "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding", "demag_padded_lengths",
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
@@ -112,6 +112,7 @@ def load(path: str | Path | None = None):
         "demag_energy_noalloc": (S, [I, I, I, D, D, D, I, P, P, P, P]),
         "demag_batch_create": (S, [I, P, P, I, POINTER(c_void_p)]),
         "demag_batch_create_ex": (S, [I, P, P, I, POINTER(demag_options), POINTER(c_void_p)]),
+        "demag_padded_lengths": (S, [I, I, I, POINTER(demag_options), POINTER(c_int)]),
         "demag_tune_padding": (S, [I, I, I, D, D, D, I, I, POINTER(demag_options), POINTER(c_double),
                                    POINTER(c_double), P]),
         "demag_batch_field": (S, [P, P, P, P, P]),
@@ -325,6 +326,14 @@ def demag_batch_create(dims, cells, prec=DEMAG_F32, pad_mode=None):
         _check(load().demag_batch_create_ex(n, d, c, int(prec), ctypes.byref(opt), ctypes.byref(h)),
                "demag_batch_create_ex")
     return h.value
+
+
+def demag_padded_lengths(nx, ny, nz, px=0, py=0, pz=0, pad_mode=0):
+    """Padded lengths (px, py, pz) a DM plan takes with these options (no device)."""
+    opt = demag_options(int(px), int(py), int(pz), int(pad_mode))
+    P = (c_int * 3)()
+    _check(load().demag_padded_lengths(int(nx), int(ny), int(nz), ctypes.byref(opt), P), "demag_padded_lengths")
+    return tuple(P)
 
 
 def demag_tune_padding(nx, ny, nz, dx, dy, dz, prec=DEMAG_F32, use_cache=True, stream=0):

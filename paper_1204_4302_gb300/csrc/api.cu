@@ -71,6 +71,32 @@ int smooth_pad(int n)
     return p;
 }
 
+// Padded lengths of a DM plan from its options (pad_mode powers of two or
+// smooth, explicit lengths checked); DEMAG_PAD_TUNED is resolved by timing
+// elsewhere and is UNSUPPORTED here.
+demag_status pad_lengths(const int n[3], const demag_options *opt, int P[3])
+{
+    if (opt && opt->pad_mode != DEMAG_PAD_POW2 && opt->pad_mode != DEMAG_PAD_SMOOTH &&
+        opt->pad_mode != DEMAG_PAD_TUNED)
+        return fail(DEMAG_ERR_INVALID_ARG, "unknown pad_mode");
+    if (opt && opt->pad_mode == DEMAG_PAD_TUNED)
+        return fail(DEMAG_ERR_UNSUPPORTED, "tuned padded lengths come from demag_tune_padding");
+    const bool smooth = opt && opt->pad_mode == DEMAG_PAD_SMOOTH;
+    for (int a = 0; a < 3; ++a) P[a] = smooth ? smooth_pad(n[a]) : default_pad(n[a]);
+    if (opt) {
+        const int req[3] = {opt->px, opt->py, opt->pz};
+        for (int a = 0; a < 3; ++a) {
+            if (req[a] == 0) continue;
+            if (!(is_pow2(req[a]) || is_smooth_even(req[a])) || req[a] < 2 * n[a] - 1)
+                return fail(DEMAG_ERR_INVALID_ARG,
+                            "padded lengths must be >= 2n - 1 and powers of two or even products of 2, 3, 5, 7");
+            if (req[a] > kMaxP) return fail(DEMAG_ERR_UNSUPPORTED, "padded lengths above 1024 are not built");
+            P[a] = req[a];
+        }
+    }
+    return DEMAG_OK;
+}
+
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
     int prev = -1;
@@ -638,6 +664,20 @@ void demag_plan_destroy(demag_plan_t p)
     delete p;
 }
 
+demag_status demag_padded_lengths(int nx, int ny, int nz, const demag_options *opt, int *P)
+{
+    if (!P) return fail(DEMAG_ERR_INVALID_ARG, "P is NULL");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DEMAG_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (nx > kMaxN || ny > kMaxN || nz > kMaxN)
+        return fail(DEMAG_ERR_UNSUPPORTED, "grid sizes above 512 per axis are not built");
+    const int n[3] = {nx, ny, nz};
+    int Q[3];
+    demag_status s = pad_lengths(n, opt, Q);
+    if (s != DEMAG_OK) return s;
+    for (int a = 0; a < 3; ++a) P[a] = Q[a];
+    return DEMAG_OK;
+}
+
 demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec,
                                   const demag_options *opt, demag_plan_t *out)
 {
@@ -650,12 +690,7 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
     if (nx > kMaxN || ny > kMaxN || nz > kMaxN)
         return fail(DEMAG_ERR_UNSUPPORTED, "grid sizes above 512 per axis are not built");
     const int n[3] = {nx, ny, nz};
-    if (opt && opt->pad_mode != DEMAG_PAD_POW2 && opt->pad_mode != DEMAG_PAD_SMOOTH &&
-        opt->pad_mode != DEMAG_PAD_TUNED)
-        return fail(DEMAG_ERR_INVALID_ARG, "unknown pad_mode");
-    const bool smooth = opt && opt->pad_mode == DEMAG_PAD_SMOOTH;
     int P[3];
-    for (int a = 0; a < 3; ++a) P[a] = smooth ? smooth_pad(n[a]) : default_pad(n[a]);
     if (opt && opt->pad_mode == DEMAG_PAD_TUNED) {
         if (opt->px || opt->py || opt->pz)
             return fail(DEMAG_ERR_INVALID_ARG, "DEMAG_PAD_TUNED takes no explicit padded lengths");
@@ -666,17 +701,8 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
         P[0] = t.px; P[1] = t.py; P[2] = t.pz;
         return create_plan(nx, ny, nz, dx, dy, dz, prec, P, DEMAG_METHOD_DM, out);
     }
-    if (opt) {
-        const int req[3] = {opt->px, opt->py, opt->pz};
-        for (int a = 0; a < 3; ++a) {
-            if (req[a] == 0) continue;
-            if (!(is_pow2(req[a]) || is_smooth_even(req[a])) || req[a] < 2 * n[a] - 1)
-                return fail(DEMAG_ERR_INVALID_ARG,
-                            "padded lengths must be >= 2n - 1 and powers of two or even products of 2, 3, 5, 7");
-            if (req[a] > kMaxP) return fail(DEMAG_ERR_UNSUPPORTED, "padded lengths above 1024 are not built");
-            P[a] = req[a];
-        }
-    }
+    demag_status s = pad_lengths(n, opt, P);
+    if (s != DEMAG_OK) return s;
     return create_plan(nx, ny, nz, dx, dy, dz, prec, P, DEMAG_METHOD_DM, out);
 }
 

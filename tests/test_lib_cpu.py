@@ -104,6 +104,36 @@ def test_padding_options_are_checked_before_any_device_call(lib):
         1  # DEMAG_ERR_INVALID_ARG
 
 
+def _smooth_even(p):
+    if p % 2:
+        return False
+    for f in (2, 3, 5, 7):
+        while p % f == 0:
+            p //= f
+    return p == 1
+
+
+def test_padded_lengths_rules(lib):
+    """Default padding: the smallest power of two >= 2n - 1; smooth: the
+    smallest even length >= 2n - 1 with prime factors 2, 3, 5, 7 (brute force
+    here); 1 for a single cell; explicit lengths kept."""
+    from paper_1204_4302_gb300 import binding
+    for n in list(range(1, 70)) + [100, 130, 200, 255, 257, 300, 333, 400, 511, 512]:
+        pw = 1 if n == 1 else 1 << (2 * n - 2).bit_length()
+        sm = 1 if n == 1 else next(p for p in range(2 * n - 1, 4 * n) if _smooth_even(p))
+        assert binding.demag_padded_lengths(n, 1, 1) == (pw, 1, 1), n
+        assert binding.demag_padded_lengths(1, n, 1, pad_mode=1) == (1, sm, 1), n
+        assert sm <= pw and sm >= 2 * n - 1
+    assert binding.demag_padded_lengths(8, 8, 8, px=18, pz=30) == (18, 16, 30)
+    assert binding.demag_padded_lengths(130, 130, 130, pad_mode=1) == (270, 270, 270)
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_padded_lengths(8, 8, 8, pad_mode=2)
+    assert e.value.name == "DEMAG_ERR_UNSUPPORTED"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_padded_lengths(8, 8, 8, px=22)
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+
+
 def test_sp_plan_arguments_are_checked_before_any_device_call(lib):
     """Scalar-potential plans: padding must be a power of two >= 2n (not 2n - 1),
     z is built up to 256 cells, and the usual size and edge checks apply."""
