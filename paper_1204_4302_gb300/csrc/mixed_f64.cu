@@ -1,0 +1,3 @@
+// FP64 instantiation of the mixed-radix passes.
+#include "mixed_impl.cuh"
+template struct demag::MixedPasses<double>;

@@ -6,7 +6,7 @@
 #include "fft_engine.cuh"
 #include <string.h>
 
-#include "mixed.cuh"
+#include "launch_util.cuh"
 #include "plan.h"
 #include "sp.cuh"
 #include "xpipe.cuh"
@@ -15,117 +15,7 @@ namespace demag {
 
 namespace {
 
-// Opt in to more than 48 KB of dynamic shared memory, once per kernel and
-// device (the cache is per template argument, i.e. per kernel).
-int sm_count()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
-    return sms;
-}
-
-template <auto Kern>
-cudaError_t allow_smem(size_t bytes)
-{
-    // Opt the kernel in to the device's whole per-block shared memory once per
-    // device (launch sizes can differ from call to call); the occupancy still
-    // follows the size each launch asks for.
-    const auto kern = Kern;
-    static int done_for = -1;
-    static size_t limit = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (done_for != dev) {
-        int optin = 0;
-        cudaFuncAttributes fa;
-        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
-        const size_t dyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-        if (dyn > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
-            return e;
-        limit = dyn > 48 * 1024 ? dyn : 48 * 1024;
-        done_for = dev;
-    }
-    return bytes <= limit ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 bool pow2_len(int L) { return L > 0 && (L & (L - 1)) == 0; }
-
-// ceil(2^32 / d): n / d == umulhi(n, magic) for n d < 2^32 (d == 1 apart)
-unsigned magic_of(int d) { return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d); }
-
-// Elements per tile of the mixed-radix kernels: the column and row passes
-// hold two buffers, the z pass six (three components, ping-pong).
-template <typename T> constexpr int gen_tile_elems(bool zpass)
-{
-    return sizeof(T) == 4 ? (zpass ? 2048 : 4096) : (zpass ? 1024 : 2048);
-}
-
-// Stage radices of the mixed-radix passes: every length <= 32 with prime
-// factors 2, 3, 5, 7 (the in-register DFTs that mixed.cuh instantiates).
-bool gen_stage_radix(int r)
-{
-    if (r < 2 || r > 32) return false;
-    for (int f : {2, 3, 5, 7})
-        while (r % f == 0) r /= f;
-    return r == 1;
-}
-
-// Fewest stages (at most `depth`), then the smallest largest radix, radices
-// in non-increasing order; false if L has no such split.
-bool gen_split(int m, int maxr, int depth, int *cur, int n, int *best, int &bn, int &bmax)
-{
-    if (m == 1) {
-        int mx = 0;
-        for (int i = 0; i < n; ++i) mx = cur[i] > mx ? cur[i] : mx;
-        if (bn == 0 || n < bn || (n == bn && mx < bmax)) {
-            for (int i = 0; i < n; ++i) best[i] = cur[i];
-            bn = n;
-            bmax = mx;
-        }
-        return true;
-    }
-    if (depth == 0) return false;
-    bool any = false;
-    for (int r = maxr; r >= 2; --r)
-        if (m % r == 0 && gen_stage_radix(r)) {
-            cur[n] = r;
-            any |= gen_split(m / r, r, depth - 1, cur, n + 1, best, bn, bmax);
-        }
-    return any;
-}
-
-// Stage plan of a mixed-radix transform of length L (a product of 2, 3, 5
-// and 7, L < 2048) over tiles of about `tile` elements, radices <= maxr.
-bool gen_plan(int L, int tile, GenRadix &g, int maxr)
-{
-    memset(&g, 0, sizeof g);
-    if (L < 2 || L >= 2048) return false;
-    g.L = L;
-    g.TC = tile / L > 1 ? tile / L : 1;
-    int cur[4], r[4], n = 0, mx = 0;
-    if (!gen_split(L, maxr, 4, cur, 0, r, n, mx) || n == 0) return false;
-    int NS = 1;
-    for (int s = 0; s < n; ++s) {
-        g.r[s] = r[s];
-        g.NS[s] = NS;
-        g.mNS[s] = magic_of(NS);
-        g.mPer[s] = magic_of(L / r[s] * g.TC);
-        NS *= r[s];
-    }
-    g.n = n;
-    g.mTC = magic_of(g.TC);
-    g.mL = magic_of(L);
-    g.mL1 = magic_of(L + 1);
-    return true;
-}
 
 template <typename T>
 __global__ void k_x1_fwd(XIn<T> a, int64_t n, typename Cplx<T>::type *__restrict__ out)
@@ -401,15 +291,7 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
                              const C *twx, cudaStream_t st, int variant)
 {
     if (nrows <= 0) return cudaSuccess;
-    if (!pow2_len(L)) {
-        GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
-        const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
-        cudaError_t e = allow_smem<k_gen_x_fwd<T>>(sm);
-        if (e != cudaSuccess) return e;
-        k_gen_x_fwd<T><<<(nrows + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(a, nrows, nvalid, out, out_rs, twx, g);
-        return cudaGetLastError();
-    }
+    if (!pow2_len(L)) return MixedPasses<T>::x_fwd(L, a, nrows, nvalid, out, out_rs, twx, st);
     // pipelined form: rows of the plain field (no per-cell weight) stored back
     // to back, 16-byte multiples, zero-padded half
     if (variant >= 1 && L >= 64 && nvalid <= L && !a.wcell && a.in_rs == nvalid && nvalid % 4 == 0 &&
@@ -458,11 +340,7 @@ cudaError_t Passes<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *o
 template <typename T>
 int Passes<T>::x_blocks(int L, int nrows)
 {
-    if (!pow2_len(L)) {
-        GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return 1;
-        return (nrows + g.TC - 1) / g.TC;
-    }
+    if (!pow2_len(L)) return MixedPasses<T>::x_blocks(L, nrows);
     int rows_per_cta;
     switch (L) {
     case 64: rows_per_cta = XShape<T, 64>::TR; break;
@@ -479,15 +357,7 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
                              const C *twx, cudaStream_t st, int variant)
 {
     if (nrows <= 0) return cudaSuccess;
-    if (!pow2_len(L)) {
-        GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
-        const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
-        cudaError_t e = allow_smem<k_gen_x_inv<T>>(sm);
-        if (e != cudaSuccess) return e;
-        k_gen_x_inv<T><<<(nrows + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, g);
-        return cudaGetLastError();
-    }
+    if (!pow2_len(L)) return MixedPasses<T>::x_inv(L, in, in_rs, nrows, nvalid, o, twx, st);
     if (variant == 2 && L >= 64 && in_rs % 2 == 0 && in_rs <= 2 * L && nvalid <= L + 1 && ((uintptr_t)in & 15) == 0) {
         const bool p1 = nvalid > L;
 #define DEMAG_PIPE(LL)                                                                         \
@@ -553,24 +423,8 @@ cudaError_t Passes<T>::col(int L, bool inv, const C *in, C *out, int ncols, int 
                            int twstride, cudaStream_t st, int variant)
 {
     if (ncols <= 0) return cudaSuccess;
-    if (!pow2_len(L)) {
-        GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
-        const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
-        const unsigned mw = magic_of(width);
-        const int grid = (ncols + g.TC - 1) / g.TC;
-        cudaError_t e;
-        if (inv) {
-            if ((e = allow_smem<k_gen_col<T, true>>(sm)) != cudaSuccess) return e;
-            k_gen_col<T, true><<<grid, kGenThreads, sm, st>>>(in, out, ncols, width, mw, iss, irs, nin, oss, ors, nout,
-                                                              tw, twstride, g);
-        } else {
-            if ((e = allow_smem<k_gen_col<T, false>>(sm)) != cudaSuccess) return e;
-            k_gen_col<T, false><<<grid, kGenThreads, sm, st>>>(in, out, ncols, width, mw, iss, irs, nin, oss, ors,
-                                                               nout, tw, twstride, g);
-        }
-        return cudaGetLastError();
-    }
+    if (!pow2_len(L))
+        return MixedPasses<T>::col(L, inv, in, out, ncols, width, iss, irs, nin, oss, ors, nout, tw, twstride, st);
     if (L <= 16) {
         // one thread per column
         const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
@@ -665,17 +519,8 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant)
 {
-    if (ncols > 0 && !pow2_len(L)) {
-        if (nrows > L) return cudaErrorInvalidValue;
-        GenRadix g;
-        if (!gen_plan(L, gen_tile_elems<T>(true), g, kGenMaxRadixZ)) return cudaErrorInvalidValue;
-        const size_t sm = 6 * swsize(L * g.TC) * sizeof(C);
-        cudaError_t e = allow_smem<k_gen_zconv<T>>(sm);
-        if (e != cudaSuccess) return e;
-        k_gen_zconv<T><<<(ncols + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(S, ncols, width, magic_of(width), ss, rs, cs,
-                                                                           nrows, nhat, Py, Kx, tw, twstride, g);
-        return cudaGetLastError();
-    }
+    if (ncols > 0 && !pow2_len(L))
+        return MixedPasses<T>::zconv(L, S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
     if (variant == 5 && ncols > 0 && 2 * nrows <= L) {
         cudaError_t e = cudaErrorNotSupported;
         switch (L) {

@@ -41,6 +41,22 @@ template <typename T> struct XOut {
     int rows_per_comp;
 };
 
+// Launchers of the mixed-radix passes (transform lengths with prime factors
+// 2, 3, 5, 7 that are not powers of two; mixed_f32.cu / mixed_f64.cu). Same
+// arguments and results as the Passes members of the same names.
+template <typename T> struct MixedPasses {
+    using C = typename CplxOf<T>::type;
+    static cudaError_t x_fwd(int L, const XIn<T> &a, int nrows, int nvalid, C *out, int64_t out_rs, const C *twx,
+                             cudaStream_t st);
+    static cudaError_t x_inv(int L, const C *in, int64_t in_rs, int nrows, int nvalid, const XOut<T> &o,
+                             const C *twx, cudaStream_t st);
+    static int x_blocks(int L, int nrows);
+    static cudaError_t col(int L, bool inv, const C *in, C *out, int ncols, int width, int64_t iss, int64_t irs,
+                           int nin, int64_t oss, int64_t ors, int nout, const C *tw, int twstride, cudaStream_t st);
+    static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                             const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st);
+};
+
 // Launchers of the field passes for element type T (defined in
 // passes_f32.cu / passes_f64.cu). L is the transform length of the pass.
 template <typename T> struct Passes {
