@@ -26,6 +26,7 @@ struct GenRadix {
     int NS[kGenMaxStages];         // product of the earlier radices
     unsigned mNS[kGenMaxStages];   // division by NS
     unsigned mPer[kGenMaxStages];  // division by (L / r) TC
+    unsigned mNB[kGenMaxStages];   // division by L / r
     unsigned mTC, mL, mL1;         // division by TC, L, L + 1
 };
 
@@ -293,9 +294,143 @@ __device__ __forceinline__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const 
 
 constexpr int kGenMaxRadixRows = 16, kGenMaxRadixZ = 32;
 
+// Stages with caller-supplied ends: the first stage reads its inputs through
+// ld(row, col) (global memory, with the pass's prologue) and the last stage
+// writes through st(row, col, value) (global memory with the epilogue, or
+// shared memory), so a plan of n stages makes n - 1 shared-memory exchanges.
+// Tiles in shared memory: XROW = false: [row][col] (columns of the y pass,
+// consecutive columns contiguous in global memory); XROW = true: [col][row]
+// (rows of the x passes, contiguous along row), and consecutive threads then
+// take consecutive butterflies of one transform.
+template <typename C, bool XROW> struct GenSmemLd {
+    const C *p;
+    int TC, L;
+    __device__ __forceinline__ C operator()(int row, int col) const
+    {
+        return p[sw(XROW ? col * L + row : row * TC + col)];
+    }
+};
+template <typename C, bool XROW> struct GenSmemSt {
+    C *p;
+    int TC, L;
+    __device__ __forceinline__ void operator()(int row, int col, C v) const
+    {
+        p[sw(XROW ? col * L + row : row * TC + col)] = v;
+    }
+};
+
+template <typename C, int R, bool INV, bool XROW, typename LD, typename ST>
+__device__ __forceinline__ void gen_stage_io(const GenRadix &g, int s, const C *__restrict__ tw, int twstride,
+                                             const LD &ld, const ST &st)
+{
+    const int L = g.L, TC = g.TC, NS = g.NS[s];
+    const int NB = L / R, total = NB * TC;
+    const int tws = (L / (NS * R)) * twstride;
+    const unsigned mNS = g.mNS[s];
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        int j, col;
+        if constexpr (XROW) {
+            col = udiv(b, NB, g.mNB[s]);
+            j = b - col * NB;
+        } else {
+            j = udiv(b, TC, g.mTC);
+            col = b - j * TC;
+        }
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld(j + r * NB, col);
+        const int q = udiv(j, NS, mNS), k = j - q * NS;
+        if (k > 0) {
+            const int kt = k * tws;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C w = __ldg(&tw[r * kt]);
+                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            }
+        }
+        MixDFT<R, INV, C>::run(v);
+        const int d = q * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) st(d + r * NS, col, v[r]);
+    }
+}
+
+template <typename C, bool INV, bool XROW, typename LD, typename ST>
+__device__ __forceinline__ void gen_stage_any(const GenRadix &g, int s, const C *__restrict__ tw, int twstride,
+                                              const LD &ld, const ST &st)
+{
+    switch (g.r[s]) {
+    case 2: gen_stage_io<C, 2, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 3: gen_stage_io<C, 3, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 4: gen_stage_io<C, 4, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 5: gen_stage_io<C, 5, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 6: gen_stage_io<C, 6, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 7: gen_stage_io<C, 7, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 8: gen_stage_io<C, 8, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 9: gen_stage_io<C, 9, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 10: gen_stage_io<C, 10, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 12: gen_stage_io<C, 12, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 14: gen_stage_io<C, 14, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 15: gen_stage_io<C, 15, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    default: gen_stage_io<C, 16, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    }
+}
+
+// Whole transform (radices <= 16) from ld to st (LASTG) or to a shared
+// buffer that is returned (A, or B when the stages end there). Shared
+// buffers used: A for the first stage's output, B from the third stage on
+// (LASTG) or from the second (otherwise). Every input is read, and a barrier
+// passed, before the first output is written (in-place calls are safe).
+template <typename C, bool INV, bool XROW, bool LASTG, typename LD, typename ST>
+__device__ __forceinline__ C *gen_fft_io(C *A, C *B, const GenRadix &g, const C *__restrict__ tw, int twstride,
+                                         const LD &ld0, const ST &stN)
+{
+    const int n = g.n;
+    if constexpr (LASTG) {
+        if (n == 1) {
+            // one stage: through shared memory, so that an in-place call (the
+            // same global buffer read and written) reads every input first
+            gen_stage_any<C, INV, XROW>(g, 0, tw, twstride, ld0, GenSmemSt<C, XROW>{A, g.TC, g.L});
+            __syncthreads();
+            for (int e = threadIdx.x; e < g.L * g.TC; e += blockDim.x) {
+                int row, col;
+                if constexpr (XROW) {
+                    col = udiv(e, g.L, g.mL);
+                    row = e - col * g.L;
+                } else {
+                    row = udiv(e, g.TC, g.mTC);
+                    col = e - row * g.TC;
+                }
+                stN(row, col, GenSmemLd<C, XROW>{A, g.TC, g.L}(row, col));
+            }
+            return nullptr;
+        }
+    }
+    gen_stage_any<C, INV, XROW>(g, 0, tw, twstride, ld0, GenSmemSt<C, XROW>{A, g.TC, g.L});
+    __syncthreads();
+    C *src = A, *dst = B;
+    for (int s = 1; s < (LASTG ? n - 1 : n); ++s) {
+        gen_stage_any<C, INV, XROW>(g, s, tw, twstride, GenSmemLd<C, XROW>{src, g.TC, g.L},
+                                    GenSmemSt<C, XROW>{dst, g.TC, g.L});
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+    }
+    if constexpr (LASTG) {
+        gen_stage_any<C, INV, XROW>(g, n - 1, tw, twstride, GenSmemLd<C, XROW>{src, g.TC, g.L}, stN);
+        return nullptr;
+    } else {
+        return src;
+    }
+}
+
+// Shared buffers a kernel of the I/O form needs for a plan of n stages.
+inline int gen_io_buffers(int n, bool last_global) { return last_global ? (n >= 3 ? 2 : 1) : (n >= 2 ? 2 : 1); }
+
 // Column transforms (as k_col2): g.TC columns per CTA, rows < nin read,
 // rows < nout written; column f = slab * width + (f mod width), mw the
-// multiplier of width.
+// multiplier of width. The first stage reads global memory, the last writes it.
 template <typename T, bool INV>
 __global__ void __launch_bounds__(kGenThreads, sizeof(T) == 4 ? 3 : 1)
 k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type *__restrict__ out, int ncols, int width,
@@ -304,31 +439,31 @@ k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type 
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int L = g.L, TC = g.TC, TS = swsize(L * TC);
+    const int TS = swsize(g.L * g.TC);
     C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
-    const int f0 = blockIdx.x * TC;
-    for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
+    const int f0 = blockIdx.x * g.TC;
+    auto ld = [&](int row, int col) {
+        const int f = f0 + col;
         C v = cmk<C>(0, 0);
-        if (f < ncols && r < nin) {
+        if (f < ncols && row < nin) {
             const int slab = udiv(f, width, mw);
-            v = in[(int64_t)slab * iss + (int64_t)r * irs + (f - slab * width)];
+            v = in[(int64_t)slab * iss + (int64_t)row * irs + (f - slab * width)];
         }
-        A[sw(e)] = v;
-    }
-    __syncthreads();
-    const C *res = gen_fft<C, INV, kGenMaxRadixRows>(A, B, 1, 0, g, tw, twstride);
-    for (int e = threadIdx.x; e < nout * TC; e += blockDim.x) {
-        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
-        if (f < ncols) {
+        return v;
+    };
+    auto st = [&](int row, int col, C v) {
+        const int f = f0 + col;
+        if (f < ncols && row < nout) {
             const int slab = udiv(f, width, mw);
-            out[(int64_t)slab * oss + (int64_t)r * ors + (f - slab * width)] = res[sw(e)];
+            out[(int64_t)slab * oss + (int64_t)row * ors + (f - slab * width)] = v;
         }
-    }
+    };
+    gen_fft_io<C, INV, false, true>(A, B, g, tw, twstride, ld, st);
 }
 
 // Real-to-complex rows (as k_x_fwd): pack pairs of reals, transform of
-// L = Px/2 points, split into X[k], k = 0..L. g.TC rows per CTA.
+// L = Px/2 points (first stage from global memory), split into X[k],
+// k = 0..L. g.TC rows per CTA.
 template <typename T>
 __global__ void __launch_bounds__(kGenThreads, sizeof(T) == 4 ? 3 : 1)
 k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ out, int64_t out_rs,
@@ -339,34 +474,40 @@ k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict_
     const int L = g.L, TR = g.TC, TS = swsize(L * TR);
     C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
     const int row0 = blockIdx.x * TR;
-    for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
-        const int rr = udiv(e, L, g.mL), n = e - rr * L, row = row0 + rr;
+    const bool pairs = (a.in_rs & 1) == 0;  // rows start on a pair boundary: one vector load per pair
+    auto ld = [&](int n, int rr) {
+        const int row = row0 + rr, x0 = 2 * n;
         C z = cmk<C>(0, 0);
-        const int x0 = 2 * n;
         if (row < nrows && x0 < nvalid) {
             const T *p = a.in + (int64_t)row * a.in_rs;
-            z.x = p[x0] * a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
-            if (x0 + 1 < nvalid)
-                z.y = p[x0 + 1] * a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0 + 1);
+            if (pairs && x0 + 1 < nvalid) {
+                z = *reinterpret_cast<const C *>(p + x0);
+            } else {
+                z.x = p[x0];
+                if (x0 + 1 < nvalid) z.y = p[x0 + 1];
+            }
+            z.x *= a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0);
+            if (x0 + 1 < nvalid) z.y *= a.wscalar * cell_weight(a.wcell, row, a.rows_per_comp, a.in_rs, x0 + 1);
         }
-        A[sw(n * TR + rr)] = z;
-    }
-    __syncthreads();
-    const C *Z = gen_fft<C, false, kGenMaxRadixRows>(A, B, 1, 0, g, twx, 2);
+        return z;
+    };
+    const GenSmemSt<C, true> none{nullptr, TR, L};
+    const C *Z = gen_fft_io<C, false, true, false>(A, B, g, twx, 2, ld, none);
     const T h = (T)0.5;
     for (int e = threadIdx.x; e < (L + 1) * TR; e += blockDim.x) {
         const int rr = udiv(e, L + 1, g.mL1), k = e - rr * (L + 1), row = row0 + rr;
         if (row >= nrows) continue;
-        const C p = Z[sw((k == L ? 0 : k) * TR + rr)];
-        const C q = Z[sw((k == 0 ? 0 : L - k) * TR + rr)];
+        const C p = Z[sw(rr * L + (k == L ? 0 : k))];
+        const C q = Z[sw(rr * L + (k == 0 ? 0 : L - k))];
         const C E = cmk<C>(h * (p.x + q.x), h * (p.y - q.y));
         const C O = cmk<C>(h * (p.y + q.y), -h * (p.x - q.x));
         out[(int64_t)row * out_rs + k] = cadd(E, cmul(O, __ldg(&twx[k])));
     }
 }
 
-// Complex-to-real rows (as k_x_inv) with the XOut epilogue; energy partials
-// one per CTA.
+// Complex-to-real rows (as k_x_inv): the first stage forms the packed
+// spectrum from X[k] and X[L-k] in global memory, the last applies the XOut
+// epilogue (energy partials one per CTA).
 template <typename T>
 __global__ void __launch_bounds__(kGenThreads, sizeof(T) == 4 ? 3 : 1)
 k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
@@ -377,8 +518,8 @@ k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nr
     const int L = g.L, TR = g.TC, TS = swsize(L * TR);
     C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
     const int row0 = blockIdx.x * TR;
-    for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
-        const int rr = udiv(e, L, g.mL), k = e - rr * L, row = row0 + rr;
+    auto ld = [&](int k, int rr) {
+        const int row = row0 + rr;
         C z = cmk<C>(0, 0);
         if (row < nrows) {
             const C *p = in + (int64_t)row * in_rs;
@@ -388,30 +529,38 @@ k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nr
             const C O2 = cmulc(D, __ldg(&twx[k]));
             z = cmk<C>(E2.x - O2.y, E2.y + O2.x);
         }
-        A[sw(k * TR + rr)] = z;
-    }
-    __syncthreads();
-    const C *Z = gen_fft<C, true, kGenMaxRadixRows>(A, B, 1, 0, g, twx, 2);
+        return z;
+    };
     const T gsc = o.gdev ? (T)(*o.gdev) : (T)1;
     const T oscale = o.oscale * gsc;
     T acc = 0;
-    // outputs x < nvalid only: n < (nvalid + 1) / 2 of each row
-    const int nh = (nvalid + 1) / 2 < L ? (nvalid + 1) / 2 : L;
-    for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
-        const int rr = udiv(e, L, g.mL), n = e - rr * L, row = row0 + rr;
-        if (row >= nrows || n >= nh) continue;
-        const C z = Z[sw(n * TR + rr)];
+    const bool pairs = (o.out_rs & 1) == 0;  // rows start on a pair boundary: vector stores and loads
+    auto st = [&](int n, int rr, C z) {
+        const int row = row0 + rr, x0 = 2 * n;
+        if (row >= nrows || x0 >= nvalid) return;
         const T hv[2] = {z.x * o.scale, z.y * o.scale};
+        const int64_t idx0 = (int64_t)row * o.out_rs + x0;
+        if (pairs && x0 + 1 < nvalid) {
+            const T w0 = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x0);
+            const T w1 = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x0 + 1);
+            if (o.out) *reinterpret_cast<C *>(o.out + idx0) = cmk<C>(hv[0] * oscale * w0, hv[1] * oscale * w1);
+            if (o.partials) {
+                const C m = *reinterpret_cast<const C *>(o.Mref + idx0);
+                acc += o.mscale * (w0 * m.x * hv[0] + w1 * m.y * hv[1]);
+            }
+            return;
+        }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int x = 2 * n + u;
+            const int x = x0 + u;
             if (x >= nvalid) continue;
             const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
-            const int64_t idx = (int64_t)row * o.out_rs + x;
+            const int64_t idx = idx0 + u;
             if (o.out) o.out[idx] = hv[u] * oscale * w;
             if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
         }
-    }
+    };
+    gen_fft_io<C, true, true, true>(A, B, g, twx, 2, ld, st);
     if (o.partials) block_partial<kGenThreads>((double)acc, o.partials, blockIdx.x);
 }
 

@@ -71,6 +71,7 @@ bool gen_plan(int L, int tile, GenRadix &g, int maxr)
         g.NS[s] = NS;
         g.mNS[s] = magic_of(NS);
         g.mPer[s] = magic_of(L / r[s] * g.TC);
+        g.mNB[s] = magic_of(L / r[s]);
         NS *= r[s];
     }
     g.n = n;
@@ -89,7 +90,7 @@ cudaError_t MixedPasses<T>::x_fwd(int L, const XIn<T> &a, int nrows, int nvalid,
     if (nrows <= 0) return cudaSuccess;
     GenRadix g;
     if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
-    const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
+    const size_t sm = gen_io_buffers(g.n, false) * swsize(L * g.TC) * sizeof(C);
     cudaError_t e = allow_smem<k_gen_x_fwd<T>>(sm);
     if (e != cudaSuccess) return e;
     k_gen_x_fwd<T><<<(nrows + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(a, nrows, nvalid, out, out_rs, twx, g);
@@ -111,7 +112,7 @@ cudaError_t MixedPasses<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, 
     if (nrows <= 0) return cudaSuccess;
     GenRadix g;
     if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
-    const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
+    const size_t sm = gen_io_buffers(g.n, true) * swsize(L * g.TC) * sizeof(C);
     cudaError_t e = allow_smem<k_gen_x_inv<T>>(sm);
     if (e != cudaSuccess) return e;
     k_gen_x_inv<T><<<(nrows + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(in, in_rs, nrows, nvalid, o, twx, g);
@@ -125,7 +126,7 @@ cudaError_t MixedPasses<T>::col(int L, bool inv, const C *in, C *out, int ncols,
     if (ncols <= 0) return cudaSuccess;
     GenRadix g;
     if (!gen_plan(L, gen_tile_elems<T>(false), g, kGenMaxRadixRows)) return cudaErrorInvalidValue;
-    const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
+    const size_t sm = gen_io_buffers(g.n, true) * swsize(L * g.TC) * sizeof(C);
     const unsigned mw = magic_of(width);
     const int grid = (ncols + g.TC - 1) / g.TC;
     cudaError_t e;
