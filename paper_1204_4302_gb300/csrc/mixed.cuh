@@ -28,6 +28,7 @@ struct GenRadix {
     unsigned mPer[kGenMaxStages];  // division by (L / r) TC
     unsigned mNB[kGenMaxStages];   // division by L / r
     unsigned mTC, mL, mL1;         // division by TC, L, L + 1
+    unsigned mCols;                // division by the grid columns of a tile (z pass: TC / 3)
 };
 
 constexpr int kGenThreads = 256;
@@ -211,87 +212,6 @@ template <int R, bool INV, typename C> struct MixDFT {
     }
 };
 
-// One Stockham stage s of radix R from src to dst, ncomp tiles of [L][TC]
-// (component stride cstride, swizzled as everywhere). Butterfly b of a
-// component: j = b / TC (0 <= j < L / R), column b % TC; it reads rows
-// j + r L / R, applies W^{r k} (k = j mod NS, W the root of order NS R) and
-// writes rows (j / NS) NS R + k + r NS. tw: W_P^m with P = L twstride.
-template <typename C, int R, bool INV>
-__device__ __forceinline__ void gen_stage(const C *src, C *dst, int ncomp, int cstride, const GenRadix &g, int s,
-                                          const C *__restrict__ tw, int twstride)
-{
-    const int L = g.L, TC = g.TC, NS = g.NS[s];
-    const int NB = L / R, per = NB * TC, total = ncomp * per;
-    const int tws = (L / (NS * R)) * twstride;
-    const unsigned mPer = g.mPer[s], mNS = g.mNS[s], mTC = g.mTC;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int comp = ncomp == 1 ? 0 : udiv(b, per, mPer);
-        const int bb = b - comp * per;
-        const int j = udiv(bb, TC, mTC), col = bb - j * TC;
-        const C *sp = src + comp * cstride;
-        C v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sp[sw((j + r * NB) * TC + col)];
-        const int q = udiv(j, NS, mNS), k = j - q * NS;
-        if (k > 0) {
-            const int kt = k * tws;
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const C w = __ldg(&tw[r * kt]);
-                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
-            }
-        }
-        MixDFT<R, INV, C>::run(v);
-        C *o = dst + comp * cstride;
-        const int d = q * NS * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) o[sw((d + r * NS) * TC + col)] = v[r];
-    }
-}
-
-// Whole transform of the tiles in a (b is the second buffer); returns the
-// buffer that holds the result. Stage radices up to MAXR are instantiated
-// (the plan never uses more): the row and column passes, memory bound, keep
-// MAXR = 16 and fewer registers; the fused z pass takes up to 32.
-template <typename C, bool INV, int MAXR>
-__device__ __forceinline__ C *gen_fft(C *a, C *b, int ncomp, int cstride, const GenRadix &g, const C *__restrict__ tw,
-                                      int twstride)
-{
-    C *src = a, *dst = b;
-    for (int s = 0; s < g.n; ++s) {
-        switch (g.r[s]) {
-        case 2: gen_stage<C, 2, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 3: gen_stage<C, 3, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 4: gen_stage<C, 4, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 5: gen_stage<C, 5, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 6: gen_stage<C, 6, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 7: gen_stage<C, 7, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 8: gen_stage<C, 8, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 9: gen_stage<C, 9, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 10: gen_stage<C, 10, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 12: gen_stage<C, 12, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 14: gen_stage<C, 14, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 15: gen_stage<C, 15, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 16: gen_stage<C, 16, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 18: if constexpr (MAXR >= 18) gen_stage<C, 18, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 20: if constexpr (MAXR >= 20) gen_stage<C, 20, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 21: if constexpr (MAXR >= 21) gen_stage<C, 21, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 24: if constexpr (MAXR >= 24) gen_stage<C, 24, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 25: if constexpr (MAXR >= 25) gen_stage<C, 25, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 27: if constexpr (MAXR >= 27) gen_stage<C, 27, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 28: if constexpr (MAXR >= 28) gen_stage<C, 28, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 30: if constexpr (MAXR >= 30) gen_stage<C, 30, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        case 32: if constexpr (MAXR >= 32) gen_stage<C, 32, INV>(src, dst, ncomp, cstride, g, s, tw, twstride); break;
-        default: break;
-        }
-        __syncthreads();
-        C *t = src;
-        src = dst;
-        dst = t;
-    }
-    return src;
-}
-
 constexpr int kGenMaxRadixRows = 16, kGenMaxRadixZ = 32;
 
 // Stages with caller-supplied ends: the first stage reads its inputs through
@@ -355,7 +275,7 @@ __device__ __forceinline__ void gen_stage_io(const GenRadix &g, int s, const C *
     }
 }
 
-template <typename C, bool INV, bool XROW, typename LD, typename ST>
+template <typename C, bool INV, bool XROW, int MAXR, typename LD, typename ST>
 __device__ __forceinline__ void gen_stage_any(const GenRadix &g, int s, const C *__restrict__ tw, int twstride,
                                               const LD &ld, const ST &st)
 {
@@ -372,16 +292,26 @@ __device__ __forceinline__ void gen_stage_any(const GenRadix &g, int s, const C 
     case 12: gen_stage_io<C, 12, INV, XROW>(g, s, tw, twstride, ld, st); break;
     case 14: gen_stage_io<C, 14, INV, XROW>(g, s, tw, twstride, ld, st); break;
     case 15: gen_stage_io<C, 15, INV, XROW>(g, s, tw, twstride, ld, st); break;
-    default: gen_stage_io<C, 16, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 16: gen_stage_io<C, 16, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 18: if constexpr (MAXR >= 18) gen_stage_io<C, 18, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 20: if constexpr (MAXR >= 20) gen_stage_io<C, 20, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 21: if constexpr (MAXR >= 21) gen_stage_io<C, 21, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 24: if constexpr (MAXR >= 24) gen_stage_io<C, 24, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 25: if constexpr (MAXR >= 25) gen_stage_io<C, 25, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 27: if constexpr (MAXR >= 27) gen_stage_io<C, 27, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 28: if constexpr (MAXR >= 28) gen_stage_io<C, 28, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 30: if constexpr (MAXR >= 30) gen_stage_io<C, 30, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    case 32: if constexpr (MAXR >= 32) gen_stage_io<C, 32, INV, XROW>(g, s, tw, twstride, ld, st); break;
+    default: break;
     }
 }
 
-// Whole transform (radices <= 16) from ld to st (LASTG) or to a shared
+// Whole transform (radices <= MAXR) from ld to st (LASTG) or to a shared
 // buffer that is returned (A, or B when the stages end there). Shared
 // buffers used: A for the first stage's output, B from the third stage on
 // (LASTG) or from the second (otherwise). Every input is read, and a barrier
 // passed, before the first output is written (in-place calls are safe).
-template <typename C, bool INV, bool XROW, bool LASTG, typename LD, typename ST>
+template <typename C, bool INV, bool XROW, bool LASTG, int MAXR, typename LD, typename ST>
 __device__ __forceinline__ C *gen_fft_io(C *A, C *B, const GenRadix &g, const C *__restrict__ tw, int twstride,
                                          const LD &ld0, const ST &stN)
 {
@@ -390,7 +320,7 @@ __device__ __forceinline__ C *gen_fft_io(C *A, C *B, const GenRadix &g, const C 
         if (n == 1) {
             // one stage: through shared memory, so that an in-place call (the
             // same global buffer read and written) reads every input first
-            gen_stage_any<C, INV, XROW>(g, 0, tw, twstride, ld0, GenSmemSt<C, XROW>{A, g.TC, g.L});
+            gen_stage_any<C, INV, XROW, MAXR>(g, 0, tw, twstride, ld0, GenSmemSt<C, XROW>{A, g.TC, g.L});
             __syncthreads();
             for (int e = threadIdx.x; e < g.L * g.TC; e += blockDim.x) {
                 int row, col;
@@ -406,11 +336,11 @@ __device__ __forceinline__ C *gen_fft_io(C *A, C *B, const GenRadix &g, const C 
             return nullptr;
         }
     }
-    gen_stage_any<C, INV, XROW>(g, 0, tw, twstride, ld0, GenSmemSt<C, XROW>{A, g.TC, g.L});
+    gen_stage_any<C, INV, XROW, MAXR>(g, 0, tw, twstride, ld0, GenSmemSt<C, XROW>{A, g.TC, g.L});
     __syncthreads();
     C *src = A, *dst = B;
     for (int s = 1; s < (LASTG ? n - 1 : n); ++s) {
-        gen_stage_any<C, INV, XROW>(g, s, tw, twstride, GenSmemLd<C, XROW>{src, g.TC, g.L},
+        gen_stage_any<C, INV, XROW, MAXR>(g, s, tw, twstride, GenSmemLd<C, XROW>{src, g.TC, g.L},
                                     GenSmemSt<C, XROW>{dst, g.TC, g.L});
         __syncthreads();
         C *t = src;
@@ -418,7 +348,7 @@ __device__ __forceinline__ C *gen_fft_io(C *A, C *B, const GenRadix &g, const C 
         dst = t;
     }
     if constexpr (LASTG) {
-        gen_stage_any<C, INV, XROW>(g, n - 1, tw, twstride, GenSmemLd<C, XROW>{src, g.TC, g.L}, stN);
+        gen_stage_any<C, INV, XROW, MAXR>(g, n - 1, tw, twstride, GenSmemLd<C, XROW>{src, g.TC, g.L}, stN);
         return nullptr;
     } else {
         return src;
@@ -458,7 +388,7 @@ k_gen_col(const typename Cplx<T>::type *__restrict__ in, typename Cplx<T>::type 
             out[(int64_t)slab * oss + (int64_t)row * ors + (f - slab * width)] = v;
         }
     };
-    gen_fft_io<C, INV, false, true>(A, B, g, tw, twstride, ld, st);
+    gen_fft_io<C, INV, false, true, kGenMaxRadixRows>(A, B, g, tw, twstride, ld, st);
 }
 
 // Real-to-complex rows (as k_x_fwd): pack pairs of reals, transform of
@@ -492,7 +422,7 @@ k_gen_x_fwd(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict_
         return z;
     };
     const GenSmemSt<C, true> none{nullptr, TR, L};
-    const C *Z = gen_fft_io<C, false, true, false>(A, B, g, twx, 2, ld, none);
+    const C *Z = gen_fft_io<C, false, true, false, kGenMaxRadixRows>(A, B, g, twx, 2, ld, none);
     const T h = (T)0.5;
     for (int e = threadIdx.x; e < (L + 1) * TR; e += blockDim.x) {
         const int rr = udiv(e, L + 1, g.mL1), k = e - rr * (L + 1), row = row0 + rr;
@@ -560,13 +490,15 @@ k_gen_x_inv(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nr
             if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
         }
     };
-    gen_fft_io<C, true, true, true>(A, B, g, twx, 2, ld, st);
+    gen_fft_io<C, true, true, true, kGenMaxRadixRows>(A, B, g, twx, 2, ld, st);
     if (o.partials) block_partial<kGenThreads>((double)acc, o.partials, blockIdx.x);
 }
 
-// Fused z pass (as k_z_conv): three components per column tile, forward
-// transforms, the 3x3 product with the folded tensor spectrum, inverse
-// transforms, rows < nrows stored. Column f = ky * width + kx.
+// Fused z pass (as k_z_conv): the three components of TC = g.TC / 3 columns
+// form one [row][3 TC] tile (component-major columns). Forward transform
+// with the first stage reading global memory (rows < nrows), the 3x3
+// product with the folded tensor spectrum in shared memory, inverse
+// transform whose last stage stores rows < nrows. Column f = ky * width + kx.
 template <typename T>
 __global__ void __launch_bounds__(kGenThreads)
 k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsigned mw, int64_t ss, int64_t rs,
@@ -575,26 +507,28 @@ k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsign
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int L = g.L, TC = g.TC, TS = swsize(L * TC);
-    C *A = reinterpret_cast<C *>(smraw), *B = A + 3 * TS;
+    const int L = g.L, TCC = g.TC, TC = TCC / 3, TS = swsize(L * TCC);
+    C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
     const int f0 = blockIdx.x * TC;
-    for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
-        C v0 = cmk<C>(0, 0), v1 = v0, v2 = v0;
-        if (f < ncols && r < nrows) {
-            const int slab = udiv(f, width, mw);
-            const int64_t q = (int64_t)slab * ss + (int64_t)r * rs + (f - slab * width);
-            v0 = S[q]; v1 = S[q + cs]; v2 = S[q + 2 * cs];
-        }
-        A[sw(e)] = v0; A[TS + sw(e)] = v1; A[2 * TS + sw(e)] = v2;
-    }
-    __syncthreads();
-    C *F = gen_fft<C, false, kGenMaxRadixZ>(A, B, 3, TS, g, tw, twstride);
+    // column cc of the tile: component cc / TC, grid column f0 + cc % TC
+    auto gaddr = [&](int row, int cc, bool &ok) {
+        const int comp = cc >= 2 * TC ? 2 : (cc >= TC ? 1 : 0), f = f0 + cc - comp * TC;
+        ok = f < ncols && row < nrows;
+        const int slab = udiv(f, width, mw);
+        return (int64_t)slab * ss + (int64_t)row * rs + (f - slab * width) + comp * cs;
+    };
+    auto ld = [&](int row, int cc) {
+        bool ok;
+        const int64_t q = gaddr(row, cc, ok);
+        return ok ? S[q] : cmk<C>(0, 0);
+    };
+    const GenSmemSt<C, false> none{nullptr, TCC, L};
+    C *F = gen_fft_io<C, false, false, false, kGenMaxRadixZ>(A, B, g, tw, twstride, ld, none);
     C *G = F == A ? B : A;
     const int hy = Py / 2 + 1, hz = L / 2 + 1;
     const int64_t plane = (int64_t)hz * hy * Kx;
     for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
-        const int kz = udiv(e, TC, g.mTC), f = f0 + e - kz * TC;
+        const int kz = udiv(e, TC, g.mCols), c = e - kz * TC, f = f0 + c;
         if (f >= ncols) continue;
         const int ky = udiv(f, width, mw), kx = f - ky * width;
         const bool fy = ky > Py / 2, fz = kz > L / 2;
@@ -605,21 +539,20 @@ k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsign
         const T nxy = sy * __ldg(&nhat[3 * plane + bq]);
         const T nxz = sz * __ldg(&nhat[4 * plane + bq]);
         const T nyz = sy * sz * __ldg(&nhat[5 * plane + bq]);
-        const C mx = F[sw(e)], my = F[TS + sw(e)], mz = F[2 * TS + sw(e)];
-        F[sw(e)] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
-        F[TS + sw(e)] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
-        F[2 * TS + sw(e)] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+        // row kz: the components at columns c, TC + c, 2 TC + c
+        const int i0 = sw(kz * TCC + c), i1 = sw(kz * TCC + TC + c), i2 = sw(kz * TCC + 2 * TC + c);
+        const C mx = F[i0], my = F[i1], mz = F[i2];
+        F[i0] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+        F[i1] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+        F[i2] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
     }
     __syncthreads();
-    const C *res = gen_fft<C, true, kGenMaxRadixZ>(F, G, 3, TS, g, tw, twstride);
-    for (int e = threadIdx.x; e < nrows * TC; e += blockDim.x) {
-        const int r = udiv(e, TC, g.mTC), f = f0 + e - r * TC;
-        if (f < ncols) {
-            const int slab = udiv(f, width, mw);
-            const int64_t q = (int64_t)slab * ss + (int64_t)r * rs + (f - slab * width);
-            S[q] = res[sw(e)]; S[q + cs] = res[TS + sw(e)]; S[q + 2 * cs] = res[2 * TS + sw(e)];
-        }
-    }
+    auto st = [&](int row, int cc, C v) {
+        bool ok;
+        const int64_t q = gaddr(row, cc, ok);
+        if (ok) S[q] = v;
+    };
+    gen_fft_io<C, true, false, true, kGenMaxRadixZ>(G, F, g, tw, twstride, GenSmemLd<C, false>{F, TCC, L}, st);
 }
 
 }  // namespace demag

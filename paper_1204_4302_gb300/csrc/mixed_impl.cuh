@@ -56,13 +56,16 @@ bool gen_split(int m, int maxr, int depth, int *cur, int n, int *best, int &bn, 
 }
 
 // Stage plan of a mixed-radix transform of length L (a product of 2, 3, 5
-// and 7, L < 2048) over tiles of about `tile` elements, radices <= maxr.
-bool gen_plan(int L, int tile, GenRadix &g, int maxr)
+// and 7, L < 2048) over tiles of about `tile` elements, radices <= maxr;
+// comps components per grid column share the tile (z pass: 3).
+bool gen_plan(int L, int tile, GenRadix &g, int maxr, int comps = 1)
 {
     memset(&g, 0, sizeof g);
     if (L < 2 || L >= 2048) return false;
     g.L = L;
-    g.TC = tile / L > 1 ? tile / L : 1;
+    const int cols = tile / L > 1 ? tile / L : 1;  // grid columns (rows of the x passes) per tile
+    g.TC = comps * cols;                             // tile columns: the components side by side
+    g.mCols = magic_of(cols);
     int cur[4], r[4], n = 0, mx = 0;
     if (!gen_split(L, maxr, 4, cur, 0, r, n, mx) || n == 0) return false;
     int NS = 1;
@@ -149,11 +152,12 @@ cudaError_t MixedPasses<T>::zconv(int L, C *S, int ncols, int width, int64_t ss,
     if (ncols <= 0) return cudaSuccess;
     if (nrows > L) return cudaErrorInvalidValue;
     GenRadix g;
-    if (!gen_plan(L, gen_tile_elems<T>(true), g, kGenMaxRadixZ)) return cudaErrorInvalidValue;
-    const size_t sm = 6 * swsize(L * g.TC) * sizeof(C);
+    if (!gen_plan(L, gen_tile_elems<T>(true), g, kGenMaxRadixZ, 3)) return cudaErrorInvalidValue;
+    const int cols = g.TC / 3;
+    const size_t sm = 2 * swsize(L * g.TC) * sizeof(C);
     cudaError_t e = allow_smem<k_gen_zconv<T>>(sm);
     if (e != cudaSuccess) return e;
-    k_gen_zconv<T><<<(ncols + g.TC - 1) / g.TC, kGenThreads, sm, st>>>(S, ncols, width, magic_of(width), ss, rs, cs,
+    k_gen_zconv<T><<<(ncols + cols - 1) / cols, kGenThreads, sm, st>>>(S, ncols, width, magic_of(width), ss, rs, cs,
                                                                        nrows, nhat, Py, Kx, tw, twstride, g);
     return cudaGetLastError();
 }
