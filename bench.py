@@ -410,6 +410,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.skip_padding:
         padding = run_padding(args, dev)
 
+    configs = None
+    if not args.skip_configs:
+        configs = run_configs(args, dev)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cpu = cpu_baseline(args.cpu_sample)
@@ -441,6 +445,7 @@ def run_ours(args, rank, world, local_rank):
             "scalar_potential": sp,
             "tensor_grid": tgr,
             "padding": padding,
+            "configs": configs,
             "energy_J": E_val,
             "passes": per_pass,
             "roofline": roof,
@@ -699,6 +704,96 @@ def run_padding(args, dev):
     return out
 
 
+def run_configs(args, dev):
+    """The other workloads of the method's benchmark set, each on its own plan
+    (autotuned): the 16^3 cube (FP64 and FP32), the 512x128x4 thin film
+    (vortex + 5% noise), the 64^3 grid with a radius-32 sphere mask, the 128^3
+    energy + gradient, and the 512x512x128 smooth state (forward field plus
+    adjoint). Time per call from CUDA events (the small grids are L2
+    resident: launch- and latency-bound, no HBM roofline), cells/s, and the
+    FP32 field's rel-max error against the FP64 plan of the same call."""
+    import numpy as np
+    import torch
+
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300 import inputs
+    from paper_1204_4302_gb300.plan import Plan
+    st = torch.cuda.current_stream(dev)
+
+    def timed(fn, k):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(k):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def relmax(a, b):
+        return float((a.double() - b.double()).abs().max() / b.double().abs().max())
+
+    out = []
+    k = max(20, args.steps)
+    specs = [
+        ("cube 16^3, 1 nm, random unit m, field + energy", (16, 16, 16), (1e-9,) * 3,
+         MS * inputs.random_unit((16, 16, 16), seed=1), None, "field"),
+        ("thin film 512x128x4, 2 nm, vortex + 5% noise, field + energy", (512, 128, 4), (2e-9,) * 3,
+         MS * inputs.vortex_noise((512, 128, 4), (1024e-9, 256e-9, 8e-9), rc=0.14 * 1024e-9, noise=0.05, seed=2),
+         None, "field"),
+        ("sphere of radius 32 cells in 64^3, 2 nm, M = 0 outside, field + energy", (64, 64, 64), (2e-9,) * 3,
+         MS * inputs.sphere_mask((64, 64, 64), 32)[None] * inputs.random_unit((64, 64, 64), seed=3), None, "field"),
+        ("cube 128^3, 2 nm, energy + dE/dm", (128, 128, 128), (2e-9,) * 3,
+         inputs.random_unit((128, 128, 128), seed=5), None, "grad"),
+        ("cuboid 512x512x128, 1 nm, smooth state, field + adjoint", (512, 512, 128), (1e-9,) * 3,
+         MS * inputs.smooth_random((512, 512, 128), 8, seed=6), None, "fwdadj"),
+    ]
+    for name, n, d, Mnp, _, kind in specs:
+        cells = n[0] * n[1] * n[2]
+        row = {"workload": name, "grid": list(n)}
+        res = {}
+        for prec in ("f32", "f64"):
+            dt = torch.float32 if prec == "f32" else torch.float64
+            plan = Plan(n, d, prec=prec, device=dev)
+            if prec == "f32":
+                plan.autotune(use_cache=False)
+            M = torch.tensor(Mnp, dtype=dt, device=dev)
+            H = torch.empty_like(M)
+            E = torch.empty((), dtype=torch.float64, device=dev)
+            if kind == "field":
+                fn = lambda: B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(),  # noqa: E731
+                                                  st.cuda_stream)
+            elif kind == "grad":
+                fn = lambda: B.demag_energy_grad(plan.handle, M.data_ptr(), None, MS, E.data_ptr(),  # noqa: E731
+                                                 H.data_ptr(), None, st.cuda_stream)
+            else:
+                H2 = torch.empty_like(M)
+                fn = lambda: (B.demag_field(plan.handle, M.data_ptr(), H.data_ptr(), st.cuda_stream),  # noqa: E731
+                              B.demag_field_adjoint(plan.handle, H.data_ptr(), H2.data_ptr(), st.cuda_stream))
+            ms = timed(fn, k if prec == "f32" else max(3, k // 4))
+            fn()
+            torch.cuda.synchronize()
+            res[prec] = (ms, H.clone(), E.item() if kind != "fwdadj" else None)
+            info = plan.info()
+            plan.close()
+            del M
+        ms32, H32, E32 = res["f32"]
+        ms64, H64, E64 = res["f64"]
+        row.update({"padded": [info["px"], info["py"], info["pz"]], "ms_per_call_f32": round(ms32, 4),
+                    "cells_per_s_f32": cells / (ms32 / 1e3), "ms_per_call_f64": round(ms64, 4),
+                    "speedup_f32_over_f64": round(ms64 / ms32, 2),
+                    "f32_rel_max_err_vs_f64": relmax(H32, H64),
+                    "energy_rel_diff_f32_f64": abs(E32 - E64) / abs(E64) if E64 else None,
+                    "output": {"field": "H", "grad": "dE/dm", "fwdadj": "H (the adjoint runs after it)"}[kind]})
+        out.append(row)
+        del res, H32, H64
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- oracle side
 def _oracle_sample(k: int):
     """The oracle's field on a k^3 grid of the same workload (same cell, same
@@ -785,6 +880,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-padding", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--skip-sp", action="store_true", help="skip the scalar-potential method leg")
     ap.add_argument("--skip-tg", action="store_true", help="skip the tensor-grid method leg")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")

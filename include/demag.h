@@ -330,6 +330,15 @@ void demag_batch_destroy(demag_batch_t batch);
 /* Number of kernels this plan has launched since creation. */
 long demag_launch_count(demag_plan_t plan);
 
+/* CUDA-graph replay (default off). When on, each distinct call of this plan
+ * (the same pointers, scales and kernel variants) is captured once into a
+ * CUDA graph on a private stream and later calls replay it with one graph
+ * launch on the caller's stream; up to 4 calls are kept (least recently used
+ * evicted). Results are the same; small grids, whose calls are bound by
+ * launch overhead, get faster. Calls with per-kernel timing on, and the
+ * autotuner's timings, launch directly. Disabling frees the graphs. */
+demag_status demag_set_graphs(demag_plan_t plan, int enable);
+
 /* Autotuner: times the kernel variants that exist for this plan's sizes (the
  * z-pass tile width and the y-pass radix order of the two-stage transforms)
  * with CUDA events on the plan's own sizes (five timed calls after two

@@ -39,7 +39,7 @@ EXPORTS = [
     "demag_field_host", "demag_plan_info", "demag_set_timing", "demag_get_timing",
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
     "demag_energy_noalloc",
-    "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding", "demag_padded_lengths",
+    "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding", "demag_padded_lengths", "demag_set_graphs",
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
@@ -104,6 +104,7 @@ def load(path: str | Path | None = None):
         "demag_field_host": (S, [P, P, P, P]),
         "demag_plan_info": (S, [P, POINTER(demag_info)]),
         "demag_set_timing": (S, [P, I]),
+        "demag_set_graphs": (S, [P, I]),
         "demag_get_timing": (S, [P, POINTER(c_double), POINTER(c_long), I]),
         "demag_launch_count": (c_long, [P]),
         "demag_plan_destroy": (None, [P]),
@@ -326,6 +327,10 @@ def demag_batch_create(dims, cells, prec=DEMAG_F32, pad_mode=None):
         _check(load().demag_batch_create_ex(n, d, c, int(prec), ctypes.byref(opt), ctypes.byref(h)),
                "demag_batch_create_ex")
     return h.value
+
+
+def demag_set_graphs(plan, enable=True):
+    _check(load().demag_set_graphs(_p(plan), 1 if enable else 0), "demag_set_graphs")
 
 
 def demag_padded_lengths(nx, ny, nz, px=0, py=0, pz=0, pad_mode=0):

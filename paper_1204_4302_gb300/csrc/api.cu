@@ -393,6 +393,95 @@ demag_status check_scalar_ptr(const void *ptr, const char *name)
     return DEMAG_OK;
 }
 
+// ----- CUDA-graph replay: each distinct call (pointers, scales, variants) is
+// captured once on a private stream and replayed with one graph launch, so
+// the host issues one launch per call instead of five or six (small grids
+// are launch-bound).
+struct GraphEntry {
+    FieldJob job;
+    int z, y, x;
+    cudaGraphExec_t exec;
+    long kernels;
+    unsigned long long stamp;
+};
+struct GraphCache {
+    std::vector<GraphEntry> entries;
+    cudaStream_t cap = nullptr;
+    unsigned long long clock = 0;
+};
+constexpr size_t kGraphSlots = 4;
+
+bool same_job(const FieldJob &a, const FieldJob &b)
+{
+    return a.in == b.in && a.phi == b.phi && a.wcell == b.wcell && a.wscalar == b.wscalar && a.out == b.out &&
+           a.oscale == b.oscale && a.gdev == b.gdev && a.E_dev == b.E_dev;
+}
+
+void graphs_free(demag_plan *p)
+{
+    GraphCache *G = static_cast<GraphCache *>(p->graphs);
+    if (!G) return;
+    for (auto &en : G->entries) cudaGraphExecDestroy(en.exec);
+    if (G->cap) cudaStreamDestroy(G->cap);
+    delete G;
+    p->graphs = nullptr;
+}
+
+demag_status run_direct(demag_plan *p, const FieldJob &job, cudaStream_t st)
+{
+    if (p->method == DEMAG_METHOD_SP) {
+        if (p->prec == DEMAG_F32) return run_field_sp<float>(p, job, st);
+        return run_field_sp<double>(p, job, st);
+    }
+    if (p->prec == DEMAG_F32) return run_field<float>(p, job, st);
+    return run_field<double>(p, job, st);
+}
+
+demag_status run_graph(demag_plan *p, const FieldJob &job, cudaStream_t st)
+{
+    GraphCache *G = static_cast<GraphCache *>(p->graphs);
+    for (auto &en : G->entries)
+        if (same_job(en.job, job) && en.z == p->zvariant && en.y == p->yvariant && en.x == p->xvariant) {
+            en.stamp = ++G->clock;
+            const cudaError_t e = cudaGraphLaunch(en.exec, st);
+            if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            p->launches += en.kernels;
+            return DEMAG_OK;
+        }
+    cudaError_t e;
+    if (!G->cap && (e = cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(DEMAG_ERR_CUDA, std::string("capture stream: ") + cudaGetErrorString(e));
+    const long l0 = p->launches;
+    if ((e = cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return fail(DEMAG_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    const demag_status s = run_direct(p, job, G->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(G->cap, &graph);
+    const long kernels = p->launches - l0;
+    p->launches = l0;  // the capture itself ran nothing
+    if (s != DEMAG_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return s != DEMAG_OK ? s : fail(DEMAG_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    if (G->entries.size() >= kGraphSlots) {  // evict the least recently used call
+        size_t old = 0;
+        for (size_t i = 1; i < G->entries.size(); ++i)
+            if (G->entries[i].stamp < G->entries[old].stamp) old = i;
+        cudaGraphExecDestroy(G->entries[old].exec);
+        G->entries.erase(G->entries.begin() + old);
+    }
+    G->entries.push_back(GraphEntry{job, p->zvariant, p->yvariant, p->xvariant, exec, kernels, ++G->clock});
+    if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess)
+        return fail(DEMAG_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    p->launches += kernels;
+    return DEMAG_OK;
+}
+
 demag_status run_job(demag_plan *p, const FieldJob &job, void *stream)
 {
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
@@ -425,14 +514,12 @@ demag_status run_job(demag_plan *p, const FieldJob &job, void *stream)
         }
         if (!job.out && !job.E_dev && !job.phi)
             return fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no output, no energy)");
-        cudaStream_t st = (cudaStream_t)stream;
-        if (p->prec == DEMAG_F32) return run_field_sp<float>(p, job, st);
-        return run_field_sp<double>(p, job, st);
+    } else if (!job.out && !job.E_dev) {
+        return fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no output, no energy)");
     }
-    if (!job.out && !job.E_dev) return fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no output, no energy)");
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->prec == DEMAG_F32) return run_field<float>(p, job, st);
-    return run_field<double>(p, job, st);
+    if (p->use_graphs && p->graphs && !p->timing) return run_graph(p, job, st);
+    return run_direct(p, job, st);
 }
 
 // ----- autotuner cache: one line per tuned geometry, "key zvariant yvariant ms"
@@ -630,6 +717,7 @@ void demag_plan_destroy(demag_plan_t p)
 {
     if (!p) return;
     DeviceGuard g(p->device);
+    graphs_free(p);
     if (p->S2 && p->S2 != p->S1) cudaFree(p->S2);
     cudaFree(p->S1);
     cudaFree(p->nhat32);
@@ -1016,6 +1104,19 @@ demag_status demag_plan_info(demag_plan_t p, demag_info *info)
     return DEMAG_OK;
 }
 
+demag_status demag_set_graphs(demag_plan_t p, int enable)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    DeviceGuard g(p->device);
+    if (enable) {
+        if (!p->graphs) p->graphs = new GraphCache;
+    } else {
+        graphs_free(p);
+    }
+    p->use_graphs = enable != 0;
+    return DEMAG_OK;
+}
+
 demag_status demag_set_timing(demag_plan_t p, int enable)
 {
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
@@ -1096,8 +1197,9 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const bool timing = p->timing;
+    const bool timing = p->timing, graphs = p->use_graphs;
     p->timing = false;
+    p->use_graphs = false;  // variants are timed by direct launches
     double best = 1e30;
     int bz = 0, by = 0, bx = 1;
     demag_status rs = DEMAG_OK;
@@ -1117,6 +1219,7 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
             if (rs == DEMAG_OK && ms / 5 < best) { best = ms / 5; bz = z; by = y; bx = x; }
         }
     p->timing = timing;
+    p->use_graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(M);

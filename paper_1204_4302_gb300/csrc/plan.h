@@ -202,4 +202,7 @@ struct demag_plan {
     double pass_ms[8];
     long pass_n[8];
     long launches;
+    // CUDA-graph replay of whole calls (api.cu): cache of captured pipelines
+    bool use_graphs;
+    void *graphs;
 };

@@ -198,6 +198,10 @@ class Plan:
         B.demag_check_pipeline(self.handle)
 
     # ------------------------------------------------------------------ timing
+    def set_graphs(self, enable: bool = True):
+        """Replay each distinct call as one captured CUDA graph (see demag_set_graphs)."""
+        B.demag_set_graphs(self.handle, enable)
+
     def set_timing(self, enable: bool = True):
         B.demag_set_timing(self.handle, enable)
 
