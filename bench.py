@@ -774,6 +774,10 @@ def run_configs(args, dev):
                 fn = lambda: (B.demag_field(plan.handle, M.data_ptr(), H.data_ptr(), st.cuda_stream),  # noqa: E731
                               B.demag_field_adjoint(plan.handle, H.data_ptr(), H2.data_ptr(), st.cuda_stream))
             ms = timed(fn, k if prec == "f32" else max(3, k // 4))
+            if prec == "f32":
+                plan.set_graphs(True)          # the same calls replayed as one captured graph each
+                ms_graph = timed(fn, k)
+                plan.set_graphs(False)
             fn()
             torch.cuda.synchronize()
             res[prec] = (ms, H.clone(), E.item() if kind != "fwdadj" else None)
@@ -783,7 +787,8 @@ def run_configs(args, dev):
         ms32, H32, E32 = res["f32"]
         ms64, H64, E64 = res["f64"]
         row.update({"padded": [info["px"], info["py"], info["pz"]], "ms_per_call_f32": round(ms32, 4),
-                    "cells_per_s_f32": cells / (ms32 / 1e3), "ms_per_call_f64": round(ms64, 4),
+                    "cells_per_s_f32": cells / (ms32 / 1e3), "ms_per_call_f32_graph": round(ms_graph, 4),
+                    "cells_per_s_f32_graph": cells / (ms_graph / 1e3), "ms_per_call_f64": round(ms64, 4),
                     "speedup_f32_over_f64": round(ms64 / ms32, 2),
                     "f32_rel_max_err_vs_f64": relmax(H32, H64),
                     "energy_rel_diff_f32_f64": abs(E32 - E64) / abs(E64) if E64 else None,
