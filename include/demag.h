@@ -83,6 +83,19 @@ typedef struct {
     int pad_mode; /* demag_pad_mode */
 } demag_options;
 
+/* Tensor-spectrum files: the one-time FP64 setup (Sec. 3.1: computed once per
+ * geometry) written to disk and read back instead of recomputed.
+ * demag_plan_save writes a set-up plan's method, precision, sizes, cell
+ * edges, padded lengths and its spectrum tables (FP32 or FP64, the plan's
+ * precision) with an FNV-1a checksum, in the byte order of the writing
+ * machine; synchronises. DEMAG_ERR_NOT_SETUP before demag_tensor_setup.
+ * demag_plan_load validates the whole file on the host (magic, version,
+ * sizes, padded lengths, table size, checksum; DEMAG_ERR_INVALID_ARG with
+ * the reason otherwise) before it touches a device, then creates the plan on
+ * the current device ready to use (no demag_tensor_setup needed). */
+demag_status demag_plan_save(demag_plan_t plan, const char *path);
+demag_status demag_plan_load(const char *path, demag_plan_t *out);
+
 /* Sizes of a plan, as chosen at creation. */
 typedef struct {
     int nx, ny, nz;          /* physical grid */
@@ -97,6 +110,7 @@ typedef struct {
                                 plans, of the kernel tables after removing the
                                 half-cell phase) */
     int method;              /* demag_method */
+    double dx, dy, dz;       /* cell edges */
 } demag_info;
 
 /* Create a plan for an nx x ny x nz grid with cell edges dx, dy, dz.

@@ -8,6 +8,7 @@ e.g. ``tensor.data_ptr()``), streams as integer handles (``cudaStream_t``).
 from __future__ import annotations
 
 import ctypes
+import os
 from ctypes import POINTER, c_double, c_int, c_long, c_size_t, c_void_p
 from pathlib import Path
 
@@ -40,6 +41,7 @@ EXPORTS = [
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
     "demag_energy_noalloc",
     "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding", "demag_padded_lengths", "demag_set_graphs",
+    "demag_plan_save", "demag_plan_load",
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
@@ -71,6 +73,7 @@ class demag_info(ctypes.Structure):
         ("launches_per_field", c_int),
         ("tensor_imag_max", c_double),
         ("method", c_int),
+        ("dx", c_double), ("dy", c_double), ("dz", c_double),
     ]
 
 
@@ -105,6 +108,8 @@ def load(path: str | Path | None = None):
         "demag_plan_info": (S, [P, POINTER(demag_info)]),
         "demag_set_timing": (S, [P, I]),
         "demag_set_graphs": (S, [P, I]),
+        "demag_plan_save": (S, [P, ctypes.c_char_p]),
+        "demag_plan_load": (S, [ctypes.c_char_p, POINTER(c_void_p)]),
         "demag_get_timing": (S, [P, POINTER(c_double), POINTER(c_long), I]),
         "demag_launch_count": (c_long, [P]),
         "demag_plan_destroy": (None, [P]),
@@ -326,6 +331,16 @@ def demag_batch_create(dims, cells, prec=DEMAG_F32, pad_mode=None):
         opt = demag_options(0, 0, 0, int(pad_mode))
         _check(load().demag_batch_create_ex(n, d, c, int(prec), ctypes.byref(opt), ctypes.byref(h)),
                "demag_batch_create_ex")
+    return h.value
+
+
+def demag_plan_save(plan, path):
+    _check(load().demag_plan_save(_p(plan), os.fsencode(path)), "demag_plan_save")
+
+
+def demag_plan_load(path):
+    h = c_void_p()
+    _check(load().demag_plan_load(os.fsencode(path), ctypes.byref(h)), "demag_plan_load")
     return h.value
 
 

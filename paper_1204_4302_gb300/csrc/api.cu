@@ -677,6 +677,36 @@ demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz
     return DEMAG_OK;
 }
 
+// ----- tensor-spectrum files (demag_plan_save / demag_plan_load)
+struct SpecHeader {
+    char magic[8];  // "DMGSPEC" and a zero byte
+    int32_t version;
+    int32_t method, prec;
+    int32_t nx, ny, nz, Px, Py, Pz;
+    int32_t ntab;
+    double dx, dy, dz;
+    double imag_max;
+    uint64_t count;     // table values that follow (float for FP32 plans, double for FP64)
+    uint64_t checksum;  // FNV-1a 64 of the table bytes
+};
+constexpr int32_t kSpecVersion = 1;
+
+uint64_t fnv1a64(const unsigned char *b, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+size_t table_count(const demag_plan *p)
+{
+    const size_t plane = (size_t)(p->Pz / 2 + 1) * (p->Py / 2 + 1) * p->Kx;
+    return (size_t)(p->method == DEMAG_METHOD_SP ? 3 : 6) * plane;
+}
+
 // A plan that is only timed (padding autotuner): its tensor spectrum is
 // zeroed instead of set up. The field passes do the same work whatever the
 // spectrum holds, so the timing is that of a set-up plan, without the FP64
@@ -1090,6 +1120,96 @@ demag_status demag_host_wait(demag_plan_t p)
     return DEMAG_OK;
 }
 
+demag_status demag_plan_save(demag_plan_t p, const char *path)
+{
+    if (!p || !path) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
+    if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    SpecHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "DMGSPEC", 8);
+    h.version = kSpecVersion;
+    h.method = p->method;
+    h.prec = p->prec;
+    h.nx = p->nx; h.ny = p->ny; h.nz = p->nz;
+    h.Px = p->Px; h.Py = p->Py; h.Pz = p->Pz;
+    h.ntab = p->method == DEMAG_METHOD_SP ? 3 : 6;
+    h.dx = p->dx; h.dy = p->dy; h.dz = p->dz;
+    h.imag_max = p->imag_max;
+    h.count = table_count(p);
+    const size_t bytes = h.count * (p->prec == DEMAG_F32 ? sizeof(float) : sizeof(double));
+    std::vector<unsigned char> buf(bytes);
+    const void *src = p->prec == DEMAG_F32 ? (const void *)p->nhat32 : (const void *)p->nhat64;
+    cudaError_t e = cudaMemcpy(buf.data(), src, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("spectrum download: ") + cudaGetErrorString(e));
+    h.checksum = fnv1a64(buf.data(), bytes);
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(DEMAG_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+    const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), 1, bytes, f) == bytes;
+    if (fclose(f) != 0 || !ok) return fail(DEMAG_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    return DEMAG_OK;
+}
+
+demag_status demag_plan_load(const char *path, demag_plan_t *out)
+{
+    if (!out || !path) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(DEMAG_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    SpecHeader h;
+    std::vector<unsigned char> buf;
+    std::string why;
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, "DMGSPEC", 8) != 0) {
+        why = "not a tensor-spectrum file";
+    } else if (h.version != kSpecVersion) {
+        why = "unknown file version";
+    } else if ((h.method != DEMAG_METHOD_DM && h.method != DEMAG_METHOD_SP) || (h.prec != DEMAG_F32 && h.prec != DEMAG_F64) ||
+               h.ntab != (h.method == DEMAG_METHOD_SP ? 3 : 6)) {
+        why = "bad method, precision or table count";
+    } else {
+        const int n[3] = {h.nx, h.ny, h.nz}, P[3] = {h.Px, h.Py, h.Pz};
+        const double d[3] = {h.dx, h.dy, h.dz};
+        for (int a = 0; a < 3 && why.empty(); ++a) {
+            const bool sp = h.method == DEMAG_METHOD_SP;
+            const int nmax = sp && a == 2 ? kMaxSPZ : kMaxN;
+            if (n[a] < 1 || n[a] > nmax || !(d[a] > 0) || !isfinite(d[a])) why = "bad grid sizes or cell edges";
+            else if (n[a] == 1 && P[a] == 1) continue;
+            else if (P[a] > (sp && a == 2 ? 2 * kMaxSPZ : kMaxP) || P[a] < (sp ? 2 * n[a] : 2 * n[a] - 1) ||
+                     !(is_pow2(P[a]) || (!sp && is_smooth_even(P[a]))))
+                why = "bad padded lengths";
+        }
+        if (why.empty()) {
+            const int Kx = h.Px == 1 ? 1 : h.Px / 2 + 1;
+            const uint64_t want = (uint64_t)h.ntab * (uint64_t)(h.Pz / 2 + 1) * (uint64_t)(h.Py / 2 + 1) * (uint64_t)Kx;
+            const size_t bytes = (size_t)want * (h.prec == DEMAG_F32 ? sizeof(float) : sizeof(double));
+            if (h.count != want) {
+                why = "table size does not match the sizes";
+            } else {
+                buf.resize(bytes);
+                if (fread(buf.data(), 1, bytes, f) != bytes || fgetc(f) != EOF) why = "truncated or oversized file";
+                else if (fnv1a64(buf.data(), bytes) != h.checksum) why = "checksum mismatch";
+            }
+        }
+    }
+    fclose(f);
+    if (!why.empty()) return fail(DEMAG_ERR_INVALID_ARG, std::string(path) + ": " + why);
+    const int P[3] = {h.Px, h.Py, h.Pz};
+    demag_plan_t p = nullptr;
+    demag_status s = create_plan(h.nx, h.ny, h.nz, h.dx, h.dy, h.dz, (demag_prec)h.prec, P, h.method, &p);
+    if (s != DEMAG_OK) return s;
+    void *dst = h.prec == DEMAG_F32 ? (void *)p->nhat32 : (void *)p->nhat64;
+    cudaError_t e = cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        demag_plan_destroy(p);
+        return fail(DEMAG_ERR_CUDA, std::string("spectrum upload: ") + cudaGetErrorString(e));
+    }
+    p->imag_max = h.imag_max;
+    p->setup_done = true;
+    *out = p;
+    return DEMAG_OK;
+}
+
 demag_status demag_plan_info(demag_plan_t p, demag_info *info)
 {
     if (!p || !info) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
@@ -1101,6 +1221,7 @@ demag_status demag_plan_info(demag_plan_t p, demag_info *info)
     info->launches_per_field = p->method == DEMAG_METHOD_SP ? 6 : 3 + 2 * (p->Py > 1);
     info->tensor_imag_max = p->imag_max;
     info->method = p->method;
+    info->dx = p->dx; info->dy = p->dy; info->dz = p->dz;
     return DEMAG_OK;
 }
 

@@ -198,6 +198,30 @@ class Plan:
         B.demag_check_pipeline(self.handle)
 
     # ------------------------------------------------------------------ timing
+    def save(self, path):
+        """Write the set-up tensor spectrum (and sizes) to a file (demag_plan_save)."""
+        B.demag_plan_save(self.handle, path)
+
+    @classmethod
+    def load(cls, path, device=None):
+        """A ready plan from a file written by save(): no tensor setup runs."""
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdemag needs a CUDA device; there is no CPU path")
+        self = cls.__new__(cls)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.handle = None
+        with torch.cuda.device(self.device):
+            self.handle = B.demag_plan_load(path)
+        info = self.info()
+        self.n = (info["nx"], info["ny"], info["nz"])
+        self.d = (info["dx"], info["dy"], info["dz"])
+        self.prec = "f32" if info["prec"] == B.DEMAG_F32 else "f64"
+        self.method = "sp" if info["method"] == B.DEMAG_METHOD_SP else "dm"
+        self.dtype = torch.float32 if self.prec == "f32" else torch.float64
+        self.shape = (3, self.n[2], self.n[1], self.n[0])
+        return self
+
     def set_graphs(self, enable: bool = True):
         """Replay each distinct call as one captured CUDA graph (see demag_set_graphs)."""
         B.demag_set_graphs(self.handle, enable)

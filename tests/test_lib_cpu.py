@@ -134,6 +134,66 @@ def test_padded_lengths_rules(lib):
     assert e.value.name == "DEMAG_ERR_INVALID_ARG"
 
 
+def _spec_file(path, *, magic=b"DMGSPEC\0", version=1, method=0, prec=0, n=(4, 3, 2), P=(8, 8, 4), ntab=6,
+               d=(1e-9, 1e-9, 1e-9), count=None, payload=None, checksum=None, extra=b""):
+    """A tensor-spectrum file in the library's format (header + FP32 table)."""
+    import struct
+    kx = P[0] // 2 + 1
+    want = ntab * (P[2] // 2 + 1) * (P[1] // 2 + 1) * kx
+    if payload is None:
+        payload = struct.pack(f"<{want}f", *[0.25 * (i % 7) for i in range(want)])
+
+    def fnv(b):
+        h = 1469598103934665603
+        for c in b:
+            h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+        return h
+    hdr = struct.pack("<8s10i3dd", magic, version, method, prec, *n, *P, ntab, *d, 0.0)
+    hdr += b"\0" * ((-len(hdr)) % 8)
+    hdr += struct.pack("<QQ", want if count is None else count, fnv(payload) if checksum is None else checksum)
+    with open(path, "wb") as f:
+        f.write(hdr + payload + extra)
+
+
+def test_spectrum_files_are_validated_before_any_device_call(lib, tmp_path):
+    """demag_plan_load checks magic, version, sizes, padded lengths, table size
+    and checksum on the host; a file that passes reaches the device step
+    (here: no CUDA device)."""
+    from paper_1204_4302_gb300 import binding
+    good = tmp_path / "good.spec"
+    _spec_file(good)
+    try:
+        h = binding.demag_plan_load(str(good))
+    except binding.DemagError as e:
+        assert e.name == "DEMAG_ERR_CUDA", e      # every check passed; no device here
+    else:
+        binding.demag_plan_destroy(h)
+    bad = {
+        "missing": None,
+        "magic": dict(magic=b"NOTSPEC\0"),
+        "version": dict(version=2),
+        "method": dict(method=5),
+        "ntab": dict(ntab=3),
+        "size": dict(n=(600, 3, 2)),
+        "padding": dict(P=(6, 8, 4)),            # below 2n - 1 for nx = 4
+        "odd padding": dict(P=(9, 8, 4)),
+        "count": dict(count=12345),
+        "checksum": dict(checksum=1),
+        "trailing": dict(extra=b"x"),
+        "edge": dict(d=(0.0, 1e-9, 1e-9)),
+    }
+    for name, kw in bad.items():
+        path = tmp_path / f"{name.replace(' ', '_')}.spec"
+        if kw is not None:
+            _spec_file(path, **kw)
+        with pytest.raises(binding.DemagError) as e:
+            binding.demag_plan_load(str(path))
+        assert e.value.name == "DEMAG_ERR_INVALID_ARG", name
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_save(None, str(tmp_path / "x.spec"))
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+
+
 def test_sp_plan_arguments_are_checked_before_any_device_call(lib):
     """Scalar-potential plans: padding must be a power of two >= 2n (not 2n - 1),
     z is built up to 256 cells, and the usual size and edge checks apply."""
