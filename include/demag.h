@@ -96,6 +96,12 @@ typedef struct {
 demag_status demag_plan_save(demag_plan_t plan, const char *path);
 demag_status demag_plan_load(const char *path, demag_plan_t *out);
 
+/* Test hook for the error paths: with n >= 1 the n-th next device allocation
+ * made by plan creation, tensor setup, the host-buffer entry points or the
+ * autotuner fails as if the device were out of memory (the call returns
+ * DEMAG_ERR_OOM and frees what it had allocated); 0 disarms it. */
+void demag_debug_fail_alloc(long n);
+
 /* Sizes of a plan, as chosen at creation. */
 typedef struct {
     int nx, ny, nz;          /* physical grid */

@@ -16,6 +16,7 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,24 @@
 using demag::Passes;
 
 namespace {
+
+// Allocation hook for tests of the error paths (demag_debug_fail_alloc):
+// when armed with n, the n-th next device allocation of the plan code fails
+// as if the device were out of memory.
+std::atomic<long> g_fail_alloc{0};
+
+template <typename P>
+cudaError_t dmalloc(P **ptr, size_t bytes)
+{
+    long n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void **>(ptr), bytes);
+}
 
 thread_local std::string g_err;
 
@@ -629,38 +648,38 @@ demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz
                     std::string(what) + ": " + cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&p->S1, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S1");
+    if ((e = dmalloc(&p->S1, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S1");
     if (p->Py > 1) {
-        if ((e = cudaMalloc(&p->S2, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S2");
+        if ((e = dmalloc(&p->S2, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc S2");
     } else {
         p->S2 = p->S1;
     }
     if (prec == DEMAG_F32) {
-        if ((e = cudaMalloc(&p->nhat32, ntab * plane * sizeof(float))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
+        if ((e = dmalloc(&p->nhat32, ntab * plane * sizeof(float))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
     } else {
-        if ((e = cudaMalloc(&p->nhat64, ntab * plane * sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
+        if ((e = dmalloc(&p->nhat64, ntab * plane * sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
     }
-    if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc partials");
-    if ((e = cudaMalloc(&p->e_dev, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc energy");
+    if ((e = dmalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc partials");
+    if ((e = dmalloc(&p->e_dev, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc energy");
     for (int a = 0; a < 3; ++a) {
         const auto t64 = twiddles<double2>(P[a]);
-        if ((e = cudaMalloc(&p->tw64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
+        if ((e = dmalloc(&p->tw64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
         if ((e = cudaMemcpy(p->tw64[a], t64.data(), sizeof(double2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
             return cleanup_fail(e, "twiddle upload");
         if (prec == DEMAG_F32) {
             const auto t32 = twiddles<float2>(P[a]);
-            if ((e = cudaMalloc(&p->tw32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
+            if ((e = dmalloc(&p->tw32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc twiddles");
             if ((e = cudaMemcpy(p->tw32[a], t32.data(), sizeof(float2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cleanup_fail(e, "twiddle upload");
         }
         if (sp) {  // exp(-pi i k / P): the half-cell shift of the node offsets
             const auto h64 = twiddles<double2>(2 * P[a]);
-            if ((e = cudaMalloc(&p->ph64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc phases");
+            if ((e = dmalloc(&p->ph64[a], sizeof(double2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc phases");
             if ((e = cudaMemcpy(p->ph64[a], h64.data(), sizeof(double2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cleanup_fail(e, "phase upload");
             if (prec == DEMAG_F32) {
                 const auto h32 = twiddles<float2>(2 * P[a]);
-                if ((e = cudaMalloc(&p->ph32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc phases");
+                if ((e = dmalloc(&p->ph32[a], sizeof(float2) * P[a])) != cudaSuccess) return cleanup_fail(e, "cudaMalloc phases");
                 if ((e = cudaMemcpy(p->ph32[a], h32.data(), sizeof(float2) * P[a], cudaMemcpyHostToDevice)) != cudaSuccess)
                     return cleanup_fail(e, "phase upload");
             }
@@ -885,13 +904,13 @@ demag_status sp_setup(demag_plan *p, cudaStream_t st)
             return done(rs);                                                                   \
         }                                                                                      \
     } while (0)
-    SETUP_CUDA(cudaMalloc(&oct, sizeof(double) * 3 * (size_t)nx * ny * nz));
-    SETUP_CUDA(cudaMalloc(&W, sizeof(double) * (size_t)Px * Py * Pz));
-    SETUP_CUDA(cudaMalloc(&St, sizeof(double2) * (size_t)Pz * Py * Kxp));
-    SETUP_CUDA(cudaMalloc(&imag, sizeof(unsigned long long)));
+    SETUP_CUDA(dmalloc(&oct, sizeof(double) * 3 * (size_t)nx * ny * nz));
+    SETUP_CUDA(dmalloc(&W, sizeof(double) * (size_t)Px * Py * Pz));
+    SETUP_CUDA(dmalloc(&St, sizeof(double2) * (size_t)Pz * Py * Kxp));
+    SETUP_CUDA(dmalloc(&imag, sizeof(unsigned long long)));
     SETUP_CUDA(cudaMemsetAsync(imag, 0, sizeof(unsigned long long), st));
     if (!t64) {
-        SETUP_CUDA(cudaMalloc(&t64, sizeof(double) * 3 * plane));
+        SETUP_CUDA(dmalloc(&t64, sizeof(double) * 3 * plane));
         own64 = true;
     }
     SETUP_CUDA(demag::sp_octant(oct, nx, ny, nz, p->dx, p->dy, p->dz, st));
@@ -950,13 +969,13 @@ demag_status demag_tensor_setup(demag_plan_t p, void *stream)
             return done(rs);                                                                   \
         }                                                                                      \
     } while (0)
-    SETUP_CUDA(cudaMalloc(&oct, sizeof(double) * 6 * (size_t)nx * ny * nz));
-    SETUP_CUDA(cudaMalloc(&W, sizeof(double) * (size_t)Px * Py * Pz));
-    SETUP_CUDA(cudaMalloc(&St, sizeof(double2) * (size_t)Pz * Py * Kxp));
-    SETUP_CUDA(cudaMalloc(&imag, sizeof(unsigned long long)));
+    SETUP_CUDA(dmalloc(&oct, sizeof(double) * 6 * (size_t)nx * ny * nz));
+    SETUP_CUDA(dmalloc(&W, sizeof(double) * (size_t)Px * Py * Pz));
+    SETUP_CUDA(dmalloc(&St, sizeof(double2) * (size_t)Pz * Py * Kxp));
+    SETUP_CUDA(dmalloc(&imag, sizeof(unsigned long long)));
     SETUP_CUDA(cudaMemsetAsync(imag, 0, sizeof(unsigned long long), st));
     if (!nh64) {
-        SETUP_CUDA(cudaMalloc(&nh64, sizeof(double) * 6 * plane));
+        SETUP_CUDA(dmalloc(&nh64, sizeof(double) * 6 * plane));
         own64 = true;
     }
     SETUP_CUDA(demag::tensor_octant(oct, nx, ny, nz, p->dx, p->dy, p->dz, st));
@@ -1042,8 +1061,8 @@ demag_status demag_field_host(demag_plan_t p, const void *M_host, void *H_host, 
     DeviceGuard g(p->device);
     if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
     const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
-    if (!p->dM) DEMAG_CUDA(cudaMalloc(&p->dM, bytes));
-    if (!p->dH) DEMAG_CUDA(cudaMalloc(&p->dH, bytes));
+    if (!p->dM) DEMAG_CUDA(dmalloc(&p->dM, bytes));
+    if (!p->dH) DEMAG_CUDA(dmalloc(&p->dH, bytes));
     cudaStream_t st = (cudaStream_t)stream;
     DEMAG_CUDA(cudaMemcpyAsync(p->dM, M_host, bytes, cudaMemcpyHostToDevice, st));
     demag_status s = run_job(p, plain_job(p->dM, p->dH, nullptr), stream);
@@ -1080,8 +1099,8 @@ demag_status demag_field_host_async(demag_plan_t p, const void *M_host, void *H_
     const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
     if (!p->async_ready) {
         for (int k = 0; k < 2; ++k) {
-            DEMAG_CUDA(cudaMalloc(&p->aM[k], bytes));
-            DEMAG_CUDA(cudaMalloc(&p->aH[k], bytes));
+            DEMAG_CUDA(dmalloc(&p->aM[k], bytes));
+            DEMAG_CUDA(dmalloc(&p->aH[k], bytes));
             DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming));
             DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_done[k], cudaEventDisableTiming));
             DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming));
@@ -1119,6 +1138,8 @@ demag_status demag_host_wait(demag_plan_t p)
     DEMAG_CUDA(cudaStreamSynchronize(p->s_out));
     return DEMAG_OK;
 }
+
+void demag_debug_fail_alloc(long n) { g_fail_alloc.store(n > 0 ? n : 0); }
 
 demag_status demag_plan_save(demag_plan_t p, const char *path)
 {
@@ -1308,8 +1329,8 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     if (p->Py == 512 || p->Py == 1024) ys.push_back(3);  // forward pass by the TMA pipeline
     const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
     void *M = nullptr, *H = nullptr;
-    DEMAG_CUDA(cudaMalloc(&M, bytes));
-    if (cudaMalloc(&H, bytes) != cudaSuccess) {
+    DEMAG_CUDA(dmalloc(&M, bytes));
+    if (dmalloc(&H, bytes) != cudaSuccess) {
         cudaFree(M);
         return fail(DEMAG_ERR_OOM, "autotune buffers");
     }
