@@ -236,7 +236,14 @@ demag_status demag_field_host(demag_plan_t plan, const void *M_host, void *H_hos
  * and two output fields) are allocated at the first call. */
 demag_status demag_field_host_async(demag_plan_t plan, const void *M_host, void *H_host, void *stream);
 
-/* Waits for every upload and download issued by demag_field_host_async. */
+/* Same, with the energy E = -(mu0/2) V sum M.H of each call written to
+ * *E_host (a host double, page-locked for the copies to overlap), valid after
+ * demag_host_wait() like H_host. E_host NULL: as demag_field_host_async. */
+demag_status demag_field_energy_host_async(demag_plan_t plan, const void *M_host, void *H_host, double *E_host,
+                                           void *stream);
+
+/* Waits for every upload and download issued by demag_field_host_async and
+ * demag_field_energy_host_async. */
 demag_status demag_host_wait(demag_plan_t plan);
 
 /* Plan sizes and memory. */

@@ -785,6 +785,7 @@ void demag_plan_destroy(demag_plan_t p)
         for (int k = 0; k < 2; ++k) {
             cudaFree(p->aM[k]);
             cudaFree(p->aH[k]);
+            cudaFree(p->aE[k]);
             cudaEventDestroy(p->ev_in[k]);
             cudaEventDestroy(p->ev_done[k]);
             cudaEventDestroy(p->ev_out[k]);
@@ -1091,6 +1092,12 @@ demag_status demag_energy_grad(demag_plan_t p, const void *m, const void *w, dou
 
 demag_status demag_field_host_async(demag_plan_t p, const void *M_host, void *H_host, void *stream)
 {
+    return demag_field_energy_host_async(p, M_host, H_host, nullptr, stream);
+}
+
+demag_status demag_field_energy_host_async(demag_plan_t p, const void *M_host, void *H_host, double *E_host,
+                                           void *stream)
+{
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (!M_host || !H_host) return fail(DEMAG_ERR_INVALID_ARG, "host buffers must not be NULL");
     if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
@@ -1101,6 +1108,7 @@ demag_status demag_field_host_async(demag_plan_t p, const void *M_host, void *H_
         for (int k = 0; k < 2; ++k) {
             DEMAG_CUDA(dmalloc(&p->aM[k], bytes));
             DEMAG_CUDA(dmalloc(&p->aH[k], bytes));
+            DEMAG_CUDA(dmalloc(&p->aE[k], sizeof(double)));
             DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming));
             DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_done[k], cudaEventDisableTiming));
             DEMAG_CUDA(cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming));
@@ -1119,11 +1127,12 @@ demag_status demag_field_host_async(demag_plan_t p, const void *M_host, void *H_
     DEMAG_CUDA(cudaMemcpyAsync(p->aM[k], M_host, bytes, cudaMemcpyHostToDevice, p->s_in));
     DEMAG_CUDA(cudaEventRecord(p->ev_in[k], p->s_in));
     DEMAG_CUDA(cudaStreamWaitEvent(st, p->ev_in[k], 0));
-    demag_status s = run_job(p, plain_job(p->aM[k], p->aH[k], nullptr), stream);
+    demag_status s = run_job(p, plain_job(p->aM[k], p->aH[k], E_host ? p->aE[k] : nullptr), stream);
     if (s != DEMAG_OK) return s;
     DEMAG_CUDA(cudaEventRecord(p->ev_done[k], st));
     DEMAG_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_done[k], 0));
     DEMAG_CUDA(cudaMemcpyAsync(H_host, p->aH[k], bytes, cudaMemcpyDeviceToHost, p->s_out));
+    if (E_host) DEMAG_CUDA(cudaMemcpyAsync(E_host, p->aE[k], sizeof(double), cudaMemcpyDeviceToHost, p->s_out));
     DEMAG_CUDA(cudaEventRecord(p->ev_out[k], p->s_out));
     p->out_recorded[k] = true;
     return DEMAG_OK;

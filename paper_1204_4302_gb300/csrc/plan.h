@@ -184,6 +184,7 @@ struct demag_plan {
     void *dM, *dH;
     // asynchronous host entry point: two device slots, copy streams, events
     void *aM[2], *aH[2];
+    double *aE[2];  // per-slot energy of the streamed host entry
     cudaStream_t s_in, s_out;
     cudaEvent_t ev_in[2], ev_done[2], ev_out[2];
     bool out_recorded[2];

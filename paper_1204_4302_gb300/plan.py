@@ -173,6 +173,17 @@ class Plan:
                 raise ValueError("host buffers must be contiguous CPU tensors of the plan's dtype and shape")
         B.demag_field_host_async(self.handle, M_host.data_ptr(), H_host.data_ptr(), self._stream())
 
+    def field_energy_host_async(self, M_host, H_host, E_host):
+        """As field_host_async, with the energy written to E_host (a pinned
+        float64 CPU tensor of one element) after host_wait()."""
+        for t in (M_host, H_host):
+            if t.device.type != "cpu" or t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors of the plan's dtype and shape")
+        if E_host.device.type != "cpu" or E_host.dtype != torch.float64 or E_host.numel() != 1:
+            raise ValueError("E_host must be a float64 CPU tensor of one element")
+        B.demag_field_energy_host_async(self.handle, M_host.data_ptr(), H_host.data_ptr(), E_host.data_ptr(),
+                                        self._stream())
+
     def host_wait(self):
         B.demag_host_wait(self.handle)
 

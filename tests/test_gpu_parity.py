@@ -221,4 +221,13 @@ def test_host_entry_point_matches_device():
     plan.host_wait()
     for m, h in zip(Ms, Hs):
         assert torch.equal(plan.field(m.cuda()).cpu(), h)
+    # streamed with the energy: H and E of every state, as on the device
+    Es = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in Ms]
+    for m, h, e in zip(Ms, Hs, Es):
+        plan.field_energy_host_async(m, h, e)
+    plan.host_wait()
+    for m, h, e in zip(Ms, Hs, Es):
+        Hd, Ed = plan.field_energy(m.cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(Hd.cpu(), h) and Ed.item() == e.item()
     plan.close()
