@@ -94,6 +94,11 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- columns
@@ -866,8 +871,11 @@ k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ o
     k_x_fwd2_tile<T, L, PIN, false>(a, nrows, nvalid, out, out_rs, twx, blockIdx.x, smraw);
 }
 
-// Complex-to-real along x (see k_x_inv), two stages, XOut epilogue.
-template <typename T, int L, bool CG, bool P1 = false>
+// Complex-to-real along x (see k_x_inv), two stages, XOut epilogue. MP: the
+// energy's reference field rows (o.Mref, nvalid a multiple of 4 and rows
+// 16-byte aligned) are copied to shared memory with cp.async at the start, so
+// their loads overlap the transform instead of following it.
+template <typename T, int L, bool CG, bool P1 = false, bool MP = false>
 __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
 {
@@ -875,7 +883,17 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
     using S = XShape<T, L>;
     constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, TR = S::TR, RS = S::RS;
     C *sm = reinterpret_cast<C *>(smraw);
+    T *smM = reinterpret_cast<T *>(sm + TR * RS);  // MP: [TR][L] reference rows
     const int row0 = tile * TR;
+    if constexpr (MP) {
+        const int chunks = nvalid / (16 / (int)sizeof(T));  // 16-byte pieces per row
+        for (int i = threadIdx.x; i < TR * chunks; i += NT) {
+            const int rr = i / chunks, c = i - rr * chunks, row = row0 + rr;
+            if (row < nrows)
+                cp_async16(&smM[rr * L + c * (16 / (int)sizeof(T))],
+                           o.Mref + (int64_t)row * o.out_rs + c * (16 / (int)sizeof(T)));
+        }
+    }
     // stage 1: thread (row, j1) builds Z[k], k = j1 + r R2, from X[k] and X[L-k]
     if (threadIdx.x < TR * R2) {
         const int rr = threadIdx.x / R2, j1 = threadIdx.x % R2, row = row0 + rr;
@@ -900,6 +918,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
 #pragma unroll
         for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
     }
+    if constexpr (MP) cp_async_wait_all();
     __syncthreads();
     T acc = 0;  // per-thread sum of a few dozen terms; blocks reduce in FP64
     if (threadIdx.x < TR * R1) {
@@ -926,7 +945,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
                     const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
                     const int64_t idx = (int64_t)row * o.out_rs + x;
                     if (o.out) o.out[idx] = hv[u] * oscale * w;
-                    if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[u];
+                    if (o.partials) acc += o.mscale * w * (MP ? smM[rr * L + x] : o.Mref[idx]) * hv[u];
                 }
             }
         }
@@ -936,13 +955,13 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
 
 // P1: one more output pair per row (x = L, L + 1, ...: rows of nx + 1 >= L
 // values, the node potential of the scalar-potential method).
-template <typename T, int L, bool P1 = false>
+template <typename T, int L, bool P1 = false, bool MP = false>
 __global__ void __launch_bounds__(Tile2<T>::NT, (L >= 512 ? Occ<T, 2 * L>::MIN_CTAS : Occ<T, L>::MIN_CTAS))
 k_x_inv2(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    k_x_inv2_tile<T, L, false, P1>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
+    k_x_inv2_tile<T, L, false, P1, MP>(in, in_rs, nrows, nvalid, o, twx, blockIdx.x, smraw);
 }
 
 }  // namespace demag

@@ -375,7 +375,13 @@ cudaError_t Passes<T>::x_inv(int L, const C *in, int64_t in_rs, int nrows, int n
         using S = XShape<T, LL>;                                                               \
         const size_t sm = (size_t)S::TR * S::RS * sizeof(C);                                   \
         const int grid = (nrows + S::TR - 1) / S::TR;                                          \
-        if (nvalid <= LL) k_x_inv2<T, LL><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx); \
+        if (o.partials && o.Mref && nvalid <= LL && nvalid % (16 / sizeof(T)) == 0 &&          \
+            o.out_rs % (16 / sizeof(T)) == 0 && ((uintptr_t)o.Mref & 15) == 0) {               \
+            const size_t smp = sm + (size_t)S::TR * LL * sizeof(T);                            \
+            cudaError_t e = allow_smem<k_x_inv2<T, LL, false, true>>(smp);                     \
+            if (e != cudaSuccess) return e;                                                    \
+            k_x_inv2<T, LL, false, true><<<grid, S::NT, smp, st>>>(in, in_rs, nrows, nvalid, o, twx); \
+        } else if (nvalid <= LL) k_x_inv2<T, LL><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx); \
         else if (nvalid == LL + 1) k_x_inv2<T, LL, true><<<grid, S::NT, sm, st>>>(in, in_rs, nrows, nvalid, o, twx); \
         else return cudaErrorInvalidValue;                                                     \
         return cudaGetLastError();                                                             \
