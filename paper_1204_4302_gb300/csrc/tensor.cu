@@ -330,11 +330,13 @@ __global__ void k_extract(const double2 *__restrict__ S, int comp, int Kx, int P
     atomicMax(imag_max, (unsigned long long)__double_as_longlong(local));
 }
 
-__global__ void k_energy_finalize(const double *__restrict__ partials, int n, double factor,
-                                  double *__restrict__ E)
+constexpr int kFinalizeThreads = 1024;  // FP64 adds are slow: many independent chains per SM
+
+__global__ void __launch_bounds__(kFinalizeThreads) k_energy_finalize(const double *__restrict__ partials, int n,
+                                                                      double factor, double *__restrict__ E)
 {
     // one block; Neumaier-compensated sums per thread, then a tree of pairs
-    __shared__ double ss[256], sc[256];
+    __shared__ double ss[kFinalizeThreads], sc[kFinalizeThreads];
     double s = 0.0, c = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double v = partials[i];
@@ -618,7 +620,7 @@ cudaError_t sp_extract(const double2 *S, int comp, int Px, int Py, int Pz, int K
 
 cudaError_t energy_finalize(const double *partials, int n, double factor, double *E, cudaStream_t st)
 {
-    k_energy_finalize<<<1, 256, 0, st>>>(partials, n, factor, E);
+    k_energy_finalize<<<1, kFinalizeThreads, 0, st>>>(partials, n, factor, E);
     return cudaGetLastError();
 }
 
