@@ -208,3 +208,44 @@ def test_batch_with_mixed_radix_padding(pad, tmp_path, monkeypatch):
         Eref = oracle.energy(m, Href, d)
         assert abs(e - Eref) <= 10 * TOL["f32"] * abs(Eref)
     b.close()
+
+
+# Every stage radix the mixed-radix passes instantiate (rows and columns: 2..16;
+# the z pass: 5..32), each reached by the plan of some padded length here.
+RADIX_CASES = [
+    ((9, 9, 20), (18, 18, 40)),       # x 9 | y 6.3 | z 8.5
+    ((10, 10, 18), (20, 20, 36)),     # x 10 | y 5.4 | z 6.6
+    ((14, 14, 21), (28, 28, 42)),     # x 14 | y 7.4 | z 7.6
+    ((20, 27, 27), (40, 54, 54)),     # x 5.4 | y 9.6 | z 9.6
+    ((25, 25, 25), (50, 50, 50)),     # x 5.5 | y 10.5 | z 10.5
+    ((42, 42, 42), (84, 84, 84)),     # x 7.6 | y 12.7 | z 12.7
+    ((49, 49, 49), (98, 98, 98)),     # x 7.7 | y 14.7 | z 14.7
+    ((75, 80, 6), (150, 160, 12)),    # x 15.5 | y 16.10 | z 12
+    ((81, 81, 4), (162, 162, 8)),     # x 9.9 | y 9.9.2
+    ((20, 20, 4), (40, 40, 8)),       # x 5.4 | y 8.5
+    ((4, 4, 75), (8, 8, 150)),        # z 15.10
+    ((4, 4, 80), (8, 8, 160)),        # z 16.10
+    ((4, 4, 81), (8, 8, 162)),        # z 18.9
+    ((4, 4, 100), (8, 8, 200)),       # z 20.10
+    ((4, 4, 147), (8, 8, 294)),       # z 21.14
+    ((4, 4, 192), (8, 8, 384)),       # z 24.16
+    ((4, 4, 125), (8, 8, 250)),       # z 25.10
+    ((4, 4, 243), (8, 8, 486)),       # z 27.18
+    ((4, 4, 196), (8, 8, 392)),       # z 28.14
+    ((4, 4, 315), (8, 8, 630)),       # z 30.21
+    ((4, 4, 320), (8, 8, 640)),       # z 32.20
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,pad", RADIX_CASES)
+def test_every_stage_radix_matches_oracle(n, pad, prec):
+    d = (1e-9, 1.1e-9, 0.9e-9)
+    M = 8e5 * inputs.random_unit(n, seed=sum(pad))
+    Href = oracle.field_fft(M, d)
+    plan = _plan(n, d, prec, pad)
+    assert (plan.info()["px"], plan.info()["py"], plan.info()["pz"]) == pad
+    H = plan.field(torch.tensor(M, dtype=DT[prec], device="cuda"))
+    torch.cuda.synchronize()
+    assert _relmax(H.double().cpu().numpy(), Href) <= TOL[prec]
+    plan.close()
