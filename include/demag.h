@@ -349,6 +349,18 @@ demag_status demag_batch_info(demag_batch_t batch, int *mode, int *persistent_ok
 demag_status demag_batch_autotune(demag_batch_t batch, int use_cache, double *ms_persistent,
                                   double *ms_branches, void *stream);
 
+/* Padding autotuner of a batch created with power-of-two or smooth padding
+ * (demag_batch_create[_ex] with pad_mode 0 or 1): runs demag_batch_autotune,
+ * builds and autotunes the same states with the other padding, and keeps the
+ * faster of the two (rebuilding the batch's plans in place when the other
+ * wins; the handle stays valid, graphs are rebuilt at the next call, and a
+ * timeout set with demag_batch_set_timeout returns to its default).
+ * ms_pow2 / ms_smooth (may be NULL) receive the best time per call of each.
+ * DEMAG_ERR_UNSUPPORTED for a batch created with DEMAG_PAD_TUNED.
+ * Synchronises. */
+demag_status demag_batch_autotune_padding(demag_batch_t batch, int use_cache, double *ms_pow2, double *ms_smooth,
+                                          void *stream);
+
 /* Graph launches made by this batch. */
 long demag_batch_launch_count(demag_batch_t batch);
 

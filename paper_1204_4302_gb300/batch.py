@@ -51,6 +51,11 @@ class Batch:
         (ms per call persistent, ms per call branches)."""
         return B.demag_batch_autotune(self.handle, use_cache, torch.cuda.current_stream(self.device).cuda_stream)
 
+    def autotune_padding(self, use_cache: bool = True):
+        """Keep the faster of power-of-two and smooth padding (rebuilding the
+        plans when needed); returns (ms per call power-of-two, smooth)."""
+        return B.demag_batch_autotune_padding(self.handle, use_cache, torch.cuda.current_stream(self.device).cuda_stream)
+
     def set_mode(self, mode: int):
         B.demag_batch_set_mode(self.handle, mode)
 

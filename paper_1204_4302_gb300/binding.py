@@ -42,6 +42,7 @@ EXPORTS = [
     "demag_energy_noalloc",
     "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding", "demag_padded_lengths", "demag_set_graphs",
     "demag_plan_save", "demag_plan_load", "demag_debug_fail_alloc", "demag_field_energy_host_async",
+    "demag_batch_autotune_padding",
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
@@ -108,6 +109,7 @@ def load(path: str | Path | None = None):
         "demag_plan_info": (S, [P, POINTER(demag_info)]),
         "demag_set_timing": (S, [P, I]),
         "demag_set_graphs": (S, [P, I]),
+        "demag_batch_autotune_padding": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
         "demag_field_energy_host_async": (S, [P, P, P, P, P]),
         "demag_debug_fail_alloc": (None, [ctypes.c_long]),
         "demag_plan_save": (S, [P, ctypes.c_char_p]),
@@ -354,6 +356,14 @@ def demag_debug_fail_alloc(n):
 def demag_field_energy_host_async(plan, M_host, H_host, E_host, stream=0):
     _check(load().demag_field_energy_host_async(_p(plan), _p(M_host), _p(H_host), _p(E_host), _p(stream)),
            "demag_field_energy_host_async")
+
+
+def demag_batch_autotune_padding(batch, use_cache=True, stream=0):
+    """Keep the faster of power-of-two and smooth padding; returns (ms_pow2, ms_smooth)."""
+    a, b = c_double(), c_double()
+    _check(load().demag_batch_autotune_padding(_p(batch), 1 if use_cache else 0, ctypes.byref(a), ctypes.byref(b),
+                                               _p(stream)), "demag_batch_autotune_padding")
+    return a.value, b.value
 
 
 def demag_set_graphs(plan, enable=True):

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fft2.cuh"
@@ -318,6 +319,10 @@ struct demag_batch {
     std::vector<const void *> curM;
     std::vector<void *> curH;
     long launches;
+    // creation inputs (to rebuild the plans with another padding)
+    std::vector<int> dims;
+    std::vector<double> cells;
+    int pad_mode;
 };
 
 namespace {
@@ -572,6 +577,9 @@ demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, 
     demag_batch *b = new demag_batch();
     b->n = n;
     b->prec = prec;
+    b->dims.assign(dims, dims + 3 * n);
+    b->cells.assign(cells, cells + 3 * n);
+    b->pad_mode = opt ? opt->pad_mode : DEMAG_PAD_POW2;
     b->timeout_cycles = 4000000000LL;  // ~2 s at 2 GHz; normal waits take microseconds
     if (cudaGetDevice(&b->device) != cudaSuccess) {
         cudaGetLastError();
@@ -750,6 +758,36 @@ demag_status demag_batch_autotune(demag_batch_t b, int use_cache, double *ms_per
     if (ms_persistent) *ms_persistent = b->persistent_ok ? t[0] : -1.0;
     if (ms_branches) *ms_branches = t[1];
     return demag_batch_status(b, stream);
+}
+
+demag_status demag_batch_autotune_padding(demag_batch_t b, int use_cache, double *ms_pow2, double *ms_smooth,
+                                          void *stream)
+{
+    if (!b) return bfail(DEMAG_ERR_INVALID_ARG, "batch is NULL");
+    if (b->pad_mode != DEMAG_PAD_POW2 && b->pad_mode != DEMAG_PAD_SMOOTH)
+        return bfail(DEMAG_ERR_UNSUPPORTED, "the batch's padding was chosen per state by timing already");
+    double tp = 0, tb = 0;
+    demag_status s = demag_batch_autotune(b, use_cache, &tp, &tb, stream);
+    if (s != DEMAG_OK) return s;
+    const double t_this = tp >= 0 && tp < tb ? tp : tb;
+    demag_options o;
+    memset(&o, 0, sizeof o);
+    o.pad_mode = b->pad_mode == DEMAG_PAD_POW2 ? DEMAG_PAD_SMOOTH : DEMAG_PAD_POW2;
+    demag_batch_t nb = nullptr;
+    s = demag_batch_create_ex(b->n, b->dims.data(), b->cells.data(), b->prec, &o, &nb);
+    if (s != DEMAG_OK) return s;
+    s = demag_batch_autotune(nb, use_cache, &tp, &tb, stream);
+    if (s != DEMAG_OK) {
+        free_batch(nb);
+        return s;
+    }
+    const double t_other = tp >= 0 && tp < tb ? tp : tb;
+    const bool was_pow2 = b->pad_mode == DEMAG_PAD_POW2;
+    if (ms_pow2) *ms_pow2 = was_pow2 ? t_this : t_other;
+    if (ms_smooth) *ms_smooth = was_pow2 ? t_other : t_this;
+    if (t_other < t_this) std::swap(*b, *nb);  // keep the faster plans; the caller's handle stays valid
+    free_batch(nb);
+    return DEMAG_OK;
 }
 
 void demag_batch_destroy(demag_batch_t b)

@@ -249,3 +249,23 @@ def test_every_stage_radix_matches_oracle(n, pad, prec):
     torch.cuda.synchronize()
     assert _relmax(H.double().cpu().numpy(), Href) <= TOL[prec]
     plan.close()
+
+
+def test_batch_padding_autotuner_keeps_the_faster_padding():
+    """demag_batch_autotune_padding times power-of-two and smooth padding of the
+    same states and keeps the faster; the fields stay the oracle's."""
+    from paper_1204_4302_gb300.batch import Batch
+    dims = [(33, 20, 9), (40, 36, 12), (17, 65, 5), (24, 24, 24)]
+    cells = [(3e-9, 3e-9, 3e-9)] * len(dims)
+    b = Batch(dims, cells)
+    t_pow2, t_smooth = b.autotune_padding(use_cache=False)
+    assert t_pow2 > 0 and t_smooth > 0
+    Ms = [8e5 * inputs.random_unit(n, seed=40 + i) for i, n in enumerate(dims)]
+    for _ in range(2):                    # the first call after a rebuild builds the graphs
+        Hs, E = b.field([torch.tensor(m, dtype=torch.float32, device="cuda") for m in Ms], energies=True)
+    torch.cuda.synchronize()
+    for m, h, e, d in zip(Ms, Hs, E.cpu().numpy(), cells):
+        Href = oracle.field_fft(m, d)
+        assert _relmax(h.double().cpu().numpy(), Href) <= TOL["f32"]
+        assert abs(e - oracle.energy(m, Href, d)) <= 10 * TOL["f32"] * abs(oracle.energy(m, Href, d))
+    b.close()
