@@ -152,8 +152,11 @@ demag_status demag_plan_create_ex(int nx, int ny, int nz, double dx, double dy, 
  * instead of three; the field is an approximation of the DM field with a
  * finite-difference error (largest at the surfaces).
  * Padded lengths: powers of two >= 2n (node-minus-cell offsets take 2n
- * values); opt (may be NULL) can ask for larger ones. Sizes: nx, ny <= 512,
- * nz <= 256. Same buffers and errors as demag_plan_create_ex.
+ * values); opt (may be NULL) can ask for larger ones, or with pad_mode
+ * DEMAG_PAD_SMOOTH for the smallest even lengths >= 2n with prime factors
+ * 2, 3, 5, 7 (mixed-radix passes; explicit lengths may be either kind;
+ * DEMAG_PAD_TUNED: DEMAG_ERR_UNSUPPORTED). Sizes: nx, ny <= 512, nz <= 256
+ * (padded z <= 512). Same buffers and errors as demag_plan_create_ex.
  * Entry points that accept an SP plan: demag_tensor_setup (computes the
  * kernel spectrum), demag_field, demag_field_energy, demag_energy,
  * demag_field_host(_async), demag_sp_potential, demag_plan_info,

@@ -611,6 +611,14 @@ int sp_pad(int n)
     return p;
 }
 
+// smallest even length >= 2n with prime factors 2, 3, 5, 7
+int sp_smooth_pad(int n)
+{
+    int p = 2 * n;
+    while (!is_smooth_even(p)) p += 2;
+    return p;
+}
+
 // Allocates a plan with padded lengths P for the given method (no launches).
 demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz, demag_prec prec, const int P[3],
                          int method, demag_plan_t *out)
@@ -855,16 +863,21 @@ demag_status demag_plan_create_sp(int nx, int ny, int nz, double dx, double dy, 
     if (prec != DEMAG_F32 && prec != DEMAG_F64) return fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
     if (nx > kMaxN || ny > kMaxN || nz > kMaxSPZ)
         return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential grids are built up to 512 x 512 x 256");
-    int P[3] = {sp_pad(nx), sp_pad(ny), sp_pad(nz)};
     const int n[3] = {nx, ny, nz};
-    if (opt && opt->pad_mode != DEMAG_PAD_POW2)
-        return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential plans use power-of-two padding");
+    if (opt && opt->pad_mode == DEMAG_PAD_TUNED)
+        return fail(DEMAG_ERR_UNSUPPORTED, "scalar-potential plans take power-of-two or smooth padding");
+    if (opt && opt->pad_mode != DEMAG_PAD_POW2 && opt->pad_mode != DEMAG_PAD_SMOOTH)
+        return fail(DEMAG_ERR_INVALID_ARG, "unknown pad_mode");
+    const bool smooth = opt && opt->pad_mode == DEMAG_PAD_SMOOTH;
+    int P[3];
+    for (int a = 0; a < 3; ++a) P[a] = smooth ? sp_smooth_pad(n[a]) : sp_pad(n[a]);
     if (opt) {
         const int req[3] = {opt->px, opt->py, opt->pz};
         for (int a = 0; a < 3; ++a) {
             if (req[a] == 0) continue;
-            if (!is_pow2(req[a]) || req[a] < 2 * n[a])
-                return fail(DEMAG_ERR_INVALID_ARG, "scalar-potential padded lengths must be powers of two >= 2n");
+            if (!(is_pow2(req[a]) || is_smooth_even(req[a])) || req[a] < 2 * n[a])
+                return fail(DEMAG_ERR_INVALID_ARG,
+                            "scalar-potential padded lengths must be >= 2n and powers of two or even products of 2, 3, 5, 7");
             if (req[a] > (a == 2 ? 2 * kMaxSPZ : kMaxP))
                 return fail(DEMAG_ERR_UNSUPPORTED, "padded length above what is built");
             P[a] = req[a];
@@ -1206,7 +1219,7 @@ demag_status demag_plan_load(const char *path, demag_plan_t *out)
             if (n[a] < 1 || n[a] > nmax || !(d[a] > 0) || !isfinite(d[a])) why = "bad grid sizes or cell edges";
             else if (n[a] == 1 && P[a] == 1) continue;
             else if (P[a] > (sp && a == 2 ? 2 * kMaxSPZ : kMaxP) || P[a] < (sp ? 2 * n[a] : 2 * n[a] - 1) ||
-                     !(is_pow2(P[a]) || (!sp && is_smooth_even(P[a]))))
+                     !(is_pow2(P[a]) || is_smooth_even(P[a])))
                 why = "bad padded lengths";
         }
         if (why.empty()) {

@@ -555,4 +555,71 @@ k_gen_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsign
     gen_fft_io<C, true, false, true, kGenMaxRadixZ>(G, F, g, tw, twstride, GenSmemLd<C, false>{F, TCC, L}, st);
 }
 
+// Fused SP z pass (as k_sp_z2) for lengths that are not powers of two: the
+// forward transforms of the three components run as in k_gen_zconv; the
+// product with the kernel tables and the half-cell phase (-i Phi, from the
+// per-axis tables phx, phy, phz) leaves one component in the first TC tile
+// columns; its inverse transform (plan g1, TC columns) stores the nout = nrows
+// + 1 node rows over component 0 (running on into the first row of component
+// 1, cs == nrows * rs: only this CTA reads or writes its columns, and every
+// input was read before the first output is written).
+template <typename T>
+__global__ void __launch_bounds__(kGenThreads)
+k_gen_sp_zconv(typename Cplx<T>::type *__restrict__ S, int ncols, int width, unsigned mw, int64_t ss, int64_t rs,
+               int64_t cs, int nrows, int nout, const T *__restrict__ that, int Py, int Kx,
+               const typename Cplx<T>::type *__restrict__ tw, const typename Cplx<T>::type *__restrict__ phx,
+               const typename Cplx<T>::type *__restrict__ phy, const typename Cplx<T>::type *__restrict__ phz,
+               const __grid_constant__ GenRadix g3, const __grid_constant__ GenRadix g1)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int L = g3.L, TCC = g3.TC, TC = g1.TC, TS = swsize(L * TCC);
+    C *A = reinterpret_cast<C *>(smraw), *B = A + TS;
+    const int f0 = blockIdx.x * TC;
+    auto ld = [&](int row, int cc) {
+        const int comp = cc >= 2 * TC ? 2 : (cc >= TC ? 1 : 0), f = f0 + cc - comp * TC;
+        C v = cmk<C>(0, 0);
+        if (f < ncols && row < nrows) {
+            const int slab = udiv(f, width, mw);
+            v = S[(int64_t)slab * ss + (int64_t)row * rs + (f - slab * width) + comp * cs];
+        }
+        return v;
+    };
+    const GenSmemSt<C, false> none{nullptr, TCC, L};
+    C *F = gen_fft_io<C, false, false, false, kGenMaxRadixZ>(A, B, g3, tw, 1, ld, none);
+    C *G = F == A ? B : A;
+    const int hy = Py / 2 + 1, hz = L / 2 + 1;
+    const int64_t plane = (int64_t)hz * hy * Kx;
+    for (int e = threadIdx.x; e < L * TC; e += blockDim.x) {
+        const int kz = udiv(e, TC, g3.mCols), c = e - kz * TC, f = f0 + c;
+        C p = cmk<C>(0, 0);
+        const C mx = F[sw(kz * TCC + c)], my = F[sw(kz * TCC + TC + c)], mz = F[sw(kz * TCC + 2 * TC + c)];
+        if (f < ncols) {
+            const int ky = udiv(f, width, mw), kx = f - ky * width;
+            const bool fy = ky > Py / 2, fz = kz > L / 2;
+            const int kyf = fy ? Py - ky : ky, kzf = fz ? L - kz : kz;
+            const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
+            const int64_t bq = ((int64_t)kzf * hy + kyf) * Kx + kx;
+            // folds: ky flips T_x and T_z, kz flips T_x and T_y
+            const T tx = sy * sz * __ldg(&that[bq]), ty = sz * __ldg(&that[plane + bq]),
+                    tz = sy * __ldg(&that[2 * plane + bq]);
+            const C pxy = cmul(__ldg(&phx[kx]), __ldg(&phy[ky]));
+            const C ph = cmul(cmk<C>(pxy.y, -pxy.x), __ldg(&phz[kz]));  // -i Phi
+            const C a = cmk<C>(tx * mx.x + ty * my.x + tz * mz.x, tx * mx.y + ty * my.y + tz * mz.y);
+            p = cmul(a, ph);
+        }
+        F[sw(kz * TCC + c)] = p;  // only this thread reads or writes element (kz, c)
+    }
+    __syncthreads();
+    auto ldf = [&](int row, int c) { return F[sw(row * TCC + c)]; };
+    auto st = [&](int row, int c, C v) {
+        const int f = f0 + c;
+        if (f < ncols && row < nout) {
+            const int slab = udiv(f, width, mw);
+            S[(int64_t)slab * ss + (int64_t)row * rs + (f - slab * width)] = v;
+        }
+    };
+    gen_fft_io<C, true, false, true, kGenMaxRadixZ>(G, F, g1, tw, 1, ldf, st);
+}
+
 }  // namespace demag

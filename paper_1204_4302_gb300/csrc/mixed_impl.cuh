@@ -162,4 +162,24 @@ cudaError_t MixedPasses<T>::zconv(int L, C *S, int ncols, int width, int64_t ss,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t MixedPasses<T>::sp_zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+                                     int nrows, int nout, const T *that, int Py, int Kx, const C *tw, const C *phx,
+                                     const C *phy, const C *phz, cudaStream_t st)
+{
+    if (ncols <= 0) return cudaSuccess;
+    if (2 * nrows > L || nout != nrows + 1 || cs != (int64_t)nrows * rs) return cudaErrorInvalidValue;
+    GenRadix g3, g1;
+    if (!gen_plan(L, gen_tile_elems<T>(true), g3, kGenMaxRadixZ, 3)) return cudaErrorInvalidValue;
+    if (!gen_plan(L, gen_tile_elems<T>(true), g1, kGenMaxRadixZ, 1)) return cudaErrorInvalidValue;
+    const int cols = g1.TC;
+    const size_t sm = 2 * swsize(L * g3.TC) * sizeof(C);
+    cudaError_t e = allow_smem<k_gen_sp_zconv<T>>(sm);
+    if (e != cudaSuccess) return e;
+    k_gen_sp_zconv<T><<<(ncols + cols - 1) / cols, kGenThreads, sm, st>>>(S, ncols, width, magic_of(width), ss, rs,
+                                                                          cs, nrows, nout, that, Py, Kx, tw, phx, phy,
+                                                                          phz, g3, g1);
+    return cudaGetLastError();
+}
+
 }  // namespace demag

@@ -588,6 +588,8 @@ cudaError_t Passes<T>::sp_zconv(int L, C *S, int ncols, int width, int64_t ss, i
     if (ncols <= 0) return cudaSuccess;
     // zero padding: nz + 1 node rows out of L >= 2 nz
     if (L < 2 || 2 * nrows > L || nout != nrows + 1 || cs != (int64_t)nrows * rs) return cudaErrorInvalidValue;
+    if (!pow2_len(L))
+        return MixedPasses<T>::sp_zconv(L, S, ncols, width, ss, rs, cs, nrows, nout, that, Py, Kx, tw, phx, phy, phz, st);
     if (variant == 5) {
         cudaError_t e = cudaErrorNotSupported;
         switch (L) {

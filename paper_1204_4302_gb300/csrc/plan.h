@@ -55,6 +55,9 @@ template <typename T> struct MixedPasses {
                            int nin, int64_t oss, int64_t ors, int nout, const C *tw, int twstride, cudaStream_t st);
     static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
                              const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st);
+    static cudaError_t sp_zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                int nout, const T *that, int Py, int Kx, const C *tw, const C *phx, const C *phy,
+                                const C *phz, cudaStream_t st);
 };
 
 // Launchers of the field passes for element type T (defined in

@@ -542,7 +542,7 @@ __global__ void k_sp_extract(const double2 *__restrict__ S, int comp, int Px, in
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int kx = (int)(idx % Kx), ky = (int)((idx / Kx) % hy), kz = (int)(idx / ((int64_t)Kx * hy));
         const double2 v = S[((int64_t)kz * Py + ky) * Kxp + kx];
-        // theta / pi, reduced exactly: kx/Px + ky/Py + kz/Pz with power-of-two P
+        // theta / pi = kx/Px + ky/Py + kz/Pz (exact for power-of-two P, to rounding otherwise)
         const double th = (double)kx / Px + (double)ky / Py + (double)kz / Pz;
         double sn, cs;
         sincospi(th, &sn, &cs);

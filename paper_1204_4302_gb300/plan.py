@@ -20,8 +20,8 @@ class Plan:
     with the finite-difference field (Eqs. "scpot" and "field").
 
     pad: None or "pow2" pads each axis to the smallest power of two >= 2n - 1;
-    "smooth" to the smallest even length >= 2n - 1 with prime factors 2, 3, 5
-    and 7 (mixed-radix passes, DM only); "tuned" to the per-axis choice of the
+    "smooth" to the smallest even length >= 2n - 1 (SP: >= 2n) with prime
+    factors 2, 3, 5 and 7 (mixed-radix passes); "tuned" (DM) to the per-axis choice of the
     two that the padding autotuner finds fastest (timed once, then cached);
     or explicit (px, py, pz)."""
 
@@ -45,7 +45,11 @@ class Plan:
         self.handle = None
         with torch.cuda.device(self.device):
             if method == "sp":
-                self.handle = B.demag_plan_create_sp(nx, ny, nz, *self.d, code, *(pad or (0, 0, 0)))
+                if pad == "smooth":
+                    self.handle = B.demag_plan_create_sp(nx, ny, nz, *self.d, code, pad_mode=B.DEMAG_PAD_SMOOTH)
+                else:
+                    self.handle = B.demag_plan_create_sp(nx, ny, nz, *self.d, code,
+                                                         *(pad if pad not in (None, "pow2") else (0, 0, 0)))
             elif pad is None or pad == "pow2":
                 self.handle = B.demag_plan_create(nx, ny, nz, *self.d, code)
             elif pad == "smooth":

@@ -240,3 +240,36 @@ def test_sp_tma_z_pass_variant(n, prec):
         assert _relmax(H, H_ref) <= tol
     assert np.array_equal(out[0], out[1])
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,pad", [((17, 9, 6), "smooth"),                 # 36 x 18 x 12
+                                   ((40, 33, 20), "smooth"),               # 80 x 70 x 40
+                                   ((13, 11, 5), (30, 42, 10)),            # odd x transform (15), radix 7 on y
+                                   ((70, 5, 100), (140, 12, 200)),         # z 200 = 20 . 10
+                                   ((6, 100, 130), (12, 250, 270))])       # y 250, z 270 = 18 . 15
+def test_sp_mixed_radix_padding_matches_oracle(n, pad, prec):
+    """Scalar-potential plans on padded lengths that are products of 2, 3, 5, 7
+    (the mixed-radix passes, including the SP z pass): field and node
+    potential against the oracle (which pads to powers of two; every even
+    period >= 2n gives the same convolution)."""
+    from paper_1204_4302_gb300.plan import Plan
+    d = (2e-9, 1.5e-9, 2.5e-9)
+    M = MS * inputs.random_unit(n, seed=sum(n) + 3)
+    phi_ref = oracle.sp_potential_fft(M, d)
+    H_ref = oracle.sp_field_from_potential(phi_ref, d)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    p = Plan(n, d, prec=prec, method="sp", pad=pad)
+    info = p.info()
+    P = (info["px"], info["py"], info["pz"])
+    assert all(v >= 2 * m for v, m in zip(P, n)) and any(v & (v - 1) for v in P), P
+    if pad != "smooth":
+        assert P == pad
+    Mt = torch.tensor(M, dtype=dt, device="cuda")
+    H = p.field(Mt).double().cpu().numpy()
+    phi = p.potential(Mt).double().cpu().numpy()
+    tol = 1e-12 if prec == "f64" else _fp32_bound(n, d, phi_ref, H_ref)
+    assert _relmax(H, H_ref) <= tol, (n, prec, _relmax(H, H_ref), tol)
+    assert _relmax(phi, phi_ref) <= (1e-12 if prec == "f64" else 8 * EPS32 * math.log2(
+        np.prod([oracle.sp_padded_size(v) for v in n]))), n
+    p.close()

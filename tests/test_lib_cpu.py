@@ -88,8 +88,18 @@ def test_padding_options_are_checked_before_any_device_call(lib):
         else:
             binding.demag_plan_destroy(h)
     with pytest.raises(binding.DemagError) as e:
-        binding.demag_plan_create_sp(8, 8, 8, 1.0, 1.0, 1.0, 0, pad_mode=1)
+        binding.demag_plan_create_sp(8, 8, 8, 1.0, 1.0, 1.0, 0, pad_mode=2)
     assert e.value.name == "DEMAG_ERR_UNSUPPORTED"
+    with pytest.raises(binding.DemagError) as e:
+        binding.demag_plan_create_sp(8, 8, 8, 1.0, 1.0, 1.0, 0, px=14)     # even and smooth but below 2n
+    assert e.value.name == "DEMAG_ERR_INVALID_ARG"
+    for kw in [{"pad_mode": 1}, {"px": 18, "pz": 20}]:   # accepted by the checks
+        try:
+            h = binding.demag_plan_create_sp(8, 8, 8, 1.0, 1.0, 1.0, 0, **kw)
+        except binding.DemagError as e:
+            assert e.name not in ("DEMAG_ERR_INVALID_ARG", "DEMAG_ERR_UNSUPPORTED"), kw
+        else:
+            binding.demag_plan_destroy(h)
     import ctypes
     lib_ = binding.load()
     d = (ctypes.c_int * 3)(8, 8, 8)
