@@ -118,26 +118,35 @@ __host__ __device__ constexpr double ct_cos_poly(double x)
     return sum;
 }
 constexpr double kCtPi = 3.14159265358979323846264338327950288;
+// The angle is kept as an exact fraction num / den of the full turn while the
+// symmetries reduce it to at most 1/8 turn; only the final angle is rounded.
 __host__ __device__ constexpr double ct_cos2pi(int e, int n)
 {
-    if (2 * e > n) e = n - e;  // cos(2 pi - x) = cos x; angle now in [0, pi]
-    double x = 2.0 * kCtPi * e / n, sg = 1.0;
-    if (x > kCtPi / 2) {  // cos(pi - x) = -cos x
-        x = kCtPi - x;
+    long long num = e % n, den = n;
+    double sg = 1.0;
+    if (2 * num > den) num = den - num;  // cos(2 pi - x) = cos x
+    if (4 * num > den) {                 // cos x = -cos(pi - x)
+        num = den - 2 * num;
+        den *= 2;
         sg = -1.0;
     }
-    return sg * (x > kCtPi / 4 ? ct_sin_poly(kCtPi / 2 - x) : ct_cos_poly(x));
+    if (8 * num > den) return sg * ct_sin_poly(2.0 * kCtPi * (double)(den - 4 * num) / (4.0 * (double)den));
+    return sg * ct_cos_poly(2.0 * kCtPi * (double)num / (double)den);
 }
 __host__ __device__ constexpr double ct_sin2pi(int e, int n)
 {
+    long long num = e % n, den = n;
     double sg = 1.0;
-    if (2 * e > n) {  // sin(2 pi - x) = -sin x
-        e = n - e;
+    if (2 * num > den) {  // sin(2 pi - x) = -sin x
+        num = den - num;
         sg = -1.0;
     }
-    double x = 2.0 * kCtPi * e / n;
-    if (x > kCtPi / 2) x = kCtPi - x;  // sin(pi - x) = sin x
-    return sg * (x > kCtPi / 4 ? ct_cos_poly(kCtPi / 2 - x) : ct_sin_poly(x));
+    if (4 * num > den) {  // sin x = sin(pi - x)
+        num = den - 2 * num;
+        den *= 2;
+    }
+    if (8 * num > den) return sg * ct_cos_poly(2.0 * kCtPi * (double)(den - 4 * num) / (4.0 * (double)den));
+    return sg * ct_sin_poly(2.0 * kCtPi * (double)num / (double)den);
 }
 
 // x W_R^E (forward, W_R = exp(-2 pi i / R)) or x conj(W_R^E) (inverse), the
