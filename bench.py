@@ -640,6 +640,7 @@ def run_batch(args, dev, rank):
     e1.synchronize()
     b.status()
     ms_autotuned = e0.elapsed_time(e1) / k
+    mode_autotuned = b.info()["mode"]
     # the per-state padding tuner (each state's lengths timed alone; no cache)
     ms_pad = {}
     for pad in ("tuned",):
@@ -667,7 +668,7 @@ def run_batch(args, dev, rank):
     else:
         os.environ["DEMAG_TUNE_CACHE"] = saved_cache
     out = {"workload": "64 states, 32..128 x 32..128 x 8..32 cells of 3 nm, FP32, field + energy",
-           "cells": cells_total, "mode": "persistent" if info["mode"] == 0 else "graph branches",
+           "cells": cells_total, "mode": "persistent" if mode_autotuned == 0 else "graph branches",
            "padding": "smooth" if pad_smooth < pad_pow2 else "pow2",
            # the configuration the autotuners keep (modes, then padding)
            "ms_per_call": round(ms_autotuned, 4), "cells_per_s": cells_total / (ms_autotuned / 1e3),
