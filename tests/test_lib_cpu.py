@@ -249,9 +249,19 @@ def test_plan_refuses_without_cuda():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
+    from paper_1204_4302_gb300.batch import Batch
     from paper_1204_4302_gb300.plan import Plan
+    from paper_1204_4302_gb300.tg import TGPlan
     with pytest.raises(RuntimeError):
         Plan((4, 4, 4), (1.0, 1.0, 1.0))
+    with pytest.raises(RuntimeError):
+        Plan((4, 4, 4), (1.0, 1.0, 1.0), method="sp", pad="smooth")
+    with pytest.raises(RuntimeError):
+        Plan.load("any.spec")
+    with pytest.raises(RuntimeError):
+        Batch([(4, 4, 4)], [(1.0, 1.0, 1.0)], pad="smooth")
+    with pytest.raises(RuntimeError):
+        TGPlan((4, 4, 4), (1.0, 1.0, 1.0), 1)
 
 
 def test_inputs_module_is_independent():
