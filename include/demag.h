@@ -283,11 +283,17 @@ demag_status demag_get_timing(demag_plan_t plan, double *ms, long *counts, int n
  * order them on one stream or with events.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and may load the
- * library's kernels; make that first call before any stream capture.
+ * library's kernels; make that first call before any stream capture. The
+ * address is kept per device together with the id of the device's context,
+ * and looked up again (the next call doing the set-up once more) after the
+ * context changed, e.g. after cudaDeviceReset.
  * Asynchronous; no cudaMalloc, cudaFree or other allocating call.
- * Returns DEMAG_ERR_INVALID_ARG for bad sizes, precision or pointers and
- * DEMAG_ERR_CUDA if the set-up or a launch fails. demag_last_error() is not
- * updated by this call. */
+ * Returns DEMAG_ERR_INVALID_ARG for bad sizes, precision or pointers,
+ * DEMAG_ERR_UNSUPPORTED beyond the capacity (checked before any product of
+ * the sizes is formed) and DEMAG_ERR_CUDA if the set-up or one of its own
+ * launches fails; an error left pending by earlier, unrelated work is not
+ * reported as this call's failure and is not cleared. demag_last_error() is
+ * not updated by this call. */
 demag_status demag_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
                                   demag_prec prec, const void *M, const void *H, double *E_dev,
                                   void *stream);
@@ -413,7 +419,14 @@ demag_status demag_tune_padding(int nx, int ny, int nz, double dx, double dy, do
  *    4 = variant 0's layout on half the columns with two CTAs per SM,
  *    5 = persistent CTAs whose input columns arrive by TMA tensor copies
  *    while the previous tile is transformed (z lengths 32..512; the
- *    autotuner tries it up to 256, where it is the fastest).
+ *    autotuner tries it up to 256, where it is the fastest),
+ *    6 = FP32 only: one persistent CTA per SM streams 8-column tiles whose
+ *    input rows arrive by a TMA tensor copy and whose tensor block arrives by
+ *    one bulk copy from a tile-ordered copy of the tensor spectrum (built at
+ *    setup, about the size of the spectrum), both one tile ahead; the
+ *    length-512 transforms run as 2 x 16 x 16 with packed FP32x2 butterflies
+ *    (z length 512, at most 256 input rows), 7 = as 6 with 4-column tiles and
+ *    two CTAs per SM.
  * y: 0 = two-stage column transform, 1 = swapped radix order (y lengths 32,
  *    128, 512), 2 = three-stage transform with more CTAs per SM (y lengths
  *    512 and 1024), 3 = as 2, with the forward pass by persistent CTAs that

@@ -287,8 +287,13 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     }
     tm.mark();
     // z forward . product . z inverse
-    e = Passes<T>::zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat, Py, Kx,
-                         twz, 1, st, p->zvariant);
+    e = cudaErrorNotSupported;
+    if ((p->zvariant == 6 || p->zvariant == 7) && f32 && p->ntile)  // persistent TMA forms, FP32 only
+        e = Passes<T>::zconv_ws(Pz, S2, Kx, Py, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz,
+                                (const T *)(const void *)p->ntile, twz, st, p->zvariant == 7 ? 4 : 8);
+    if (e == cudaErrorNotSupported)
+        e = Passes<T>::zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat, Py, Kx,
+                             twz, 1, st, p->zvariant >= 6 ? 0 : p->zvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("z convolution: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -734,6 +739,26 @@ size_t table_count(const demag_plan *p)
     return (size_t)(p->method == DEMAG_METHOD_SP ? 3 : 6) * plane;
 }
 
+// The tile-ordered copy of the FP32 tensor spectrum read by the persistent
+// TMA z pass (z variant 6), built from nhat32 on the plan's stream; plans whose
+// z length that kernel does not support keep none.
+cudaError_t build_ntile(demag_plan *p, cudaStream_t st)
+{
+    if (p->prec != DEMAG_F32 || p->method != DEMAG_METHOD_DM || !p->nhat32) return cudaSuccess;
+    const size_t n = Passes<float>::tile_tensor_elems(p->Pz, p->Py, p->Kx);
+    if (n == 0) return cudaSuccess;
+    if (!p->ntile) {
+        cudaError_t e = dmalloc(&p->ntile, n * sizeof(float));
+        if (e != cudaSuccess) {
+            p->ntile = nullptr;
+            return e;
+        }
+        p->ntile_bytes = n * sizeof(float);
+        p->device_bytes += p->ntile_bytes;
+    }
+    return Passes<float>::tile_tensor(p->Pz, p->nhat32, p->ntile, p->Py, p->Kx, st);
+}
+
 // A plan that is only timed (padding autotuner): its tensor spectrum is
 // zeroed instead of set up. The field passes do the same work whatever the
 // spectrum holds, so the timing is that of a set-up plan, without the FP64
@@ -743,7 +768,10 @@ demag_status zero_spectrum_for_timing(demag_plan *p, cudaStream_t st)
     const size_t plane = (size_t)(p->Pz / 2 + 1) * (p->Py / 2 + 1) * p->Kx;
     cudaError_t e = p->nhat32 ? cudaMemsetAsync(p->nhat32, 0, 6 * plane * sizeof(float), st)
                               : cudaMemsetAsync(p->nhat64, 0, 6 * plane * sizeof(double), st);
-    if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("timing plan: ") + cudaGetErrorString(e));
+    if (e == cudaSuccess) e = build_ntile(p, st);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
+                    std::string("timing plan: ") + cudaGetErrorString(e));
     p->setup_done = true;
     return DEMAG_OK;
 }
@@ -779,6 +807,7 @@ void demag_plan_destroy(demag_plan_t p)
     cudaFree(p->S1);
     cudaFree(p->nhat32);
     cudaFree(p->nhat64);
+    cudaFree(p->ntile);
     for (int a = 0; a < 3; ++a) {
         cudaFree(p->tw64[a]); cudaFree(p->tw32[a]);
         cudaFree(p->ph64[a]); cudaFree(p->ph32[a]);
@@ -1011,6 +1040,7 @@ demag_status demag_tensor_setup(demag_plan_t p, void *stream)
                                            (int64_t)Py * Kxp, Pz, p->tw64[2], 1, st));
         SETUP_CUDA(demag::tensor_extract(St, c, Px, Py, Pz, Kxp, nh64, p->nhat32, imag, st));
     }
+    SETUP_CUDA(build_ntile(p, st));
     unsigned long long bits = 0;
     SETUP_CUDA(cudaMemcpyAsync(&bits, imag, sizeof(bits), cudaMemcpyDeviceToHost, st));
     SETUP_CUDA(cudaStreamSynchronize(st));
@@ -1247,6 +1277,12 @@ demag_status demag_plan_load(const char *path, demag_plan_t *out)
         demag_plan_destroy(p);
         return fail(DEMAG_ERR_CUDA, std::string("spectrum upload: ") + cudaGetErrorString(e));
     }
+    if ((e = build_ntile(p, nullptr)) == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        demag_plan_destroy(p);
+        return fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
+                    std::string("tile-ordered tensor: ") + cudaGetErrorString(e));
+    }
     p->imag_max = h.imag_max;
     p->setup_done = true;
     *out = p;
@@ -1346,6 +1382,10 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     if (z2 && dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
     if (z2 && dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(4);   // half tile, two CTAs per SM
     if (z2 && p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input (DM and SP)
+    if (dm && p->ntile) {  // persistent, TMA input and tensor tiles, FP32: 8 or 4 columns per tile
+        zs.push_back(6);
+        zs.push_back(7);
+    }
     if (p->Py == 32 || p->Py == 128 || p->Py == 512) ys.push_back(1);
     if (p->Py == 512 || p->Py == 1024) ys.push_back(2);  // three-stage, more CTAs per SM
     if (p->Py == 512 || p->Py == 1024) ys.push_back(3);  // forward pass by the TMA pipeline
@@ -1476,7 +1516,7 @@ demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
 
 demag_status demag_set_variants(demag_plan_t p, int z, int y)
 {
-    if (!p || z < 0 || z > 5 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
+    if (!p || z < 0 || z > 7 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->zvariant = z;
     p->yvariant = y;
     return DEMAG_OK;

@@ -6,10 +6,13 @@
 #include "fft_engine.cuh"
 #include <string.h>
 
+#include <algorithm>
+
 #include "launch_util.cuh"
 #include "plan.h"
 #include "sp.cuh"
 #include "xpipe.cuh"
+#include "zws.cuh"
 
 namespace demag {
 
@@ -276,6 +279,91 @@ cudaError_t sp_zconv_tma(typename Cplx<T>::type *S, int ncols, int width, int64_
     return cudaGetLastError();
 }
 }  // namespace
+
+namespace {
+// Map of S2 [3][nz][Py][Kxp] complex seen as reals for the persistent z pass:
+// dims (2 Kx, Py, nz, 3), box (2 TC, 1, nz, 3). Cached for the last arguments.
+template <int L, int TC>
+bool zws_input_map(CUtensorMap *out, const float2 *S, int Kx, int Py, int nz, int64_t ss, int64_t rs, int64_t cs)
+{
+    static CUtensorMap cache;
+    static const void *k_S = nullptr;
+    static int64_t k_key[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t key[6] = {Kx, Py, nz, ss, rs, cs};
+    if (k_S == S && memcmp(key, k_key, sizeof key) == 0) {
+        *out = cache;
+        return true;
+    }
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * Kx, (cuuint64_t)Py, (cuuint64_t)nz, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)ss * sizeof(float2), (cuuint64_t)rs * sizeof(float2),
+                                   (cuuint64_t)cs * sizeof(float2)};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * TC), 1, (cuuint32_t)nz, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&cache, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(static_cast<const void *>(S)), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        k_S = nullptr;
+        return false;
+    }
+    k_S = S;
+    memcpy(k_key, key, sizeof key);
+    *out = cache;
+    return true;
+}
+
+template <int TC>
+cudaError_t zws_launch(float2 *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows, const float *ntile,
+                       const float2 *tw, cudaStream_t st)
+{
+    using Sh = ZwsShape<512, TC>;
+    CUtensorMap map;
+    if (!zws_input_map<512, TC>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
+    const size_t sm = zws_smem_bytes<512, TC>(nrows);
+    if (sm > 227 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = allow_smem<k_z_ws<512, TC>>(sm);
+    if (e != cudaSuccess) return e;
+    const int ntx = (Kx + TC - 1) / TC;
+    const int ntiles = ntx * Py;
+    const int cap = sm_count() * resident_ctas<k_z_ws<512, TC>>(Sh::NT, sm);
+    k_z_ws<512, TC><<<ntiles < cap ? ntiles : cap, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx,
+                                                                     ntiles);
+    return cudaGetLastError();
+}
+}  // namespace
+
+template <typename T>
+size_t Passes<T>::tile_tensor_elems(int L, int Py, int Kx)
+{
+    if (sizeof(T) != 4 || L != 512) return 0;
+    return (size_t)(Py / 2 + 1) * zws_ntx4(Kx) * ZwsShape<512, 4>::TZB;
+}
+
+template <typename T>
+cudaError_t Passes<T>::tile_tensor(int L, const T *nhat, T *ntile, int Py, int Kx, cudaStream_t st)
+{
+    if (sizeof(T) != 4 || L != 512) return cudaErrorNotSupported;
+    const size_t n = tile_tensor_elems(L, Py, Kx);
+    const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 16);
+    k_tile_tensor<T><<<grid, 256, 0, st>>>(nhat, ntile, Kx, Py / 2 + 1, ZwsShape<512, 4>::HZ, zws_ntx4(Kx));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Passes<T>::zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                const T *ntile, const C *tw, cudaStream_t st, int tc)
+{
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorNotSupported;
+    } else {
+        if (L != 512 || !ntile || nrows < 1 || 2 * nrows > L || ((uintptr_t)S & 15) || ((uintptr_t)ntile & 15) ||
+            (ss * (int64_t)sizeof(C)) % 16 || (rs * (int64_t)sizeof(C)) % 16 || (cs * (int64_t)sizeof(C)) % 16)
+            return cudaErrorNotSupported;
+        return tc == 4 ? zws_launch<4>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st)
+                       : zws_launch<8>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st);
+    }
+}
 
 template <typename T>
 int Passes<T>::pipe_error_take()

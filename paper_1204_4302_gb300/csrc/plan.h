@@ -88,6 +88,15 @@ template <typename T> struct Passes {
     static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant = 0);
+    // persistent z pass streaming column tiles by TMA (FP32, L = 512, at most
+    // L/2 input rows); ntile: the tile-ordered tensor copy (tile_tensor); tc:
+    // columns per tile, 8 (one CTA per SM) or 4 (two CTAs per SM).
+    // cudaErrorNotSupported when the arguments do not allow it.
+    static cudaError_t zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                const T *ntile, const C *tw, cudaStream_t st, int tc = 8);
+    // elements of the tile-ordered tensor copy for zconv_ws (0: not used for this L)
+    static size_t tile_tensor_elems(int L, int Py, int Kx);
+    static cudaError_t tile_tensor(int L, const T *nhat, T *ntile, int Py, int Kx, cudaStream_t st);
     template <int L>
     static cudaError_t zconv_pipe(C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs, int nrows,
                                   const T *nhat, int Py, int Kx, const C *tw, int twstride, cudaStream_t st);
@@ -173,6 +182,10 @@ struct demag_plan {
     // tensor spectrum [6][Pz/2+1][Py/2+1][Kx] (SP: kernel tables [3][...])
     double *nhat64;
     float *nhat32;
+    // tile-ordered copy of nhat32 for the persistent TMA z pass (z variant 6;
+    // FP32 tensor-method plans whose z length it supports), else null
+    float *ntile;
+    size_t ntile_bytes;
     // SP: half-sample phase factors exp(-pi i k / P) per axis, k < P
     double2 *ph64[3];
     float2 *ph32[3];

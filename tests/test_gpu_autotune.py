@@ -31,7 +31,7 @@ def test_every_variant_matches_oracle(n, prec, tol):
     p = Plan(n, d, prec=prec)
     Mt = torch.tensor(M, dtype=dt, device="cuda")
     for x in (0, 1, 2):
-        for z in (0, 1, 2, 3, 4, 5):
+        for z in (0, 1, 2, 3, 4, 5, 6, 7):
             for y in (0, 1, 2, 3):
                 p.set_variants(z, y, x)
                 H = p.field(Mt).double().cpu().numpy()
