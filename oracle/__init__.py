@@ -274,15 +274,32 @@ def wrapped_tensor(octant: np.ndarray, P) -> np.ndarray:
     return W
 
 
-def tensor_spectrum(octant: np.ndarray, P) -> np.ndarray:
+def _rfftn(a, s=None, axes=None, workers=None):
+    """numpy.fft.rfftn, or scipy.fft.rfftn over `workers` threads (the same
+    transform; used for grids where one thread would take minutes)."""
+    if workers and workers > 1:
+        import scipy.fft
+        return scipy.fft.rfftn(a, s=s, axes=axes, workers=workers)
+    return np.fft.rfftn(a, s=s, axes=axes)
+
+
+def _irfftn(a, s=None, axes=None, workers=None):
+    if workers and workers > 1:
+        import scipy.fft
+        return scipy.fft.irfftn(a, s=s, axes=axes, workers=workers)
+    return np.fft.irfftn(a, s=s, axes=axes)
+
+
+def tensor_spectrum(octant: np.ndarray, P, workers: int | None = None) -> np.ndarray:
     """Real-to-complex 3-D DFT of the wrapped tensor: (6, Pz, Py, Px//2+1) complex."""
     W = wrapped_tensor(octant, P)
-    return np.fft.rfftn(W, axes=(1, 2, 3))
+    return _rfftn(W, axes=(1, 2, 3), workers=workers)
 
 
 def field_fft(M: np.ndarray, d, P=None, octant: np.ndarray | None = None,
-              spectrum: np.ndarray | None = None) -> np.ndarray:
-    """Zero-padded FFT convolution H = -N * M in float64 (numpy.fft)."""
+              spectrum: np.ndarray | None = None, workers: int | None = None) -> np.ndarray:
+    """Zero-padded FFT convolution H = -N * M in float64 (numpy.fft; with
+    workers > 1, scipy.fft's threaded transforms of the same definition)."""
     M = _check_m(M)
     _, nz, ny, nx = M.shape
     if P is None:
@@ -291,15 +308,15 @@ def field_fft(M: np.ndarray, d, P=None, octant: np.ndarray | None = None,
     if spectrum is None:
         if octant is None:
             octant = tensor_octant((nx, ny, nz), d)
-        spectrum = tensor_spectrum(octant, (Px, Py, Pz))
+        spectrum = tensor_spectrum(octant, (Px, Py, Pz), workers=workers)
     Nh = spectrum
-    Mh = np.fft.rfftn(M, s=(Pz, Py, Px), axes=(1, 2, 3))
+    Mh = _rfftn(M, s=(Pz, Py, Px), axes=(1, 2, 3), workers=workers)
     xx, yy, zz, xy, xz, yz = Nh
     Hh = np.empty_like(Mh)
     Hh[0] = -(xx * Mh[0] + xy * Mh[1] + xz * Mh[2])
     Hh[1] = -(xy * Mh[0] + yy * Mh[1] + yz * Mh[2])
     Hh[2] = -(xz * Mh[0] + yz * Mh[1] + zz * Mh[2])
-    H = np.fft.irfftn(Hh, s=(Pz, Py, Px), axes=(1, 2, 3))
+    H = _irfftn(Hh, s=(Pz, Py, Px), axes=(1, 2, 3), workers=workers)
     return np.ascontiguousarray(H[:, :nz, :ny, :nx])
 
 

@@ -192,6 +192,18 @@ def test_bruteforce_equals_fft(n):
     np.testing.assert_allclose(Hf, Hb, rtol=0, atol=1e-13 * np.max(np.abs(Hb)))
 
 
+@pytest.mark.parametrize("n", [(5, 4, 3), (7, 1, 6)])
+def test_threaded_fft_path_equals_bruteforce(n):
+    """The threaded transforms (workers > 1, used for the full-size grids)
+    give the direct pair sum too."""
+    pytest.importorskip("scipy")
+    d = (1.0, 0.9, 1.3)
+    M = inputs.random_unit(n, seed=12)
+    Hb = oracle.field_bruteforce(M, d)
+    Hf = oracle.field_fft(M, d, workers=4)
+    np.testing.assert_allclose(Hf, Hb, rtol=0, atol=1e-13 * np.max(np.abs(Hb)))
+
+
 def test_padding_invariance():
     """Any period P >= 2N - 1 gives the same field on the physical cells."""
     n = (6, 5, 3)
