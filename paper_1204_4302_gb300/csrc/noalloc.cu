@@ -36,6 +36,7 @@ static __device__ __align__(256) double g_partials[kMaxPartials];
 
 std::mutex g_lock;
 double *g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx[kMaxDevices] = {0};
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -84,9 +85,41 @@ k_sum_partials(const double *__restrict__ partials, int count, double factor, do
     if (threadIdx.x == 0) *E = factor * (ss[0] + sc[0]);
 }
 
+// Identity of the current device's context (the driver's 64-bit context
+// id, unique for the life of the process), so that an address looked up in
+// a context that has since been destroyed (cudaDeviceReset) is never reused.
+// 0 when the driver entry points are unavailable: then the address is looked
+// up again on every call.
+using CtxGetCurrent = int (*)(void **);
+using CtxGetId = int (*)(void *, unsigned long long *);
+
+unsigned long long context_id()
+{
+    static CtxGetCurrent get_current = nullptr;
+    static CtxGetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrent>(a);
+            get_id = reinterpret_cast<CtxGetId>(b);
+        }
+    }
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
 // Device address of g_partials on the current device. The host-side name of
 // a __device__ array is only a stand-in and must never reach a kernel; the
-// address is looked up once per device and cached.
+// address is looked up once per device and context and cached.
 demag_status partials_address(double **out)
 {
     int dev = -1;
@@ -94,15 +127,24 @@ demag_status partials_address(double **out)
         cudaGetLastError();
         return DEMAG_ERR_CUDA;
     }
+    // make the device's primary context current (it is created here after a
+    // reset), so that its id can be read
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DEMAG_ERR_CUDA;
+    }
+    const unsigned long long ctx = context_id();
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            g_addr[dev] = nullptr;
             return DEMAG_ERR_CUDA;
         }
         g_addr[dev] = static_cast<double *>(p);
+        g_ctx[dev] = ctx;
     }
     *out = g_addr[dev];
     return DEMAG_OK;
@@ -130,9 +172,12 @@ extern "C" demag_status demag_energy_noalloc(int nx, int ny, int nz, double dx, 
         !isfinite(dy) || !isfinite(dz))
         return DEMAG_ERR_INVALID_ARG;
     if (prec != DEMAG_F32 && prec != DEMAG_F64) return DEMAG_ERR_INVALID_ARG;
+    // capacity check before any integer product: 3 nx ny nz in double is
+    // exact far beyond the cap, so a huge grid cannot wrap around
+    if (3.0 * (double)nx * (double)ny * (double)nz > (double)kMaxPartials * kValuesPerBlock)
+        return DEMAG_ERR_UNSUPPORTED;  // beyond the fixed array
     const int64_t n = 3 * (int64_t)nx * ny * nz;
     const int64_t blocks = (n + kValuesPerBlock - 1) / kValuesPerBlock;
-    if (blocks > kMaxPartials) return DEMAG_ERR_UNSUPPORTED;  // beyond the fixed array
     if (!M || !H || !E_dev || ((uintptr_t)M & 15u) || ((uintptr_t)H & 15u) || ((uintptr_t)E_dev & 7u))
         return DEMAG_ERR_INVALID_ARG;
     double *partials = nullptr;
@@ -143,10 +188,21 @@ extern "C" demag_status demag_energy_noalloc(int nx, int ny, int nz, double dx, 
     if (!is_device_ptr(M, dev) || !is_device_ptr(H, dev) || !is_device_ptr(E_dev, dev))
         return DEMAG_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == DEMAG_F32)
-        k_dot_partials<float><<<(unsigned)blocks, kThreads, 0, st>>>((const float *)M, (const float *)H, n, partials);
-    else
-        k_dot_partials<double><<<(unsigned)blocks, kThreads, 0, st>>>((const double *)M, (const double *)H, n, partials);
-    k_sum_partials<<<1, kThreads, 0, st>>>(partials, (int)blocks, -0.5 * kMu0 * dx * dy * dz, E_dev);
-    return cudaGetLastError() == cudaSuccess ? DEMAG_OK : DEMAG_ERR_CUDA;
+    // Launch errors are taken from the launch calls themselves, so an error
+    // left pending by unrelated earlier work is neither reported as this
+    // call's failure nor cleared from the caller's view.
+    const bool clean = cudaPeekAtLastError() == cudaSuccess;
+    int64_t nn = n;
+    const double factor = -0.5 * kMu0 * dx * dy * dz;
+    int count = (int)blocks;
+    void *dot_args[] = {(void *)&M, (void *)&H, (void *)&nn, (void *)&partials};
+    void *sum_args[] = {(void *)&partials, (void *)&count, (void *)&factor, (void *)&E_dev};
+    const void *dot = prec == DEMAG_F32 ? (const void *)k_dot_partials<float> : (const void *)k_dot_partials<double>;
+    cudaError_t e = cudaLaunchKernel(dot, dim3((unsigned)blocks), dim3(kThreads), dot_args, 0, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel((const void *)k_sum_partials, dim3(1), dim3(kThreads), sum_args, 0, st);
+    if (e != cudaSuccess) {
+        if (clean) cudaGetLastError();  // clear this call's own launch error only
+        return DEMAG_ERR_CUDA;
+    }
+    return DEMAG_OK;
 }

@@ -268,3 +268,14 @@ def test_inputs_module_is_independent():
     """The input generators import neither the library nor the oracle."""
     src = open(os.path.join(ROOT, "paper_1204_4302_gb300", "inputs.py")).read()
     assert "import oracle" not in src and "binding" not in src and "torch" not in src
+
+
+def test_noalloc_capacity_is_checked_before_the_sizes_are_multiplied(lib):
+    """Axes whose product overflows 64-bit integers (2^21 each: 3 * 2^63) and
+    axes just beyond the fixed array are refused as unsupported before any
+    device call, never wrapped to a small or negative size."""
+    from paper_1204_4302_gb300 import binding
+    for dims in ((1 << 21, 1 << 21, 1 << 21), (2 ** 31 - 1, 2 ** 31 - 1, 2 ** 31 - 1), (1024, 1024, 512)):
+        with pytest.raises(binding.DemagError) as e:
+            binding.demag_energy_noalloc(*dims, 1.0, 1.0, 1.0, binding.DEMAG_F32, None, None, None)
+        assert e.value.name == "DEMAG_ERR_UNSUPPORTED", dims

@@ -43,6 +43,16 @@ def test_noalloc_energy_matches_regular_energy_twice(prec, tol):
         for e in got:
             assert abs(e - ref) <= tol * abs(ref), (e, ref)
         assert got[0] == got[1]
+        # on a non-default stream, with the device's free memory unchanged
+        side = torch.cuda.Stream()
+        E2 = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        with torch.cuda.stream(side):
+            B.demag_energy_noalloc(*n, *d, code, M.data_ptr(), H.data_ptr(), E2.data_ptr(), side.cuda_stream)
+        side.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert E2.item() == got[0]
         # a grid beyond the fixed partial-sum array is refused, nothing launched
         with pytest.raises(B.DemagError) as err:
             B.demag_energy_noalloc(1024, 1024, 512, *d, code, M.data_ptr(), H.data_ptr(), E.data_ptr())
