@@ -205,9 +205,23 @@ demag_status demag_field_adjoint(demag_plan_t plan, const void *G, void *out, vo
 demag_status demag_field_energy(demag_plan_t plan, const void *M, void *H, double *E_dev,
                                 void *stream);
 
-/* Energy only: computes E for M without storing H (the last pass keeps only
- * the energy sums), synchronises the stream and writes E to *E_out (host). */
+/* Energy only: computes E for M without storing H, synchronises the stream
+ * and writes E to *E_out (host). By default (demag_set_spectral_energy) the
+ * energy is taken in Fourier space (Parseval's identity applied to the
+ * paper's Sec. 2 energy: E = (mu0/2) (V / (Px Py Pz)) sum_k w(kx) M^H N^ M
+ * over the half spectrum, w = 1 for kx = 0 and kx = Px/2, else 2), in the z
+ * pass right after the forward transforms, so the inverse passes do not run;
+ * plans whose z length has no spectral form (1024, lengths that are not
+ * powers of two) run the field pipeline and sum M.H in its last pass. */
 demag_status demag_energy(demag_plan_t plan, const void *M, double *E_out, void *stream);
+
+/* Route of energies computed without a field (demag_energy, and
+ * demag_energy_grad with G = NULL): enable != 0 (the default) takes the
+ * spectral sum where the plan allows it, 0 always runs the field pipeline.
+ * Both give E within rounding; the spectral route skips the y and x inverse
+ * passes. Tensor-method plans only (scalar-potential plans always run their
+ * own pipeline). */
+demag_status demag_set_spectral_energy(demag_plan_t plan, int enable);
 
 /* Energy and its gradient for a magnetization given as M = Ms * w * m, with m
  * the reduced magnetization [3][nz][ny][nx] (device), w an optional per-cell

@@ -46,6 +46,7 @@ EXPORTS = [
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
+    "demag_set_spectral_energy",
     "demag_field_host_async", "demag_host_wait",
     "demag_plan_create_sp", "demag_sp_potential",
     "demag_get_x_variant", "demag_set_x_variant", "demag_check_pipeline",
@@ -108,6 +109,7 @@ def load(path: str | Path | None = None):
         "demag_field_host": (S, [P, P, P, P]),
         "demag_plan_info": (S, [P, POINTER(demag_info)]),
         "demag_set_timing": (S, [P, I]),
+        "demag_set_spectral_energy": (S, [P, I]),
         "demag_set_graphs": (S, [P, I]),
         "demag_batch_autotune_padding": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
         "demag_field_energy_host_async": (S, [P, P, P, P, P]),
@@ -291,6 +293,10 @@ def demag_plan_info(plan) -> dict:
 
 def demag_set_timing(plan, enable=True):
     _check(load().demag_set_timing(_p(plan), int(bool(enable))), "demag_set_timing")
+
+
+def demag_set_spectral_energy(plan, enable=True):
+    _check(load().demag_set_spectral_energy(_p(plan), int(bool(enable))), "demag_set_spectral_energy")
 
 
 def demag_get_timing(plan, n=6):

@@ -272,6 +272,10 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     xo.rows_per_comp = nz * ny;
     PassTimer tm(p, st);
     cudaError_t e;
+    // energy without a field: the spectral (Parseval) sum in the z pass,
+    // E = (mu0/2) (V / (Px Py Pz)) sum_k w(kx) M^H N^ M, no inverse passes
+    const bool spectral = !job.out && job.E_dev && p->spectral_energy &&
+                          Passes<T>::zenergy_blocks(Pz, Py, Kx) > 0;
     // x forward
     if (Px == 1) e = Passes<T>::x1_fwd(xi, rows, S1, st);
     else e = Passes<T>::x_fwd(Px / 2, xi, rows, nx, S1, Kxp, twx, st, p->xvariant);
@@ -286,9 +290,32 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
         p->launches++;
     }
     tm.mark();
+    if (spectral) {
+        int nparts = 0;
+        e = cudaErrorNotSupported;
+        if ((p->zvariant == 6 || p->zvariant == 7) && f32 && p->ntile)
+            e = Passes<T>::zconv_ws_energy(Pz, S2, Kx, Py, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz,
+                                           (const T *)(const void *)p->ntile, twz, p->partials, &nparts, st,
+                                           p->zvariant == 7 ? 4 : 8);
+        if (e == cudaErrorNotSupported)
+            e = Passes<T>::zconv_energy(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat,
+                                        Py, Kx, twz, 1, p->partials, &nparts, st);
+        if (e != cudaSuccess)
+            return fail(DEMAG_ERR_CUDA, std::string("z spectral energy: ") + cudaGetErrorString(e));
+        p->launches++;
+        tm.mark();
+        tm.mark();  // no inverse y pass
+        tm.mark();  // no inverse x pass
+        const double V = p->dx * p->dy * p->dz;
+        e = demag::energy_finalize(p->partials, nparts, 0.5 * kMu0 * V / ((double)Px * Py * Pz), job.E_dev, st);
+        if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
+        p->launches++;
+        tm.mark();
+        return DEMAG_OK;
+    }
     // z forward . product . z inverse
     e = cudaErrorNotSupported;
-    if ((p->zvariant == 6 || p->zvariant == 7) && f32 && p->ntile)  // persistent TMA forms, FP32 only
+    if (p->zvariant >= 6 && f32 && p->ntile)  // persistent TMA forms, FP32 only
         e = Passes<T>::zconv_ws(Pz, S2, Kx, Py, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz,
                                 (const T *)(const void *)p->ntile, twz, st, p->zvariant == 7 ? 4 : 8);
     if (e == cudaErrorNotSupported)
@@ -655,6 +682,12 @@ demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz
                               : (prec == DEMAG_F32 ? Passes<float>::x_blocks(p->Px / 2, rows)
                                                    : Passes<double>::x_blocks(p->Px / 2, rows));
     if (sp) p->npartials = Passes<float>::sp_grad_blocks(nx, ny, nz);
+    if (!sp) {  // room for the spectral energy's per-CTA sums
+        const int ze = prec == DEMAG_F32 ? Passes<float>::zenergy_blocks(p->Pz, p->Py, p->Kx)
+                                         : Passes<double>::zenergy_blocks(p->Pz, p->Py, p->Kx);
+        p->npartials = std::max(p->npartials, ze);
+    }
+    p->spectral_energy = true;
     auto cleanup_fail = [&](cudaError_t e, const char *what) {
         demag_plan_destroy(p);
         return fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
@@ -1503,6 +1536,13 @@ demag_status demag_tune_padding(int nx, int ny, int nz, double dx, double dy, do
         tune_store(kpow2, cand[0][0], cand[1][0], cand[2][0], tpow2);
     }
     g_err.clear();
+    return DEMAG_OK;
+}
+
+demag_status demag_set_spectral_energy(demag_plan_t p, int enable)
+{
+    if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    p->spectral_energy = enable != 0;
     return DEMAG_OK;
 }
 

@@ -308,6 +308,25 @@ __device__ __forceinline__ void tensor_product(const T *__restrict__ nhat, int64
     z = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
 }
 
+// m^H N^ m at one frequency for the real symmetric folded tensor (the
+// spectral energy density of the Parseval form of E, paper Sec. 2).
+template <typename T, typename C>
+__device__ __forceinline__ T quad_form(const C &x, const C &y, const C &z, T nxx, T nyy, T nzz, T nxy, T nxz, T nyz)
+{
+    const T pxx = x.x * x.x + x.y * x.y, pyy = y.x * y.x + y.y * y.y, pzz = z.x * z.x + z.y * z.y;
+    const T pxy = x.x * y.x + x.y * y.y, pxz = x.x * z.x + x.y * z.y, pyz = y.x * z.x + y.y * z.y;
+    return nxx * pxx + nyy * pyy + nzz * pzz + (T)2 * (nxy * pxy + nxz * pxz + nyz * pyz);
+}
+
+// Weight of column kx in the half spectrum's Parseval sum: the columns kx = 0
+// and kx = Px/2 (= Kx - 1 for Px >= 2) stand for themselves, every other one
+// for itself and its Hermitian partner.
+template <typename T>
+__device__ __forceinline__ T kx_weight(int kx, int Kx)
+{
+    return (kx == 0 || kx == Kx - 1) ? (T)1 : (T)2;
+}
+
 // Order of the ky rows over the z-pass CTAs: 0, Py/2, 1, Py-1, 2, Py-2, ...
 // so that the two rows sharing a folded tensor row run at about the same
 // time and the second read of that tensor block hits L2.
@@ -365,10 +384,10 @@ __device__ __forceinline__ void tensor_block_prefetch(T *smT, const T *__restric
 // + kx with ky = ky_pair_order(i). The CTA's block of the tensor spectrum
 // ([6][L/2+1][Py/2+1][Kx], folded in ky and kz) is copied to shared memory
 // asynchronously while the first stage runs.
-template <typename T, int L, int V, bool CG>
+template <typename T, int L, int V, bool CG, bool EONLY = false>
 __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
           int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
-          int twstride, int tile, unsigned char *smraw)
+          int twstride, int tile, unsigned char *smraw, double *partials = nullptr)
 {
     using C = typename Cplx<T>::type;
     using Sh = ZShape<T, L, V>;
@@ -416,6 +435,7 @@ __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restric
     const bool act2 = threadIdx.x < TC * R1;
     const int c2 = threadIdx.x % TC, j2 = threadIdx.x / TC, f2 = f0 + c2;
     C v0[R2], v1[R2], v2[R2];
+    T e = 0;  // EONLY: this thread's part of sum_k w m^H N^ m
     if (act2) {
         const C *s = sm + sw(j2 * TC + c2);
 #pragma unroll
@@ -450,14 +470,25 @@ __device__ __forceinline__ void k_z_conv2_tile(typename Cplx<T>::type *__restric
                 const T nxx = t[0], nyy = t[TC], nzz = t[2 * TC];
                 const T nxy = sy * t[3 * TC], nxz = sz * t[4 * TC], nyz = sy * sz * t[5 * TC];
                 const C mx = v0[r], my = v1[r], mz = v2[r];
-                v0[r] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
-                v1[r] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
-                v2[r] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+                if constexpr (EONLY) {
+                    e += quad_form<T>(mx, my, mz, nxx, nyy, nzz, nxy, nxz, nyz);
+                } else {
+                    v0[r] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+                    v1[r] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+                    v2[r] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+                }
             }
+            if constexpr (EONLY) e *= kx_weight<T>(f2 - (f2 / width) * width, Kx);
         }
-        RegDFT<R2, true, C>::run(v0);
-        RegDFT<R2, true, C>::run(v1);
-        RegDFT<R2, true, C>::run(v2);
+        if constexpr (!EONLY) {
+            RegDFT<R2, true, C>::run(v0);
+            RegDFT<R2, true, C>::run(v1);
+            RegDFT<R2, true, C>::run(v2);
+        }
+    }
+    if constexpr (EONLY) {
+        block_partial<NT>((double)e, partials, tile);
+        return;
     }
     __syncthreads();  // all stage-2 reads done before the buffers are rewritten
     if (act2) {
@@ -508,6 +539,20 @@ k_z_conv2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     k_z_conv2_tile<T, L, V, false>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, blockIdx.x, smraw);
+}
+
+// Spectral energy of the z columns (EONLY form of k_z_conv2): forward z
+// transforms, then per CTA the sum over its columns and all kz of
+// w(kx) m^H N^ m into partials[blockIdx.x]; nothing is written back.
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(ZShape<T, L, V>::NT, ZShape<T, L, V>::MIN_CTAS)
+k_z_energy2(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+            int nrows, const T *__restrict__ nhat, int Py, int Kx, const typename Cplx<T>::type *__restrict__ tw,
+            int twstride, double *__restrict__ partials)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_z_conv2_tile<T, L, V, false, true>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, blockIdx.x,
+                                         smraw, partials);
 }
 
 // Fused z pass, persistent and software pipelined (L >= 32): each CTA loops
@@ -695,12 +740,47 @@ k_z_conv3(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
 }
 
 // Fused z pass for L <= 16: one thread per column, all in registers.
-template <typename T, int L, bool CG>
+template <typename T, int L, bool CG, bool EONLY = false>
 __device__ __forceinline__ void k_z_conv1_tile(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
-          int nrows, const T *__restrict__ nhat, int Py, int Kx, int tile, unsigned char *smraw)
+          int nrows, const T *__restrict__ nhat, int Py, int Kx, int tile, unsigned char *smraw, double *partials = nullptr)
 {
     using C = typename Cplx<T>::type;
     const int f = tile * Tile2<T>::NT + threadIdx.x;
+    if constexpr (EONLY) {
+        T e = 0;
+        if (f < ncols) {
+            const int ky = f / width, kx = f - ky * width;
+            const int64_t base = (int64_t)ky * ss + kx;
+            C a[L], b[L], c[L];
+#pragma unroll
+            for (int r = 0; r < L; ++r) {
+                const bool ok = r < nrows;
+                a[r] = ok ? S[base + (int64_t)r * rs] : cmk<C>(0, 0);
+                b[r] = ok ? S[base + (int64_t)r * rs + cs] : cmk<C>(0, 0);
+                c[r] = ok ? S[base + (int64_t)r * rs + 2 * cs] : cmk<C>(0, 0);
+            }
+            RegDFT<L, false, C>::run(a);
+            RegDFT<L, false, C>::run(b);
+            RegDFT<L, false, C>::run(c);
+            const bool fy = ky > Py / 2;
+            const int kyf = fy ? Py - ky : ky;
+            const T sy = fy ? (T)-1 : (T)1;
+            const int hy = Py / 2 + 1;
+            const int64_t plane = (int64_t)(L / 2 + 1) * hy * Kx;
+#pragma unroll
+            for (int r = 0; r < L; ++r) {
+                const bool fz = r > L / 2;
+                const T sz = fz ? (T)-1 : (T)1;
+                const int64_t bb = ((int64_t)(fz ? L - r : r) * hy + kyf) * Kx + kx;
+                e += quad_form<T>(a[r], b[r], c[r], __ldg(&nhat[bb]), __ldg(&nhat[plane + bb]),
+                                  __ldg(&nhat[2 * plane + bb]), sy * __ldg(&nhat[3 * plane + bb]),
+                                  sz * __ldg(&nhat[4 * plane + bb]), sy * sz * __ldg(&nhat[5 * plane + bb]));
+            }
+            e *= kx_weight<T>(kx, Kx);
+        }
+        block_partial<Tile2<T>::NT>((double)e, partials, tile);
+        return;
+    }
     if (f >= ncols) return;
     const int ky = f / width, kx = f - ky * width;
     const int64_t base = (int64_t)ky * ss + kx;
@@ -746,6 +826,16 @@ k_z_conv1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t 
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     k_z_conv1_tile<T, L, false>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, blockIdx.x, smraw);
+}
+
+// Spectral energy of the z columns for L <= 16 (EONLY form of k_z_conv1).
+template <typename T, int L>
+__global__ void __launch_bounds__(Tile2<T>::NT, (L >= 16 ? 1 : 2))
+k_z_energy1(typename Cplx<T>::type *__restrict__ S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+            int nrows, const T *__restrict__ nhat, int Py, int Kx, double *__restrict__ partials)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    k_z_conv1_tile<T, L, false, true>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, blockIdx.x, smraw, partials);
 }
 
 }  // namespace demag

@@ -313,22 +313,24 @@ bool zws_input_map(CUtensorMap *out, const float2 *S, int Kx, int Py, int nz, in
     return true;
 }
 
-template <int TC>
+template <int TC, bool EONLY = false>
 cudaError_t zws_launch(float2 *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows, const float *ntile,
-                       const float2 *tw, cudaStream_t st)
+                       const float2 *tw, cudaStream_t st, double *partials = nullptr, int *nparts = nullptr)
 {
     using Sh = ZwsShape<512, TC>;
     CUtensorMap map;
     if (!zws_input_map<512, TC>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
     const size_t sm = zws_smem_bytes<512, TC>(nrows);
     if (sm > 227 * 1024) return cudaErrorNotSupported;
-    cudaError_t e = allow_smem<k_z_ws<512, TC>>(sm);
+    cudaError_t e = allow_smem<k_z_ws<512, TC, EONLY>>(sm);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + TC - 1) / TC;
     const int ntiles = ntx * Py;
-    const int cap = sm_count() * resident_ctas<k_z_ws<512, TC>>(Sh::NT, sm);
-    k_z_ws<512, TC><<<ntiles < cap ? ntiles : cap, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx,
-                                                                     ntiles);
+    const int cap = sm_count() * resident_ctas<k_z_ws<512, TC, EONLY>>(Sh::NT, sm);
+    const int grid = ntiles < cap ? ntiles : cap;
+    if (nparts) *nparts = grid;
+    k_z_ws<512, TC, EONLY><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx, ntiles,
+                                                     partials);
     return cudaGetLastError();
 }
 }  // namespace
@@ -363,6 +365,78 @@ cudaError_t Passes<T>::zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t
         return tc == 4 ? zws_launch<4>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st)
                        : zws_launch<8>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st);
     }
+}
+
+template <typename T>
+cudaError_t Passes<T>::zconv_ws_energy(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                       const T *ntile, const C *tw, double *partials, int *nparts, cudaStream_t st,
+                                       int tc)
+{
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorNotSupported;
+    } else {
+        if (L != 512 || !ntile || nrows < 1 || 2 * nrows > L || ((uintptr_t)S & 15) || ((uintptr_t)ntile & 15) ||
+            (ss * (int64_t)sizeof(C)) % 16 || (rs * (int64_t)sizeof(C)) % 16 || (cs * (int64_t)sizeof(C)) % 16)
+            return cudaErrorNotSupported;
+        return tc == 4 ? zws_launch<4, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts)
+                       : zws_launch<8, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts);
+    }
+}
+
+template <typename T>
+int Passes<T>::zenergy_blocks(int L, int Py, int Kx)
+{
+    const int ncols = Py * Kx;
+    if (ncols <= 0 || !pow2_len(L) || L > 512) return 0;
+    int n;
+    if (L <= 16) {
+        n = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
+    } else {
+        int tc;
+        switch (L) {
+        case 32: tc = ZShape<T, 32, 0>::TC; break;
+        case 64: tc = ZShape<T, 64, 0>::TC; break;
+        case 128: tc = ZShape<T, 128, 0>::TC; break;
+        case 256: tc = ZShape<T, 256, 0>::TC; break;
+        default: tc = ZShape<T, 512, 0>::TC; break;
+        }
+        n = (ncols + tc - 1) / tc;
+    }
+    const int ws = 2 * sm_count();  // the persistent form: at most two CTAs per SM
+    return n > ws ? n : ws;
+}
+
+template <typename T>
+cudaError_t Passes<T>::zconv_energy(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+                                    int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
+                                    double *partials, int *nparts, cudaStream_t st)
+{
+    if (ncols <= 0 || !pow2_len(L) || L > 512 || (L > 1 && 2 * nrows > L)) return cudaErrorNotSupported;
+    if (L <= 16) {
+        const int grid = (ncols + Tile2<T>::NT - 1) / Tile2<T>::NT;
+        *nparts = grid;
+#define DEMAG_CASE(LL)                                                                                     \
+    case LL:                                                                                               \
+        k_z_energy1<T, LL><<<grid, Tile2<T>::NT, 0, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx,   \
+                                                           partials);                                     \
+        return cudaGetLastError();
+        switch (L) { DEMAG_CASE(1) DEMAG_CASE(2) DEMAG_CASE(4) DEMAG_CASE(8) DEMAG_CASE(16) default: return cudaErrorNotSupported; }
+#undef DEMAG_CASE
+    }
+#define DEMAG_CASE(LL)                                                                                     \
+    case LL: {                                                                                             \
+        using Sh = ZShape<T, LL, 0>;                                                                       \
+        const size_t sm = 3 * swsize(LL * Sh::TC) * sizeof(C) + (LL / 2 + 1) * 6 * Sh::TC * sizeof(T);     \
+        cudaError_t e = allow_smem<k_z_energy2<T, LL, 0>>(sm);                                             \
+        if (e != cudaSuccess) return e;                                                                    \
+        const int grid = (ncols + Sh::TC - 1) / Sh::TC;                                                    \
+        *nparts = grid;                                                                                    \
+        k_z_energy2<T, LL, 0><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, \
+                                                        twstride, partials);                              \
+        return cudaGetLastError();                                                                         \
+    }
+    switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorNotSupported; }
+#undef DEMAG_CASE
 }
 
 template <typename T>

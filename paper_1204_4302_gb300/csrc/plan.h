@@ -94,6 +94,19 @@ template <typename T> struct Passes {
     // cudaErrorNotSupported when the arguments do not allow it.
     static cudaError_t zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
                                 const T *ntile, const C *tw, cudaStream_t st, int tc = 8);
+    // spectral energy (the Parseval form of E, no inverse passes): forward z
+    // transforms and the per-CTA sums of w(kx) m^H N^ m into partials
+    // (*nparts of them). zconv_ws_energy: the persistent TMA form (as
+    // zconv_ws); zconv_energy: the two-stage / one-thread forms (power-of-two
+    // L <= 512). cudaErrorNotSupported where the form does not exist.
+    static cudaError_t zconv_ws_energy(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
+                                       const T *ntile, const C *tw, double *partials, int *nparts, cudaStream_t st,
+                                       int tc = 8);
+    static cudaError_t zconv_energy(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
+                                    int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
+                                    double *partials, int *nparts, cudaStream_t st);
+    // partial sums the spectral energy may write (0: no spectral form for L)
+    static int zenergy_blocks(int L, int Py, int Kx);
     // elements of the tile-ordered tensor copy for zconv_ws (0: not used for this L)
     static size_t tile_tensor_elems(int L, int Py, int Kx);
     static cudaError_t tile_tensor(int L, const T *nhat, T *ntile, int Py, int Kx, cudaStream_t st);
@@ -213,6 +226,9 @@ struct demag_plan {
     int yvariant;
     int xvariant;
     bool tuned;
+    // energy without a field by the spectral (Parseval) sum where the z
+    // length allows it (on by default; demag_set_spectral_energy)
+    bool spectral_energy;
     // timing
     bool timing;
     void *ring;  // per-kernel timing events (api.cu)

@@ -294,10 +294,16 @@ __host__ __device__ inline size_t zws_smem_bytes(int nrows)
 // block are processed at about the same time. map: S2 [3][nz][Py][Kxp] as
 // reals, box (2 TC, 1, nz, 3). ntile: the tile-ordered tensor copy. twg: the
 // z axis twiddle table W_L^m, m < L.
-template <int L, int TC>
+//
+// EONLY: the spectral (Parseval) energy instead of the field: after the
+// forward transforms each thread sums w(kx) m^H N^ m over its frequencies,
+// nothing is transformed back or written; partials[blockIdx.x] receives the
+// CTA's sum over all its tiles (NaN if a wait gave up).
+template <int L, int TC, bool EONLY = false>
 __global__ void __launch_bounds__(ZwsShape<L, TC>::NT, ZwsShape<L, TC>::MIN_CTAS)
 k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, int Py, int64_t ss, int64_t rs,
-       int64_t cs, int nrows, const float *__restrict__ ntile, const float2 *__restrict__ twg, int ntx, int ntiles)
+       int64_t cs, int nrows, const float *__restrict__ ntile, const float2 *__restrict__ twg, int ntx, int ntiles,
+       double *__restrict__ partials = nullptr)
 {
     static_assert(L == 512, "the persistent z pass is built for L = 512");
     using Sh = ZwsShape<L, TC>;
@@ -343,6 +349,12 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
         for (int h = 0; h < NSUB; ++h) bulk_g2s(tz + h * TZS, src + h * TZB, TZB * (unsigned)sizeof(float), &bar[1]);
     };
 
+    double eacc = 0.0;  // EONLY: this thread's sum over its tiles
+    auto fail_exit_partial = [&]() {
+        if constexpr (EONLY) {
+            if (tid == 0) partials[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+    };
     int t = blockIdx.x;
     if (tid == 0 && t < ntiles) {
         issue_in(t);
@@ -358,17 +370,22 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
         // 32-point DFT outputs 2m + p at rows 32 j1 + 2m + p (p = 0 even, 1 odd)
         {
             const int j1 = (tid / TC) & 15, p = tid / (16 * TC);
-#pragma unroll 1
+            // the three components' loads first, then their transforms
+            float2 v[3][16];
+#pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
-                float2 v[16];
                 const float2 *src = stg + ((size_t)comp * nrows + j1) * TC + c;
 #pragma unroll
-                for (int r = 0; r < 16; ++r) v[r] = j1 + 16 * r < nrows ? src[16 * r * TC] : make_float2(0.f, 0.f);
-                if (p) zw::tw32_half(v);
-                zw::dft16<false>(v);
+                for (int r = 0; r < 16; ++r)
+                    v[comp][r] = j1 + 16 * r < nrows ? src[16 * r * TC] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                if (p) zw::tw32_half(v[comp]);
+                zw::dft16<false>(v[comp]);
                 float2 *dst = ex + ((size_t)comp * EXR + 33 * j1 + p) * TC + c;
 #pragma unroll
-                for (int m = 0; m < 16; ++m) dst[2 * m * TC] = v[m];
+                for (int m = 0; m < 16; ++m) dst[2 * m * TC] = v[comp][m];
             }
         }
         __syncthreads();  // staging buffer consumed, exchange written
@@ -379,6 +396,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 mbar_wait_bounded(&bar[1], par, kPipeWaitCycles);
                 atomicExch(&g_xpipe_error, 1);
             }
+            fail_exit_partial();
             return;
         }
         if (tid == 0 && next < ntiles) {
@@ -409,6 +427,30 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
             if (!mbar_wait_bounded(&bar[1], par, kPipeWaitCycles)) s_fail = 1;
             const float *tb = tz + (c >> 2) * TZS + (c & 3);
             const float szm = j2 == 0 ? 1.f : -1.f;  // kz = L/2 + j2: folded unless j2 = 0
+            if constexpr (EONLY) {
+                float e = 0.f;
+                auto quad_all = [&](auto syneg) {
+                    constexpr bool SN = decltype(syneg)::value;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        const int kzf = m < 8 ? j2 + 32 * m : (m == 8 ? 256 - j2 : 512 - j2 - 32 * m);
+                        const float *q = tb + kzf * 4;
+                        float txz = q[4 * HZ * 4], tyz = q[5 * HZ * 4];
+                        if (m == 8) {
+                            txz *= szm;
+                            tyz *= szm;
+                        } else if (m > 8) {
+                            txz = -txz;
+                            tyz = -tyz;
+                        }
+                        const float nxy = SN ? -q[3 * HZ * 4] : q[3 * HZ * 4], nyz = SN ? -tyz : tyz;
+                        e += quad_form<float>(a[m], b[m], d[m], q[0], q[HZ * 4], q[2 * HZ * 4], nxy, txz, nyz);
+                    }
+                };
+                if (ky > Py / 2) quad_all(std::true_type{});
+                else quad_all(std::false_type{});
+                eacc += (double)(e * kx_weight<float>(kx0 + c, Kx));
+            } else {
             auto prod_all = [&](auto syneg) {
                 constexpr bool SN = decltype(syneg)::value;
 #pragma unroll
@@ -445,6 +487,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 o[(EXR + 33 * r) * TC] = b[r];
                 o[(2 * EXR + 33 * r) * TC] = d[r];
             }
+            }  // !EONLY
         }
         __syncthreads();  // tensor block consumed, exchange written
         if (s_fail) {
@@ -454,12 +497,15 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 mbar_wait_bounded(&bar[1], par, kPipeWaitCycles);
                 atomicExch(&g_xpipe_error, 1);
             }
+            fail_exit_partial();
             return;
         }
         if (tid == 0 && next < ntiles) {
             fence_proxy_async_smem();
             issue_tz(next);
         }
+
+        if constexpr (EONLY) continue;  // no inverse transforms
 
         // ---- stage 3: rows 32 n1 + k1 (k1 < 32, already twiddled by
         // W_L^-(n1 k1) in stage 2), 32-point inverse DFT, outputs
@@ -484,6 +530,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
         }
         __syncthreads();  // exchange read before the next tile's stage 1 writes it
     }
+    if constexpr (EONLY) block_partial<NT>(eacc, partials, blockIdx.x);
 }
 
 }  // namespace demag

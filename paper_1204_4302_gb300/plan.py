@@ -241,6 +241,11 @@ class Plan:
         """Replay each distinct call as one captured CUDA graph (see demag_set_graphs)."""
         B.demag_set_graphs(self.handle, enable)
 
+    def set_spectral_energy(self, enable: bool = True):
+        """Energies without a field by the Parseval sum in the z pass (default)
+        or by the field pipeline (see demag_set_spectral_energy)."""
+        B.demag_set_spectral_energy(self.handle, enable)
+
     def set_timing(self, enable: bool = True):
         B.demag_set_timing(self.handle, enable)
 
