@@ -346,3 +346,25 @@ def test_mpmath_closed_form_rounding():
     dz = s / mpmath.pi
     t = oracle.cell_tensor((0, 0, 0), (1.0, 2.0, 3.0))
     assert abs(t[2] - float(dz)) < 1e-15
+
+
+def test_rel_errors_two_cell_case_by_hand():
+    """The error measures on a two-cell field worked out by hand: H_ref has
+    3 and -4 in two entries (max |H_ref| = 4, ||H_ref||_2 = 5); H differs by
+    0.5 and -1.2 in two others (max 1.2, ||diff||_2 = 1.3). rel-max = 0.3,
+    rel-RMS = 0.26 (the Frobenius form of Sec. 3.2, Eq. "relr"), and the
+    field error of Sec. 5.1, Eq. "relerr", sqrt(sum |diff|^2 / N) with N = 2
+    cells: sqrt(1.69 / 2)."""
+    Href = np.zeros((3, 1, 1, 2))
+    Href[0, 0, 0, 0] = 3.0
+    Href[1, 0, 0, 1] = -4.0
+    H = Href.copy()
+    H[2, 0, 0, 0] += 0.5
+    H[0, 0, 0, 1] -= 1.2
+    e = oracle.rel_errors(H, Href)
+    assert e["rel_max"] == pytest.approx(0.3, rel=1e-15)
+    assert e["rel_rms"] == pytest.approx(0.26, rel=1e-15)
+    assert e["paper_relerr"] == pytest.approx(math.sqrt(0.845), rel=1e-15)
+    # swapped operands change the normaliser: ||H||_2 = sqrt(26.69)
+    f = oracle.rel_errors(Href, H)
+    assert f["rel_rms"] == pytest.approx(1.3 / math.sqrt(26.69), rel=1e-15)
