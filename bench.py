@@ -41,12 +41,17 @@ MU0 = 4e-7 * math.pi
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 PASS_NAMES = ["x_fwd", "y_fwd", "z_conv", "y_inv", "x_inv", "energy"]
+STATES = 40          # independent 256^3 states per step (about 1 s per 20 steps)
+L2_BYTES = 129 << 20  # GB300 L2: working sets below it are not HBM-bound
+FP64_TFLOPS = 1.25   # nominal GB300 FP64 rate (the FP64 form's ALU ceiling)
+# FP32 CUDA-core rate: 152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def pass_bytes(n, P, elem=4):
+def pass_bytes(n, P, elem=4, energy=True):
     """Algorithmic HBM bytes of each kernel per launch (the data each pass must
     read and write once): spectra are complex (2 elem), the tensor spectrum is
-    6 real octant arrays."""
+    6 real octant arrays; with the energy the last pass also reads M."""
     nx, ny, nz = n
     Px, Py, Pz = P
     Kx = Px // 2 + 1
@@ -60,8 +65,28 @@ def pass_bytes(n, P, elem=4):
         "y_fwd": s1 + s2,
         "z_conv": 2 * s2 + nh,
         "y_inv": s2 + s1,
-        "x_inv": s1 + 3 * cells * elem + 3 * cells * elem,  # reads S1 and M, writes H
+        "x_inv": s1 + 3 * cells * elem + (3 * cells * elem if energy else 0),  # reads S1 (and M), writes H
     }
+
+
+def fft_flops(L: int) -> float:
+    """Flops of one complex FFT of length L (the 5 L log2 L count)."""
+    return 5.0 * L * math.log2(L) if L > 1 else 0.0
+
+
+def step_flops(n, P) -> float:
+    """Arithmetic of one field step as the 5 L log2 L count of its transforms
+    (pruned: the forward passes run on the physical rows, the x pair-packed
+    R2C as a half-length complex transform) plus the 3x3 product (36 flops per
+    frequency). An estimate for the ALU ceiling, not an instruction count."""
+    nx, ny, nz = n
+    Px, Py, Pz = P
+    Kx = Px // 2 + 1
+    x = 3 * nz * ny * fft_flops(Px // 2)           # forward and inverse x: 2x this
+    y = 3 * nz * Kx * fft_flops(Py)                # forward and inverse y: 2x this
+    z = 3 * Py * Kx * fft_flops(Pz)                # forward and inverse z: 2x this
+    prod = 36.0 * Pz * Py * Kx
+    return 2 * (x + y + z) + prod
 
 
 SP_PASS_NAMES = ["x_fwd", "y_fwd", "sp_z", "y_inv", "x_inv", "sp_grad"]
@@ -230,9 +255,18 @@ def run_ours(args, rank, world, local_rank):
 
     n = N_GRID
     cells = n[0] * n[1] * n[2]
-    # independent state per rank (replicas of the method, distinct inputs)
+    S = args.states
+    # independent states per rank (replicas of the method, distinct inputs):
+    # state 0 from the shared numpy generator (the oracle tests' state), the
+    # others from seeded device generators
     m_np = inputs.random_unit(n, seed=SEED + rank)
     M = torch.tensor(MS * m_np, dtype=torch.float32, device=dev)
+    Ms_list = [M]
+    for i in range(1, S):
+        g = torch.Generator(device=dev).manual_seed(1000003 * (rank + 1) + i)
+        mi = torch.randn(3, n[2], n[1], n[0], device=dev, generator=g)
+        Ms_list.append(MS * mi / mi.norm(dim=0, keepdim=True))
+        del mi
 
     t0 = time.perf_counter()
     plan = Plan(n, CELL, prec="f32", device=dev)
@@ -246,13 +280,18 @@ def run_ours(args, rank, world, local_rank):
     info = plan.info()
     P = (info["px"], info["py"], info["pz"])
     H = torch.empty_like(M)
-    E = torch.empty((), dtype=torch.float64, device=dev)
+    Hb = [H, torch.empty_like(M)]
+    Es = torch.empty(S, dtype=torch.float64, device=dev)
+    E = Es[0]
     st = torch.cuda.current_stream(dev)
 
     from paper_1204_4302_gb300 import binding as B
 
     def step():
-        B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
+        # one step: field + energy of every state of the batch
+        for i, Mi in enumerate(Ms_list):
+            B.demag_field_energy(plan.handle, Mi.data_ptr(), Hb[i & 1].data_ptr(), Es[i:].data_ptr(),
+                                 st.cuda_stream)
 
     for _ in range(args.warmup):
         step()
@@ -261,7 +300,6 @@ def run_ours(args, rank, world, local_rank):
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    plan.set_timing(True)
     launches0 = plan.launch_count()
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -274,14 +312,23 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = ev0.elapsed_time(ev1)
     launches = plan.launch_count() - launches0
-    pass_ms, pass_n = plan.get_timing(6)
-    plan.set_timing(False)
     clocks = sampler.stop() if sampler else None
     ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = whole_job_rate(cells, world, args.steps, ms)
+    ms_per_field = ms_per_step / S
+    value = whole_job_rate(cells * S, world, args.steps, ms)
+
+    # per-pass times from a separate run (event timing adds events per call;
+    # the headline above ran without them)
+    plan.set_timing(True)
+    for _ in range(max(20, args.steps)):
+        B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
+    torch.cuda.synchronize()
+    pass_ms, pass_n = plan.get_timing(6)
+    plan.set_timing(False)
 
     # energy sanity (device value, read after timing)
+    B.demag_field_energy(plan.handle, M.data_ptr(), H.data_ptr(), E.data_ptr(), st.cuda_stream)
     E_val = float(E.item())
 
     # ---------------------------------------------------------------- roofline
@@ -332,10 +379,19 @@ def run_ours(args, rank, world, local_rank):
         diff = (H.double() - H64)
         rel_max = float(diff.abs().max() / H64.abs().max())
         rel_rms = float(diff.norm() / H64.norm())
-        f64 = {"ms_per_step": round(ms64, 4), "cells_per_s": cells / (ms64 / 1e3),
-               "speedup_f32_over_f64": round(ms64 / ms_per_step, 2),
+        b64 = sum(pass_bytes(n, P, 8).values())
+        fl64 = step_flops(n, P)
+        f64 = {"ms_per_field": round(ms64, 4), "cells_per_s": cells / (ms64 / 1e3),
+               "speedup_f32_over_f64": round(ms64 / ms_per_field, 2),
                "f32_rel_max_err_vs_f64": rel_max, "f32_rel_rms_err_vs_f64": rel_rms,
-               "energy_rel_diff": abs(E_val - float(E64.item())) / abs(float(E64.item()))}
+               "energy_rel_diff": abs(E_val - float(E64.item())) / abs(float(E64.item())),
+               # the FP64 form's two ceilings: HBM bytes of its passes and its
+               # FFT + product arithmetic against the FP64 rate
+               "hbm": {"bytes": b64, "gbs": round(b64 / (ms64 * 1e-3) / 1e9, 1),
+                       "frac": round(b64 / (ms64 * 1e-3) / 1e9 / peak, 3), "peak_gbs": peak},
+               "fp64": {"flops": fl64, "tflops": round(fl64 / (ms64 * 1e-3) / 1e12, 3),
+                        "frac": round(fl64 / (ms64 * 1e-3) / 1e12 / FP64_TFLOPS, 3), "peak_tflops": FP64_TFLOPS,
+                        "peak_source": "nominal GB300 FP64 rate (not measured)"}}
         plan64.close()
         del M64, H64
 
@@ -367,44 +423,83 @@ def run_ours(args, rank, world, local_rank):
         # end to end through the public API from pinned host buffers: every
         # step uploads its M and downloads its H; streamed calls overlap one
         # step's copies with the neighbouring steps' fields
-        Mh = M.cpu().pin_memory()
-        Hh = [torch.empty_like(Mh).pin_memory() for _ in range(2)]
+        NH = min(4, S)
+        Mh = [Ms_list[i].cpu().pin_memory() for i in range(NH)]
+        Hh = [torch.empty_like(Mh[0]).pin_memory() for _ in range(2)]
         Eh = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in range(2)]
-        for i in range(3):
-            plan.field_energy_host_async(Mh, Hh[i % 2], Eh[i % 2])
+
+        def e2e_step(step_idx):
+            # the step's S states: each uploaded from pinned host memory,
+            # field + energy computed, H and E downloaded (streamed calls)
+            for i in range(S):
+                plan.field_energy_host_async(Mh[i % NH], Hh[(step_idx * S + i) % 2], Eh[(step_idx * S + i) % 2])
+
+        e2e_step(0)
         plan.host_wait()
         barrier()
-        ke = max(5, args.steps)
+        ke = max(2, args.steps)
         t0 = time.perf_counter()
         for i in range(ke):
-            plan.field_energy_host_async(Mh, Hh[i % 2], Eh[i % 2])
+            e2e_step(i)
         plan.host_wait()
         barrier()
         te = (time.perf_counter() - t0) / ke
         tmax = max_over_ranks(te, dist, dev)
-        e2e_energy_rel = abs(float(Eh[(ke - 1) % 2].item()) - E_val) / abs(E_val)
+        plan.field_energy_host_async(Mh[0], Hh[0], Eh[0])
+        plan.host_wait()
+        e2e_energy_rel = abs(float(Eh[0].item()) - E_val) / abs(E_val)
         # the same calls one at a time (upload, field, download, synchronise)
         from paper_1204_4302_gb300 import binding as B
         t1 = time.perf_counter()
         for i in range(3):
-            B.demag_field_host(plan.handle, Mh.data_ptr(), Hh[0].data_ptr(), st.cuda_stream)
+            B.demag_field_host(plan.handle, Mh[0].data_ptr(), Hh[0].data_ptr(), st.cuda_stream)
         ts = (time.perf_counter() - t1) / 3
         nbytes = 3 * cells * 4
-        e2e = {"value": world * cells / tmax, "unit": "cells/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes + 8, "ms_per_step": round(tmax * 1e3, 4),
-               "mode": "streamed demag_field_energy_host_async calls (field + energy, H and E downloaded), "
-                       "pinned buffers",
+        e2e = {"value": world * cells * S / tmax, "unit": "cells/s", "h2d_bytes_per_step": nbytes * S,
+               "d2h_bytes_per_step": (nbytes + 8) * S, "ms_per_step": round(tmax * 1e3, 4),
+               "mode": f"streamed demag_field_energy_host_async calls, {S} states per step (field + energy, "
+                       "H and E downloaded), pinned buffers",
                "energy_rel_diff_vs_device_step": e2e_energy_rel,
-               "ms_per_step_synchronous_field_only": round(ts * 1e3, 4)}
+               "ms_per_field_synchronous_field_only": round(ts * 1e3, 4)}
+        del Mh, Hh
+
+    # energy without a field (minimisation loops): the spectral (Parseval) sum
+    # against the field pipeline's energy, same states
+    energy_only = None
+    if not args.skip_grad:
+        def estep():
+            for i, Mi in enumerate(Ms_list):
+                B.demag_energy_grad(plan.handle, Mi.data_ptr(), None, 1.0, Es[i:].data_ptr(), None, None,
+                                    st.cuda_stream)
+        res = {}
+        for route in (True, False):
+            plan.set_spectral_energy(route)
+            estep()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(max(2, args.steps // 2)):
+                estep()
+            e1.record(st)
+            e1.synchronize()
+            res[route] = (e0.elapsed_time(e1) / max(2, args.steps // 2) / S, float(Es[0].item()))
+        plan.set_spectral_energy(True)
+        energy_only = {"ms_per_energy_spectral": round(res[True][0], 4),
+                       "ms_per_energy_field_pipeline": round(res[False][0], 4),
+                       "cells_per_s_spectral": cells / (res[True][0] / 1e3),
+                       "speedup_spectral": round(res[False][0] / res[True][0], 3),
+                       "energy_rel_diff": abs(res[True][1] - res[False][1]) / abs(res[False][1]),
+                       "ms_per_field_energy_step": round(ms_per_field, 4)}
 
     batch = None
     if not args.skip_batch:
-        batch = run_batch(args, dev, rank)
+        batch = run_batch(args, dev, rank, peak)
 
     sp = None
     if not args.skip_sp:
         sp = run_sp(args, dev, M, H, peak)
-        sp["speedup_over_dm"] = round(ms_per_step / sp["ms_per_step"], 3)
+        sp["speedup_over_dm"] = round(ms_per_field / sp["ms_per_step"], 3)
 
     tgr = None
     if not args.skip_tg:
@@ -416,11 +511,11 @@ def run_ours(args, rank, world, local_rank):
 
     configs = None
     if not args.skip_configs:
-        configs = run_configs(args, dev)
+        configs = run_configs(args, dev, peak)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
-        cpu = cpu_baseline(args.cpu_sample)
+        cpu = cpu_baseline(args.ref_sample, args.cpu_headline)
 
     if rank == 0:
         out = {
@@ -431,13 +526,17 @@ def run_ours(args, rank, world, local_rank):
             "steps": args.steps,
             "warmup": args.warmup,
             "ms_per_step": round(ms_per_step, 4),
+            "ms_per_field": round(ms_per_field, 5),
+            "states_per_step": S,
+            "timed_region_s": round(ms / 1e3, 3),
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic (seeded random unit magnetization)",
-            "config": {"workload": "DM stray field + energy, 256x256x256 cells of 2 nm, padded 512^3, FP32 "
-                                   "FFT/product, FP64 tensor setup",
+            "config": {"workload": f"DM stray field + energy, 256x256x256 cells of 2 nm, padded 512^3, FP32 "
+                                   f"FFT/product, FP64 tensor setup; {S} independent states per step",
+                       "states_per_step": S,
                        "grid": list(n), "padded": list(P), "cell_m": list(CELL), "Ms": MS,
                        "parallelism": f"replicas x{world} (independent states)",
                        "l2": "inputs and spectra (~2 GB) larger than L2, no flush needed"},
@@ -451,6 +550,7 @@ def run_ours(args, rank, world, local_rank):
             "padding": padding,
             "configs": configs,
             "energy_J": E_val,
+            "energy_only": energy_only,
             "passes": per_pass,
             "roofline": roof,
             "clocks": clocks,
@@ -574,8 +674,17 @@ def run_tg(args, dev, peak):
         e1.record(st)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / k
+        R = plan.info()["sinc_terms"]
+        # the dense block-CP contraction Phi[k][j][i] = sum_K Z[K][k] Y[K][j] X[K][i]
+        # over K = 3 R r terms: 2 cells K flops (the step's dominant arithmetic)
+        fl = 2.0 * cells * 3 * R * r
         ent = {"rank": r, "ms_per_step": round(ms, 4), "cells_per_s": cells / (ms / 1e3),
-               "sinc_terms": plan.info()["sinc_terms"], "energy_J": float(E.item())}
+               "sinc_terms": R, "energy_J": float(E.item()),
+               "alu": {"bound": "alu", "flops_contraction": fl, "tflops": round(fl / (ms * 1e-3) / 1e12, 2),
+                       "peak_tflops": round(FP32_TFLOPS, 1),
+                       "frac": round(fl / (ms * 1e-3) / 1e12 / FP32_TFLOPS, 3),
+                       "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)",
+                       "time": "whole TG step (factor transforms, contraction, differences, energy)"}}
         plan.close()
         if r == 8 and not args.skip_f64:
             p64 = TGPlan(n, CELL, r, prec="f64", device=dev)
@@ -589,7 +698,7 @@ def run_tg(args, dev, peak):
     return out
 
 
-def run_batch(args, dev, rank):
+def run_batch(args, dev, rank, peak):
     """64 independent states of uneven sizes (32..128 x 32..128 x 8..32 cells of
     3 nm, seeded random unit m), FP32, one graph launch per batch call."""
     import torch
@@ -667,8 +776,19 @@ def run_batch(args, dev, rank):
         os.environ.pop("DEMAG_TUNE_CACHE", None)
     else:
         os.environ["DEMAG_TUNE_CACHE"] = saved_cache
+    # algorithmic bytes of every pass of every state at the kept padding
+    kept_mode = B.DEMAG_PAD_SMOOTH if pad_smooth < pad_pow2 else B.DEMAG_PAD_POW2
+    bytes_total = 0
+    for nn in dims:
+        Pst = tuple(B.demag_padded_lengths(*nn, pad_mode=kept_mode))
+        bytes_total += sum(pass_bytes(nn, Pst, 4).values())
+    gbs_call = bytes_total / (ms_autotuned * 1e-3) / 1e9
     out = {"workload": "64 states, 32..128 x 32..128 x 8..32 cells of 3 nm, FP32, field + energy",
-           "cells": cells_total, "mode": "persistent" if mode_autotuned == 0 else "graph branches",
+           "cells": cells_total,
+           "hbm": {"bytes_per_call": bytes_total, "gbs": round(gbs_call, 1),
+                   "frac_whole_call": round(gbs_call / peak, 3),
+                   "note": "all passes of all states over the batch call's time (the states' passes run "
+                           "concurrently, so no single-pass times exist)"}, "mode": "persistent" if mode_autotuned == 0 else "graph branches",
            "padding": "smooth" if pad_smooth < pad_pow2 else "pow2",
            # the configuration the autotuners keep (modes, then padding)
            "ms_per_call": round(ms_autotuned, 4), "cells_per_s": cells_total / (ms_autotuned / 1e3),
@@ -728,7 +848,7 @@ def run_padding(args, dev):
     return out
 
 
-def run_configs(args, dev):
+def run_configs(args, dev, peak):
     """The other workloads of the method's benchmark set, each on its own plan
     (autotuned): the 16^3 cube (FP64 and FP32), the 512x128x4 thin film
     (vortex + 5% noise), the 64^3 grid with a radius-32 sphere mask, the 128^3
@@ -802,6 +922,24 @@ def run_configs(args, dev):
                 plan.set_graphs(True)          # the same calls replayed as one captured graph each
                 ms_graph = timed(fn, k)
                 plan.set_graphs(False)
+                # per-pass event times (separate run) and, for working sets
+                # larger than L2, each pass's fraction of the HBM peak
+                plan.set_timing(True)
+                timed(fn, k)
+                pms, pn = plan.get_timing(6)
+                plan.set_timing(False)
+                pinfo = plan.info()
+                Pp = (pinfo["px"], pinfo["py"], pinfo["pz"])
+                pbytes = pass_bytes(n, Pp, 4, energy=kind != "fwdadj")
+                work = sum(pbytes.values()) * (2 if kind == "fwdadj" else 1)
+                passes = {}
+                for i, nm in enumerate(PASS_NAMES[:5]):
+                    if pn[i]:
+                        t = pms[i] / pn[i]
+                        gbs = pbytes[nm] / (t * 1e-3) / 1e9
+                        passes[nm] = {"ms": round(t, 4), "gbs": round(gbs, 1)}
+                        if work > L2_BYTES:
+                            passes[nm]["frac"] = round(gbs / peak, 3)
             fn()
             torch.cuda.synchronize()
             res[prec] = (ms, H.clone(), E.item() if kind != "fwdadj" else None)
@@ -816,6 +954,7 @@ def run_configs(args, dev):
                     "speedup_f32_over_f64": round(ms64 / ms32, 2),
                     "f32_rel_max_err_vs_f64": relmax(H32, H64),
                     "energy_rel_diff_f32_f64": abs(E32 - E64) / abs(E64) if E64 else None,
+                    "passes_f32": passes, "hbm_roofline_quoted": work > L2_BYTES,
                     "output": {"field": "H", "grad": "dE/dm", "fwdadj": "H (the adjoint runs after it)"}[kind]})
         out.append(row)
         del res, H32, H64
@@ -824,46 +963,95 @@ def run_configs(args, dev):
 
 
 # ------------------------------------------------------------------- oracle side
-def _oracle_sample(k: int):
-    """The oracle's field on a k^3 grid of the same workload (same cell, same
-    state recipe); returns a callable that runs one field evaluation."""
-    import numpy as np
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                v = ln.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_sample(k: int, workers: int):
+    """The oracle's field + energy on a k^3 grid of the same workload (same
+    cell, same state recipe), its FFTs threaded over `workers` cores; the
+    tensor table and spectrum are set up once (untimed, the method's setup /
+    apply split). Returns a callable that runs one evaluation."""
     import oracle
     from paper_1204_4302_gb300 import inputs
     n = (k, k, k)
     M = MS * inputs.random_unit(n, seed=SEED)
     P = tuple(oracle.padded_size(v) for v in n)
-    spec = oracle.tensor_spectrum(oracle.tensor_octant(n, CELL), P)   # setup, untimed
+    t0 = time.perf_counter()
+    spec = oracle.tensor_spectrum(oracle.tensor_octant(n, CELL, threads=workers), P, workers=workers)
+    setup_s = time.perf_counter() - t0
 
     def run():
-        H = oracle.field_fft(M, CELL, P=P, spectrum=spec)
+        H = oracle.field_fft(M, CELL, P=P, spectrum=spec, workers=workers)
         return oracle.energy(M, H, CELL)
-    return run, k ** 3
+    return run, k ** 3, setup_s
 
 
-def cpu_baseline(k: int):
-    run, cells = _oracle_sample(k)
+def _time_oracle(run, reps_max: int, budget_s: float):
     run()
     t0 = time.perf_counter()
     reps = 0
     while True:
         run()
         reps += 1
-        if time.perf_counter() - t0 > 8.0 or reps >= 5:
+        if time.perf_counter() - t0 > budget_s or reps >= reps_max:
             break
-    dt = (time.perf_counter() - t0) / reps
-    return {"value": cells / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy-FFT oracle field + energy on a {k}^3 grid of the same workload "
-                      f"(2 nm cells, random unit m), tensor spectrum precomputed; {reps} runs, "
-                      f"{dt:.2f} s each"}
+    return (time.perf_counter() - t0) / reps, reps
+
+
+def cpu_baseline(k: int, k_head: int):
+    """The FP64 oracle timed on the host cores: on the bounded sample the
+    reference arm times per step (k^3) and on the headline grid (k_head^3)."""
+    cores = _host_cores()
+    model = _cpu_model()
+    run, cells, setup_s = _oracle_sample(k, cores)
+    dt, reps = _time_oracle(run, 5, 10.0)
+    out = {"value": cells / dt, "unit": "cells/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+           "sample": f"FP64 oracle (numpy / threaded scipy FFT convolution + fsum energy) field + energy on a "
+                     f"{k}^3 grid of the same workload (2 nm cells, random unit m), FFTs over {cores} cores, "
+                     f"tensor spectrum set up once ({setup_s:.1f} s, untimed); {reps} runs, {dt:.2f} s each; the "
+                     f"reference arm times the same sample per step"}
+    del run
+    if k_head and k_head != k:
+        run, cells_h, setup_h = _oracle_sample(k_head, cores)
+        dth, reps_h = _time_oracle(run, 2, 20.0)
+        out["headline_grid"] = {"grid": [k_head] * 3, "value": cells_h / dth, "unit": "cells/s",
+                                "s_per_field": round(dth, 3), "runs": reps_h, "setup_s": round(setup_h, 1),
+                                "cores": cores}
+    return out
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     k = args.ref_sample
-    run, cells = _oracle_sample(k)
+    cores = _host_cores()
+    run, cells, setup_s = _oracle_sample(k, cores)
     for _ in range(args.warmup):
         run()
     t0 = time.perf_counter()
@@ -871,6 +1059,8 @@ def run_reference(args, rank, world):
         run()
     dt = (time.perf_counter() - t0) / args.steps
     value = cells / dt
+    sample = (f"FP64 oracle field + energy per step on a {k}^3 grid of the same workload, FFTs over {cores} "
+              f"cores, tensor spectrum set up once ({setup_s:.1f} s, untimed)")
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -887,9 +1077,8 @@ def run_reference(args, rank, world):
         "data": "synthetic (seeded random unit magnetization)",
         "config": {"workload": "DM stray field + energy, 256x256x256 cells of 2 nm (bounded sample, see cpu_baseline)",
                    "grid": list(N_GRID), "sample_grid": [k, k, k]},
-        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 numpy-FFT oracle field + energy per step on a {k}^3 grid of the "
-                                   f"same workload, tensor spectrum precomputed"},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": _cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -898,11 +1087,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--states", type=int, default=STATES, help="independent states per step")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=128)
-    ap.add_argument("--ref-sample", type=int, default=64)
+    ap.add_argument("--ref-sample", type=int, default=128,
+                    help="grid edge of the oracle sample per reference step (and of cpu_baseline.value)")
+    ap.add_argument("--cpu-headline", type=int, default=256,
+                    help="grid edge of the oracle timed on the headline grid (0: skip)")
     ap.add_argument("--skip-f64", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

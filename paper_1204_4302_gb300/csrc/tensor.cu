@@ -22,6 +22,9 @@
 //         1/|R| come from their three-term recurrence. Truncation ~1e-15.
 #include <math.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include <vector>
 
 #include "plan.h"
@@ -269,6 +272,16 @@ __device__ void far_multipole(double X, double Y, double Z, double a, double b, 
     }
 }
 
+// Regime of an offset: touching cells (closed form), separated within
+// kFar cells (tent quadrature), far (multipole).
+__device__ __forceinline__ int tensor_regime(int i, int j, int k, double X, double Y, double Z, double dmax)
+{
+    if (i <= 1 && j <= 1 && k <= 1) return 0;
+    return X * X + Y * Y + Z * Z >= (kFar * dmax) * (kFar * dmax) ? 2 : 1;
+}
+
+// Far offsets, one thread each (the near and mid offsets are left to
+// k_tensor_octant_warp).
 __global__ void k_tensor_octant(double *__restrict__ out, int nx, int ny, int nz, double a, double b,
                                 double c)
 {
@@ -278,11 +291,84 @@ __global__ void k_tensor_octant(double *__restrict__ out, int nx, int ny, int nz
         const int i = (int)(idx % nx), j = (int)((idx / nx) % ny), k = (int)(idx / ((int64_t)nx * ny));
         const double X = i * a, Y = j * b, Z = k * c;
         const double dmax = fmax(a, fmax(b, c));
+        if (tensor_regime(i, j, k, X, Y, Z, dmax) != 2) continue;
         double v[6];
-        if (i <= 1 && j <= 1 && k <= 1) near_closed(X, Y, Z, a, b, c, v);
-        else if (X * X + Y * Y + Z * Z >= (kFar * dmax) * (kFar * dmax)) far_multipole(X, Y, Z, a, b, c, v);
-        else mid_quadrature(X, Y, Z, a, b, c, v);
+        far_multipole(X, Y, Z, a, b, c, v);
         for (int q = 0; q < 6; ++q) out[q * n + idx] = v[q];
+    }
+}
+
+// Near and mid offsets, one warp each: the 27 stencil points of the closed
+// form, or the (z, y) node pairs of the tent quadrature, are spread over the
+// lanes and the six sums reduced across the warp. The offsets of the box
+// [0, bx) x [0, by) x [0, bz) (which holds every near and mid offset of the
+// table) that are far are skipped (warp-uniform).
+__global__ void __launch_bounds__(256) k_tensor_octant_warp(double *__restrict__ out, int nx, int ny, int nz,
+                                                            double a, double b, double c, int bx, int by, int bz)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int lane = threadIdx.x & 31;
+    const int64_t nbox = (int64_t)bx * by * bz;
+    const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nbox; w += wstep) {
+        const int i = (int)(w % bx), j = (int)((w / bx) % by), k = (int)(w / ((int64_t)bx * by));
+        const double X = i * a, Y = j * b, Z = k * c;
+        const double dmax = fmax(a, fmax(b, c));
+        const int reg = tensor_regime(i, j, k, X, Y, Z, dmax);
+        if (reg == 2) continue;
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        double scale;
+        if (reg == 0) {
+            if (lane < 27) {
+                const int p = lane % 3 - 1, q = (lane / 3) % 3 - 1, t = lane / 9 - 1;
+                const double wt = (p == 0 ? 2.0 : -1.0) * (q == 0 ? 2.0 : -1.0) * (t == 0 ? 2.0 : -1.0);
+                const double x = X + p * a, y = Y + q * b, z = Z + t * c;
+                s[0] = wt * newell_f(x, y, z);
+                s[1] = wt * newell_f(y, x, z);
+                s[2] = wt * newell_f(z, y, x);
+                s[3] = wt * newell_g(x, y, z);
+                s[4] = wt * newell_g(x, z, y);
+                s[5] = wt * newell_g(y, z, x);
+            }
+            scale = 1.0 / (4.0 * 3.14159265358979323846 * a * b * c);
+        } else {
+            const double gx = fmax(0.0, fabs(X) - a), gy = fmax(0.0, fabs(Y) - b), gz = fmax(0.0, fabs(Z) - c);
+            const double gap = sqrt(gx * gx + gy * gy + gz * gz);
+            const int nxn = half_axis_nodes(gap, a), nyn = half_axis_nodes(gap, b), nzn = half_axis_nodes(gap, c);
+            const int pairs = 4 * nzn * nyn;
+            for (int pr = lane; pr < pairs; pr += 32) {
+                const int kk = pr / (2 * nyn), jj = pr - kk * (2 * nyn);
+                double uz, wz, uy, wy;
+                tent_node(nzn, kk, c, uz, wz);
+                tent_node(nyn, jj, b, uy, wy);
+                const double rz = Z + uz, ry = Y + uy;
+                double pp[6] = {0, 0, 0, 0, 0, 0};
+                for (int ii = 0; ii < 2 * nxn; ++ii) {
+                    double ux, wx;
+                    tent_node(nxn, ii, a, ux, wx);
+                    const double rx = X + ux;
+                    const double r2 = rx * rx + ry * ry + rz * rz;
+                    const double ir = rsqrt(r2);
+                    const double ir2 = ir * ir;
+                    const double f = wx * ir2 * ir2 * ir;  // w / r^5
+                    pp[0] += f * (3.0 * rx * rx - r2);
+                    pp[1] += f * (3.0 * ry * ry - r2);
+                    pp[2] += f * (3.0 * rz * rz - r2);
+                    pp[3] += f * 3.0 * rx * ry;
+                    pp[4] += f * 3.0 * rx * rz;
+                    pp[5] += f * 3.0 * ry * rz;
+                }
+                const double wyz = wy * wz;
+                for (int q = 0; q < 6; ++q) s[q] += wyz * pp[q];
+            }
+            scale = -a * b * c / (4.0 * 3.14159265358979323846);
+        }
+        for (int q = 0; q < 6; ++q)
+            for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        if (lane == 0) {
+            const int64_t idx = ((int64_t)k * ny + j) * nx + i;
+            for (int q = 0; q < 6; ++q) out[q * n + idx] = scale * s[q];
+        }
     }
 }
 
@@ -570,7 +656,17 @@ cudaError_t tensor_octant(double *out, int nx, int ny, int nz, double dx, double
     if (!upload_rules()) return cudaErrorUnknown;
     const double h = fmax(dx, fmax(dy, dz));
     const int64_t n = (int64_t)nx * ny * nz;
-    k_tensor_octant<<<grid_for(n, 64), 64, 0, st>>>(out, nx, ny, nz, dx / h, dy / h, dz / h);
+    const double a = dx / h, b = dy / h, c = dz / h;
+    k_tensor_octant<<<grid_for(n, 64), 64, 0, st>>>(out, nx, ny, nz, a, b, c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the box that holds every offset closer than kFar cells (and the 2x2x2
+    // touching ones): |i a| < kFar (max edge = 1 after scaling)
+    const int bx = (int)std::min<double>(nx, std::max(2.0, std::floor(kFar / a) + 1));
+    const int by = (int)std::min<double>(ny, std::max(2.0, std::floor(kFar / b) + 1));
+    const int bz = (int)std::min<double>(nz, std::max(2.0, std::floor(kFar / c) + 1));
+    const int64_t warps = (int64_t)bx * by * bz;
+    k_tensor_octant_warp<<<grid_for(warps * 32, 256), 256, 0, st>>>(out, nx, ny, nz, a, b, c, bx, by, bz);
     return cudaGetLastError();
 }
 
