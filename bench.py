@@ -138,7 +138,7 @@ def whole_job_rate(cells_per_rank: int, world: int, steps: int, ms_max: float) -
 # The sources that define the field-step kernels of the DM and SP pipelines
 # and their launch shapes (the per-kernel DRAM traffic in profiles/traffic.json
 # is valid while these are unchanged).
-STEP_KERNEL_SOURCES = ("fft_engine.cuh", "fft2.cuh", "xpipe.cuh", "sp.cuh", "passes_impl.cuh", "passes_f32.cu",
+STEP_KERNEL_SOURCES = ("fft_engine.cuh", "fft2.cuh", "xpipe.cuh", "zws.cuh", "sp.cuh", "passes_impl.cuh", "passes_f32.cu",
                        "passes_f64.cu", "plan.h")
 
 

@@ -313,42 +313,50 @@ bool zws_input_map(CUtensorMap *out, const float2 *S, int Kx, int Py, int nz, in
     return true;
 }
 
-template <int TC, bool EONLY = false>
+template <int L, int TC, bool EONLY = false>
 cudaError_t zws_launch(float2 *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows, const float *ntile,
                        const float2 *tw, cudaStream_t st, double *partials = nullptr, int *nparts = nullptr)
 {
-    using Sh = ZwsShape<512, TC>;
+    using Sh = ZwsShape<L, TC>;
     CUtensorMap map;
-    if (!zws_input_map<512, TC>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
-    const size_t sm = zws_smem_bytes<512, TC>(nrows);
+    if (!zws_input_map<L, TC>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
+    const size_t sm = zws_smem_bytes<L, TC>(nrows);
     if (sm > 227 * 1024) return cudaErrorNotSupported;
-    cudaError_t e = allow_smem<k_z_ws<512, TC, EONLY>>(sm);
+    cudaError_t e = allow_smem<k_z_ws<L, TC, EONLY>>(sm);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + TC - 1) / TC;
     const int ntiles = ntx * Py;
-    const int cap = sm_count() * resident_ctas<k_z_ws<512, TC, EONLY>>(Sh::NT, sm);
+    const int cap = sm_count() * resident_ctas<k_z_ws<L, TC, EONLY>>(Sh::NT, sm);
     const int grid = ntiles < cap ? ntiles : cap;
     if (nparts) *nparts = grid;
-    k_z_ws<512, TC, EONLY><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx, ntiles,
-                                                     partials);
+    k_z_ws<L, TC, EONLY><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx, ntiles,
+                                                   partials);
     return cudaGetLastError();
+}
+
+// Arguments the persistent z pass takes (TMA alignment, at most L/2 rows).
+bool zws_ok(int L, const void *S, const void *ntile, int nrows, int64_t ss, int64_t rs, int64_t cs, size_t csize)
+{
+    return (L == 256 || L == 512) && ntile && nrows >= 1 && 2 * nrows <= L && ((uintptr_t)S & 15) == 0 &&
+           ((uintptr_t)ntile & 15) == 0 && (ss * (int64_t)csize) % 16 == 0 && (rs * (int64_t)csize) % 16 == 0 &&
+           (cs * (int64_t)csize) % 16 == 0;
 }
 }  // namespace
 
 template <typename T>
 size_t Passes<T>::tile_tensor_elems(int L, int Py, int Kx)
 {
-    if (sizeof(T) != 4 || L != 512) return 0;
-    return (size_t)(Py / 2 + 1) * zws_ntx4(Kx) * ZwsShape<512, 4>::TZB;
+    if (sizeof(T) != 4 || (L != 256 && L != 512)) return 0;
+    return (size_t)(Py / 2 + 1) * zws_ntx4(Kx) * 24 * (L / 2 + 1);  // [hy][ntx4][6][HZ][4]
 }
 
 template <typename T>
 cudaError_t Passes<T>::tile_tensor(int L, const T *nhat, T *ntile, int Py, int Kx, cudaStream_t st)
 {
-    if (sizeof(T) != 4 || L != 512) return cudaErrorNotSupported;
     const size_t n = tile_tensor_elems(L, Py, Kx);
+    if (n == 0) return cudaErrorNotSupported;
     const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 16);
-    k_tile_tensor<T><<<grid, 256, 0, st>>>(nhat, ntile, Kx, Py / 2 + 1, ZwsShape<512, 4>::HZ, zws_ntx4(Kx));
+    k_tile_tensor<T><<<grid, 256, 0, st>>>(nhat, ntile, Kx, Py / 2 + 1, L / 2 + 1, zws_ntx4(Kx));
     return cudaGetLastError();
 }
 
@@ -359,11 +367,12 @@ cudaError_t Passes<T>::zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t
     if constexpr (sizeof(T) != 4) {
         return cudaErrorNotSupported;
     } else {
-        if (L != 512 || !ntile || nrows < 1 || 2 * nrows > L || ((uintptr_t)S & 15) || ((uintptr_t)ntile & 15) ||
-            (ss * (int64_t)sizeof(C)) % 16 || (rs * (int64_t)sizeof(C)) % 16 || (cs * (int64_t)sizeof(C)) % 16)
-            return cudaErrorNotSupported;
-        return tc == 4 ? zws_launch<4>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st)
-                       : zws_launch<8>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st);
+        if (!zws_ok(L, S, ntile, nrows, ss, rs, cs, sizeof(C))) return cudaErrorNotSupported;
+        if (L == 256)
+            return tc == 4 ? zws_launch<256, 4>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st)
+                           : zws_launch<256, 8>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st);
+        return tc == 4 ? zws_launch<512, 4>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st)
+                       : zws_launch<512, 8>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st);
     }
 }
 
@@ -375,11 +384,12 @@ cudaError_t Passes<T>::zconv_ws_energy(int L, C *S, int Kx, int Py, int64_t ss, 
     if constexpr (sizeof(T) != 4) {
         return cudaErrorNotSupported;
     } else {
-        if (L != 512 || !ntile || nrows < 1 || 2 * nrows > L || ((uintptr_t)S & 15) || ((uintptr_t)ntile & 15) ||
-            (ss * (int64_t)sizeof(C)) % 16 || (rs * (int64_t)sizeof(C)) % 16 || (cs * (int64_t)sizeof(C)) % 16)
-            return cudaErrorNotSupported;
-        return tc == 4 ? zws_launch<4, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts)
-                       : zws_launch<8, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts);
+        if (!zws_ok(L, S, ntile, nrows, ss, rs, cs, sizeof(C))) return cudaErrorNotSupported;
+        if (L == 256)
+            return tc == 4 ? zws_launch<256, 4, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts)
+                           : zws_launch<256, 8, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts);
+        return tc == 4 ? zws_launch<512, 4, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts)
+                       : zws_launch<512, 8, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts);
     }
 }
 

@@ -88,8 +88,8 @@ template <typename T> struct Passes {
     static cudaError_t zconv(int L, C *S, int ncols, int width, int64_t ss, int64_t rs, int64_t cs,
                              int nrows, const T *nhat, int Py, int Kx, const C *tw, int twstride,
                              cudaStream_t st, int variant = 0);
-    // persistent z pass streaming column tiles by TMA (FP32, L = 512, at most
-    // L/2 input rows); ntile: the tile-ordered tensor copy (tile_tensor); tc:
+    // persistent z pass streaming column tiles by TMA (FP32, L = 256 or 512, at
+    // most L/2 input rows); ntile: the tile-ordered tensor copy (tile_tensor); tc:
     // columns per tile, 8 (one CTA per SM) or 4 (two CTAs per SM).
     // cudaErrorNotSupported when the arguments do not allow it.
     static cudaError_t zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,

@@ -141,6 +141,38 @@ __device__ __forceinline__ void dft16(float2 (&v)[16])
         for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
 }
 
+// 16-point forward DFT of v[0..7] (v[8..15] are zero padding): the first
+// level's 4-point DFTs see two non-zero inputs each.
+__device__ __forceinline__ void dft16_half_in(float2 (&v)[16])
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        const float2 a0 = v[n2], a1 = v[n2 + 4];
+        v[n2] = add(a0, a1);
+        v[n2 + 4] = add_mi(a0, a1);
+        v[n2 + 8] = sub(a0, a1);
+        v[n2 + 12] = add_pi(a0, a1);
+    }
+    v[5] = tw<16, 1, false>(v[5]);
+    v[9] = tw<16, 2, false>(v[9]);
+    v[13] = tw<16, 3, false>(v[13]);
+    v[6] = tw<16, 2, false>(v[6]);
+    v[10] = tw<16, 4, false>(v[10]);
+    v[14] = tw<16, 6, false>(v[14]);
+    v[7] = tw<16, 3, false>(v[7]);
+    v[11] = tw<16, 6, false>(v[11]);
+    v[15] = tw<16, 9, false>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<false>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    float2 t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 // 16-point inverse DFT of which only the outputs 0..7 are formed (into
 // v[0..7]); v[8..15] are left undefined.
 __device__ __forceinline__ void idft16_lo(float2 (&v)[16])
@@ -246,12 +278,17 @@ __device__ __forceinline__ void product(float2 &mx, float2 &my, float2 &mz, floa
 // columns ([6][HZ][4] floats each, TZB floats), laid TZS floats apart in
 // shared memory (TZS = 16 mod 32 banks: the two sub-blocks of an 8-column
 // tile fall in different bank halves).
-template <int L, int TC> struct ZwsShape;
-template <int TC> struct ZwsShape<512, TC> {
+// L = 512 runs as 2 x 16 x 16 (R1 = 32: a 32-point stage whose input half is
+// padding, done as two 16-point DFTs), L = 256 as 16 x 16 (R1 = 16: a
+// 16-point stage on 8 input rows). The exchange rows R1 j + k are padded by
+// one row every R1 rows (EXR rows per component).
+template <int L, int TC> struct ZwsShape {
+    static_assert(L == 256 || L == 512, "the persistent z pass is built for L = 256 and 512");
     static_assert(TC == 4 || TC == 8, "tile width 4 or 8");
-    static constexpr int NT = 32 * TC, HZ = 257, EXR = 528;  // EXR: rows per component with padding
-    static constexpr int TZB = 6 * HZ * 4, TZS = TZB + 24, NSUB = TC / 4;
-    static constexpr int MIN_CTAS = TC == 4 ? 2 : 1;
+    static constexpr int R1 = L / 16;
+    static constexpr int NT = R1 * TC, HZ = L / 2 + 1, EXR = L + 16;
+    static constexpr int TZB = 6 * HZ * 4, TZS = TZB + 24, NSUB = TC / 4;  // HZ odd: TZS = 16 mod 32
+    static constexpr int MIN_CTAS = (L == 512 && TC == 8) ? 1 : 2;
 };
 
 // Tile-ordered copy of the FP32 octant tensor spectrum for the persistent z
@@ -288,7 +325,7 @@ __host__ __device__ inline size_t zws_smem_bytes(int nrows)
     return 128 + stg + ex + tz + 2 * sizeof(uint64_t);
 }
 
-// The persistent fused z pass (L = 512, FP32). Tile t covers the columns
+// The persistent fused z pass (L = 256 or 512, FP32). Tile t covers the columns
 // kx = kxt TC .. kxt TC + TC - 1 (kxt = t % ntx) of the ky row
 // ky_pair_order(t / ntx), so that the two ky rows sharing a folded tensor
 // block are processed at about the same time. map: S2 [3][nz][Py][Kxp] as
@@ -305,9 +342,9 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
        int64_t cs, int nrows, const float *__restrict__ ntile, const float2 *__restrict__ twg, int ntx, int ntiles,
        double *__restrict__ partials = nullptr)
 {
-    static_assert(L == 512, "the persistent z pass is built for L = 512");
     using Sh = ZwsShape<L, TC>;
     constexpr int NT = Sh::NT, HZ = Sh::HZ, EXR = Sh::EXR, TZB = Sh::TZB, TZS = Sh::TZS, NSUB = Sh::NSUB;
+    constexpr int R1 = Sh::R1, RP = R1 + 1;  // stage-1 radix; padded row stride of the row groups
     constexpr unsigned TZ_BYTES = (unsigned)(NSUB * TZB * sizeof(float));
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char *base = smraw + ((128 - (smem_u32(smraw) & 127)) & 127);
@@ -366,10 +403,12 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
         const int ky = tile_ky(t), kx0 = (t % ntx) * TC;
         if (!mbar_wait_bounded(&bar[0], par, kPipeWaitCycles)) s_fail = 1;
 
-        // ---- stage 1: rows j1 + 16 r (r < 16; the upper half is padding) ->
-        // 32-point DFT outputs 2m + p at rows 32 j1 + 2m + p (p = 0 even, 1 odd)
+        // ---- stage 1. L = 512: rows j1 + 16 r (r < 16; the upper half is
+        // padding) -> 32-point DFT outputs 2m + p at rows 32 j1 + 2m + p
+        // (p = 0 even, 1 odd). L = 256: rows j1 + 16 r (r < 8) -> 16-point
+        // DFT outputs at rows 16 j1 + m.
         {
-            const int j1 = (tid / TC) & 15, p = tid / (16 * TC);
+            const int j1 = (tid / TC) & 15, p = L == 512 ? tid / (16 * TC) : 0;
             // the three components' loads first, then their transforms
             float2 v[3][16];
 #pragma unroll
@@ -377,15 +416,22 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 const float2 *src = stg + ((size_t)comp * nrows + j1) * TC + c;
 #pragma unroll
                 for (int r = 0; r < 16; ++r)
-                    v[comp][r] = j1 + 16 * r < nrows ? src[16 * r * TC] : make_float2(0.f, 0.f);
+                    v[comp][r] = (r < L / 32 && j1 + 16 * r < nrows) ? src[16 * r * TC] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
-                if (p) zw::tw32_half(v[comp]);
-                zw::dft16<false>(v[comp]);
-                float2 *dst = ex + ((size_t)comp * EXR + 33 * j1 + p) * TC + c;
+                if constexpr (L == 512) {
+                    if (p) zw::tw32_half(v[comp]);
+                    zw::dft16<false>(v[comp]);
+                    float2 *dst = ex + ((size_t)comp * EXR + RP * j1 + p) * TC + c;
 #pragma unroll
-                for (int m = 0; m < 16; ++m) dst[2 * m * TC] = v[comp][m];
+                    for (int m = 0; m < 16; ++m) dst[2 * m * TC] = v[comp][m];
+                } else {
+                    zw::dft16_half_in(v[comp]);
+                    float2 *dst = ex + ((size_t)comp * EXR + RP * j1) * TC + c;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) dst[m * TC] = v[comp][m];
+                }
             }
         }
         __syncthreads();  // staging buffer consumed, exchange written
@@ -404,16 +450,16 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
             issue_in(next);
         }
 
-        // ---- stage 2: rows 32 r + j2 of the three components: twiddle,
-        // 16-point DFTs (kz = j2 + 32 m), product, inverse DFTs, in place
+        // ---- stage 2: rows R1 r + j2 of the three components: twiddle,
+        // 16-point DFTs (kz = j2 + R1 m), product, inverse DFTs, in place
         {
             float2 a[16], b[16], d[16];
             const float2 *s = ex + (size_t)j2 * TC + c;
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
-                a[r] = s[33 * r * TC];
-                b[r] = s[(EXR + 33 * r) * TC];
-                d[r] = s[(2 * EXR + 33 * r) * TC];
+                a[r] = s[RP * r * TC];
+                b[r] = s[(EXR + RP * r) * TC];
+                d[r] = s[(2 * EXR + RP * r) * TC];
             }
 #pragma unroll
             for (int r = 1; r < 16; ++r) {
@@ -433,7 +479,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                     constexpr bool SN = decltype(syneg)::value;
 #pragma unroll
                     for (int m = 0; m < 16; ++m) {
-                        const int kzf = m < 8 ? j2 + 32 * m : (m == 8 ? 256 - j2 : 512 - j2 - 32 * m);
+                        const int kzf = m < 8 ? j2 + R1 * m : (m == 8 ? L / 2 - j2 : L - j2 - R1 * m);
                         const float *q = tb + kzf * 4;
                         float txz = q[4 * HZ * 4], tyz = q[5 * HZ * 4];
                         if (m == 8) {
@@ -455,7 +501,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 constexpr bool SN = decltype(syneg)::value;
 #pragma unroll
                 for (int m = 0; m < 16; ++m) {
-                    const int kzf = m < 8 ? j2 + 32 * m : (m == 8 ? 256 - j2 : 512 - j2 - 32 * m);
+                    const int kzf = m < 8 ? j2 + R1 * m : (m == 8 ? L / 2 - j2 : L - j2 - R1 * m);
                     const float *q = tb + kzf * 4;
                     float txz = q[4 * HZ * 4], tyz = q[5 * HZ * 4];
                     if (m == 8) {
@@ -483,9 +529,9 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
             float2 *o = ex + (size_t)j2 * TC + c;
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
-                o[33 * r * TC] = a[r];
-                o[(EXR + 33 * r) * TC] = b[r];
-                o[(2 * EXR + 33 * r) * TC] = d[r];
+                o[RP * r * TC] = a[r];
+                o[(EXR + RP * r) * TC] = b[r];
+                o[(2 * EXR + RP * r) * TC] = d[r];
             }
             }  // !EONLY
         }
@@ -507,24 +553,44 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
 
         if constexpr (EONLY) continue;  // no inverse transforms
 
-        // ---- stage 3: rows 32 n1 + k1 (k1 < 32, already twiddled by
-        // W_L^-(n1 k1) in stage 2), 32-point inverse DFT, outputs
-        // z = n1 + 16 n2 < nz to global memory
+        // ---- stage 3: rows R1 n1 + k1 (k1 < R1, already twiddled by
+        // W_L^-(n1 k1) in stage 2), R1-point inverse DFT of which the outputs
+        // n2 < R1/2 are formed: z = n1 + 16 n2 < nz to global memory
+        if constexpr (L == 512) {
 #pragma unroll 1
-        for (int b = tid; b < 3 * 16 * TC; b += NT) {
-            const int comp = b / (16 * TC), n1 = (b / TC) & 15;
-            float2 u[32];
-            const float2 *s = ex + ((size_t)comp * EXR + 33 * n1) * TC + c;
+            for (int b = tid; b < 3 * 16 * TC; b += NT) {
+                const int comp = b / (16 * TC), n1 = (b / TC) & 15;
+                float2 u[32];
+                const float2 *s = ex + ((size_t)comp * EXR + RP * n1) * TC + c;
 #pragma unroll
-            for (int k1 = 0; k1 < 32; ++k1) u[k1] = s[k1 * TC];
-            float2 y[16];
-            zw::idft32_lo(u, y);
-            if (kx0 + c < Kx) {
-                float2 *col = S + (int64_t)comp * cs + (int64_t)ky * ss + kx0 + c;
+                for (int k1 = 0; k1 < 32; ++k1) u[k1] = s[k1 * TC];
+                float2 y[16];
+                zw::idft32_lo(u, y);
+                if (kx0 + c < Kx) {
+                    float2 *col = S + (int64_t)comp * cs + (int64_t)ky * ss + kx0 + c;
 #pragma unroll
-                for (int n2 = 0; n2 < 16; ++n2) {
-                    const int z = n1 + 16 * n2;
-                    if (z < nrows) col[(int64_t)z * rs] = y[n2];
+                    for (int n2 = 0; n2 < 16; ++n2) {
+                        const int z = n1 + 16 * n2;
+                        if (z < nrows) col[(int64_t)z * rs] = y[n2];
+                    }
+                }
+            }
+        } else {
+            const int n1 = tid / TC;
+#pragma unroll 1
+            for (int comp = 0; comp < 3; ++comp) {
+                float2 u[16];
+                const float2 *s = ex + ((size_t)comp * EXR + RP * n1) * TC + c;
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) u[k1] = s[k1 * TC];
+                zw::idft16_lo(u);
+                if (kx0 + c < Kx) {
+                    float2 *col = S + (int64_t)comp * cs + (int64_t)ky * ss + kx0 + c;
+#pragma unroll
+                    for (int n2 = 0; n2 < 8; ++n2) {
+                        const int z = n1 + 16 * n2;
+                        if (z < nrows) col[(int64_t)z * rs] = u[n2];
+                    }
                 }
             }
         }

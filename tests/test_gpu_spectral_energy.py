@@ -37,6 +37,7 @@ SHAPES = [
     (33, 17, 5),     # ragged
     (9, 17, 129),    # Pz = 512: persistent TMA kernel (FP32) / two-stage (FP64)
     (40, 6, 200),
+    (40, 6, 100),    # Pz = 256: persistent TMA kernel at L = 256 (FP32)
 ]
 
 

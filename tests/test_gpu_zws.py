@@ -5,7 +5,8 @@ against the FP64 oracle element by element (rel-max <= 1e-5), against the
 two-stage z kernel (variant 0) on the same plan, and on the edge cases of its
 tiling: ragged column tiles (Kx not a multiple of 8), nz below L/2, one ky
 row (Py = 1), the fold of ky and kz at their Nyquist rows, and plans that
-cannot take it (Px = 1, FP64) falling back to the two-stage kernel."""
+cannot take it (Px = 1, FP64) falling back to the two-stage kernel; z
+lengths 512 (2 x 16 x 16) and 256 (16 x 16)."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,7 @@ def _relmax(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-# (nx, ny, nz) with Pz = 512: every grid has 129 <= nz <= 256
+# (nx, ny, nz) with Pz = 512 (129 <= nz <= 256) and Pz = 256 (65 <= nz <= 128)
 SHAPES = [
     (9, 17, 129),    # Kx = 17: three tiles, the last with one column; Py = 64
     (5, 3, 256),     # nz = L/2 exactly; Kx = 9: a tile of one column
@@ -36,6 +37,11 @@ SHAPES = [
     (33, 1, 256),    # Py = 1: one ky row
     (16, 2, 140),    # Py = 4: ky = Py/2 on the fold
     (7, 30, 255),    # odd sizes
+    (9, 17, 65),     # L = 256 from here
+    (5, 3, 128),
+    (20, 12, 100),
+    (33, 1, 128),
+    (7, 30, 127),
 ]
 
 
@@ -102,6 +108,27 @@ def test_plans_the_persistent_pass_cannot_take_fall_back(n, prec):
         p.set_variants(zv, 0, 1)
         H = p.field(torch.tensor(M, dtype=dt, device="cuda")).double().cpu().numpy()
         assert _relmax(H, Href) <= (1e-5 if prec == "f32" else 1e-12)
+    p.close()
+
+
+def test_persistent_z_pass_large_cuboid_against_two_stage_kernel():
+    """512 x 512 x 128 (padded 1024 x 1024 x 256, the large workload): L = 256
+    forms against the two-stage kernel on the same plan."""
+    from paper_1204_4302_gb300.plan import Plan
+    n, d = (512, 512, 128), (1e-9, 1e-9, 1e-9)
+    g = torch.Generator(device="cuda").manual_seed(6)
+    M = torch.randn(3, 128, 512, 512, device="cuda", generator=g)
+    M = 8e5 * M / M.norm(dim=0, keepdim=True)
+    p = Plan(n, d, prec="f32")
+    p.set_variants(0, 2, 1)
+    H0, E0 = p.field_energy(M)
+    for zv in (6, 7):
+        p.set_variants(zv, 2, 1)
+        H6, E6 = p.field_energy(M)
+        rel = float((H6 - H0).abs().max() / H0.abs().max())
+        assert rel <= 2e-6, (zv, rel)
+        assert abs(E6.item() - E0.item()) <= 1e-5 * abs(E0.item())
+    p.check_pipeline()
     p.close()
 
 
