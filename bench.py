@@ -269,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
         del mi
 
     t0 = time.perf_counter()
-    plan = Plan(n, CELL, prec="f32", device=dev)
+    plan = Plan(n, CELL, prec="f32", device=dev, pad=None if args.pad == "pow2" else args.pad)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     if args.variants:
@@ -732,6 +732,39 @@ def run_batch(args, dev, rank, peak):
     e1.synchronize()
     b.status()
     ms_call = e0.elapsed_time(e1) / k
+    def time_modes():
+        """Every batch mode timed on the batch's current padding, the
+        pass-batched mode's per-pass event times; the tuned mode restored."""
+        tuned_mode = b.info()["mode"]
+        mode_ms = {}
+        for mode, name in ((0, "persistent"), (2, "pass_batched"), (1, "branches")):
+            try:
+                b.set_mode(mode)
+            except B.DemagError:
+                continue
+            for _ in range(3):
+                B.demag_batch_field(b.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+            e0.record(st)
+            for _ in range(k):
+                B.demag_batch_field(b.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+            e1.record(st)
+            e1.synchronize()
+            mode_ms[name] = round(e0.elapsed_time(e1) / k, 4)
+        pass_times = None
+        try:
+            b.set_mode(2)
+            b.set_timing(True)
+            for _ in range(k):
+                B.demag_batch_field(b.handle, mp, hp, E.data_ptr(), st.cuda_stream)
+            tms, calls = b.get_timing()
+            b.set_timing(False)
+            pass_times = [t / max(calls, 1) for t in tms]
+        except B.DemagError:
+            pass
+        b.set_mode(tuned_mode)
+        return mode_ms, pass_times
+
+    modes_pow2 = time_modes()
     launches_per_call = (b.launch_count() - l0) / k
     cells_total = sum(a * bb * c for a, bb, c in dims)
     info = b.info()
@@ -750,6 +783,7 @@ def run_batch(args, dev, rank, peak):
     b.status()
     ms_autotuned = e0.elapsed_time(e1) / k
     mode_autotuned = b.info()["mode"]
+    modes_kept = time_modes()
     # the per-state padding tuner (each state's lengths timed alone; no cache)
     ms_pad = {}
     for pad in ("tuned",):
@@ -776,19 +810,43 @@ def run_batch(args, dev, rank, peak):
         os.environ.pop("DEMAG_TUNE_CACHE", None)
     else:
         os.environ["DEMAG_TUNE_CACHE"] = saved_cache
-    # algorithmic bytes of every pass of every state at the kept padding
+    # algorithmic bytes of every pass of every state (kept padding: the whole
+    # call's fraction; power-of-two padding: the pass-batched per-pass ones)
+    def batch_bytes(pad_mode):
+        tot = 0
+        per = {nm: 0 for nm in PASS_NAMES[:5]}
+        for nn in dims:
+            pbs = pass_bytes(nn, tuple(B.demag_padded_lengths(*nn, pad_mode=pad_mode)), 4)
+            tot += sum(pbs.values())
+            for nm in per:
+                per[nm] += pbs[nm]
+        return tot, per
+
     kept_mode = B.DEMAG_PAD_SMOOTH if pad_smooth < pad_pow2 else B.DEMAG_PAD_POW2
-    bytes_total = 0
-    for nn in dims:
-        Pst = tuple(B.demag_padded_lengths(*nn, pad_mode=kept_mode))
-        bytes_total += sum(pass_bytes(nn, Pst, 4).values())
+    bytes_total, _ = batch_bytes(kept_mode)
     gbs_call = bytes_total / (ms_autotuned * 1e-3) / 1e9
+    mode_ms_pow2, pass_times = modes_pow2
+    mode_ms_kept, _ = modes_kept
+    passes_batched = None
+    if pass_times:
+        bytes_p2, bytes_pass = batch_bytes(B.DEMAG_PAD_POW2)
+        passes_batched = {"padding": "pow2"}
+        for i, nm in enumerate(PASS_NAMES[:5]):
+            t = pass_times[i]
+            gbs = bytes_pass[nm] / (t * 1e-3) / 1e9
+            passes_batched[nm] = {"ms": round(t, 4), "bytes": bytes_pass[nm], "gbs": round(gbs, 1),
+                                  "frac": round(gbs / peak, 3)}
+        passes_batched["energy"] = {"ms": round(pass_times[5], 4)}
+        tp2 = sum(pass_times)
+        passes_batched["whole_call_frac"] = round(bytes_p2 / (tp2 * 1e-3) / 1e9 / peak, 3)
     out = {"workload": "64 states, 32..128 x 32..128 x 8..32 cells of 3 nm, FP32, field + energy",
            "cells": cells_total,
            "hbm": {"bytes_per_call": bytes_total, "gbs": round(gbs_call, 1),
                    "frac_whole_call": round(gbs_call / peak, 3),
-                   "note": "all passes of all states over the batch call's time (the states' passes run "
-                           "concurrently, so no single-pass times exist)"}, "mode": "persistent" if mode_autotuned == 0 else "graph branches",
+                   "note": "all passes of all states over the kept mode's time per call"},
+           "ms_per_call_by_mode_pow2_padding": mode_ms_pow2,
+           "ms_per_call_by_mode_kept_padding": mode_ms_kept,
+           "passes_pass_batched": passes_batched, "mode": {0: "persistent", 1: "graph branches", 2: "pass-batched launches"}[mode_autotuned],
            "padding": "smooth" if pad_smooth < pad_pow2 else "pow2",
            # the configuration the autotuners keep (modes, then padding)
            "ms_per_call": round(ms_autotuned, 4), "cells_per_s": cells_total / (ms_autotuned / 1e3),
@@ -1105,14 +1163,18 @@ def main():
     ap.add_argument("--skip-sp", action="store_true", help="skip the scalar-potential method leg")
     ap.add_argument("--skip-tg", action="store_true", help="skip the tensor-grid method leg")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants (for profiling runs)")
+    ap.add_argument("--pad", choices=["pow2", "smooth"], default="pow2",
+                    help="padded lengths of the headline plan (smooth: mixed-radix passes; for profiling runs)")
     ap.add_argument("--variants", default="", help="fixed z,y,x kernel variants instead of autotuning")
-    ap.add_argument("--grid", type=int, default=0, help="cubic grid edge (default 256, the headline)")
+    ap.add_argument("--grid", default="", help="grid edge n (cubic) or nx,ny,nz (default 256^3, the headline; "
+                                               "other grids are for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     global N_GRID
     if args.grid:
-        N_GRID = (args.grid,) * 3
+        g = [int(v) for v in args.grid.split(",")]
+        N_GRID = tuple(g) if len(g) == 3 else (g[0],) * 3
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

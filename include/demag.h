@@ -346,9 +346,20 @@ demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, 
 demag_status demag_batch_field(demag_batch_t batch, const void *const *M, void *const *H, double *E_dev,
                                void *stream);
 
-/* 0 = persistent kernel (DEMAG_ERR_UNSUPPORTED if not available), 1 = graph
- * of per-state branches. */
+/* 0 = persistent kernel, 2 = pass-batched launches (one launch per pass
+ * over all states, the six captured in one graph; the default where
+ * available), both DEMAG_ERR_UNSUPPORTED if the batch's sizes are outside
+ * their tile functions (FP32, power-of-two lengths, x <= 1024, y <= 512,
+ * z <= 256); 1 = graph of per-state branches. */
 demag_status demag_batch_set_mode(demag_batch_t batch, int mode);
+
+/* Per-pass timing of the pass-batched mode: with enable != 0 each call
+ * launches the six passes directly with a CUDA event around each and waits
+ * for them; demag_batch_get_timing adds up ms[k] per pass (k: x forward,
+ * y forward, z, y inverse, x inverse, energy) over *calls calls since the
+ * last demag_batch_set_timing. Other modes do not record. */
+demag_status demag_batch_set_timing(demag_batch_t batch, int enable);
+demag_status demag_batch_get_timing(demag_batch_t batch, double *ms, long *calls);
 
 /* Limit of each dependency wait of the persistent kernel, in seconds of GPU
  * clock (default about 2 s; normal waits take microseconds). stall_state >= 0

@@ -10,6 +10,7 @@ from . import binding as B
 class Batch:
     PERSISTENT = 0
     BRANCHES = 1
+    PASSES = 2
 
     PAD = {None: None, "pow2": 0, "smooth": 1, "tuned": 2}
 
@@ -47,8 +48,9 @@ class Batch:
         return Hs, E
 
     def autotune(self, use_cache: bool = True):
-        """Tune every state's plan and choose the faster batch mode; returns
-        (ms per call persistent, ms per call branches)."""
+        """Tune every state's plan and choose the fastest batch mode (persistent,
+        branches, pass-batched); returns (ms per call persistent, ms per call
+        branches)."""
         return B.demag_batch_autotune(self.handle, use_cache, torch.cuda.current_stream(self.device).cuda_stream)
 
     def autotune_padding(self, use_cache: bool = True):
@@ -67,6 +69,14 @@ class Batch:
 
     def info(self) -> dict:
         return B.demag_batch_info(self.handle)
+
+    def set_timing(self, enable: bool = True):
+        """Per-pass event timing of the pass-batched mode (see demag_batch_set_timing)."""
+        B.demag_batch_set_timing(self.handle, enable)
+
+    def get_timing(self):
+        """(ms per pass summed over the timed calls, number of calls)."""
+        return B.demag_batch_get_timing(self.handle)
 
     def launch_count(self) -> int:
         return B.demag_batch_launch_count(self.handle)

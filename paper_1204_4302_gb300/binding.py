@@ -44,6 +44,7 @@ EXPORTS = [
     "demag_plan_save", "demag_plan_load", "demag_debug_fail_alloc", "demag_field_energy_host_async",
     "demag_batch_autotune_padding",
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
+    "demag_batch_set_timing", "demag_batch_get_timing",
     "demag_batch_status", "demag_batch_info", "demag_batch_launch_count", "demag_batch_destroy",
     "demag_autotune", "demag_get_variants", "demag_set_variants", "demag_batch_autotune",
     "demag_set_spectral_energy",
@@ -110,6 +111,8 @@ def load(path: str | Path | None = None):
         "demag_plan_info": (S, [P, POINTER(demag_info)]),
         "demag_set_timing": (S, [P, I]),
         "demag_set_spectral_energy": (S, [P, I]),
+        "demag_batch_set_timing": (S, [P, I]),
+        "demag_batch_get_timing": (S, [P, POINTER(c_double), POINTER(c_long)]),
         "demag_set_graphs": (S, [P, I]),
         "demag_batch_autotune_padding": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
         "demag_field_energy_host_async": (S, [P, P, P, P, P]),
@@ -420,6 +423,17 @@ def demag_batch_info(batch) -> dict:
                                    ctypes.byref(grid), ctypes.byref(smem)), "demag_batch_info")
     return {"mode": mode.value, "persistent_ok": bool(ok.value), "items": items.value, "grid": grid.value,
             "smem": smem.value}
+
+
+def demag_batch_set_timing(batch, enable=True):
+    _check(load().demag_batch_set_timing(_p(batch), int(bool(enable))), "demag_batch_set_timing")
+
+
+def demag_batch_get_timing(batch):
+    ms = (c_double * 6)()
+    calls = c_long()
+    _check(load().demag_batch_get_timing(_p(batch), ms, ctypes.byref(calls)), "demag_batch_get_timing")
+    return list(ms), calls.value
 
 
 def demag_batch_launch_count(batch) -> int:

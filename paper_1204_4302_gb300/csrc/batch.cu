@@ -2,7 +2,7 @@
 // uneven sizes: every state has its own plan (geometry, tensor spectrum,
 // spectra), and one call evaluates all of them.
 //
-// Persistent mode (default when every state's sizes are supported): a single
+// Persistent mode: a single
 // kernel launch works through a queue of (pass, state, tile) items in
 // pass-major order. An item of pass p waits until all tiles of pass p - 1 of
 // its state are done (per-(pass, state) completion counters). Waits are
@@ -12,12 +12,20 @@
 // wrote them. The counter reset and the launch are captured once in a CUDA
 // graph that each call replays.
 //
+// Pass-batched mode (the default where the persistent tile functions cover
+// every state): one launch per pass covers that pass's tiles of every state,
+// the six launches are captured once into a CUDA graph and replayed; the
+// stream order of the launches replaces the persistent kernel's waits, and
+// each launch holds only its own pass's tile functions (fewer registers, more
+// CTAs per SM than the single persistent kernel).
+//
 // Branch mode: each state's five-kernel pipeline is captured on its own
 // stream into one CUDA graph (independent branches run concurrently).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -145,11 +153,13 @@ __device__ void energy_tile(const BatchState &st)
     if (threadIdx.x == 0 && st.E) *st.E = st.efactor * (ss[0] + sc[0]);
 }
 
-__device__ void run_item(const BatchState &st, int pass, int tile, unsigned char *sm)
+template <int PASS>
+__device__ __forceinline__ void run_item_t(const BatchState &st, int tile, unsigned char *sm)
 {
     const int nx = st.nx, ny = st.ny, nz = st.nz, Px = st.Px, Py = st.Py, Pz = st.Pz, Kx = st.Kx, Kxp = st.Kxp;
     const int rows = 3 * nz * ny;
-    switch (pass) {
+    (void)rows; (void)Pz; (void)nx;
+    switch (PASS) {
     case 0: {
         XIn<float> a;
         a.in = st.M; a.in_rs = nx; a.wcell = nullptr; a.wscalar = 1.f; a.rows_per_comp = nz * ny;
@@ -165,7 +175,7 @@ __device__ void run_item(const BatchState &st, int pass, int tile, unsigned char
     }
     case 1:
     case 3: {
-        const bool inv = pass == 3;
+        const bool inv = PASS == 3;
         const float2 *in = inv ? st.S2 : st.S1;
         float2 *out = inv ? st.S1 : st.S2;
         const int64_t iss = inv ? (int64_t)Py * Kxp : (int64_t)ny * Kxp, oss = inv ? (int64_t)ny * Kxp : (int64_t)Py * Kxp;
@@ -225,6 +235,82 @@ __device__ void run_item(const BatchState &st, int pass, int tile, unsigned char
         energy_tile(st);
         break;
     }
+}
+
+__device__ void run_item(const BatchState &st, int pass, int tile, unsigned char *sm)
+{
+    switch (pass) {
+    case 0: run_item_t<0>(st, tile, sm); break;
+    case 1: run_item_t<1>(st, tile, sm); break;
+    case 2: run_item_t<2>(st, tile, sm); break;
+    case 3: run_item_t<3>(st, tile, sm); break;
+    case 4: run_item_t<4>(st, tile, sm); break;
+    case 5: run_item_t<5>(st, tile, sm); break;
+    }
+}
+
+// One tile of pass PASS for a state whose transform length of that pass is
+// the compile-time L (x: Px/2, y: Py, z: Pz).
+template <int PASS, int L>
+__device__ __forceinline__ void run_item_L(const BatchState &st, int tile, unsigned char *sm)
+{
+    const int nx = st.nx, ny = st.ny, nz = st.nz, Px = st.Px, Py = st.Py, Pz = st.Pz, Kx = st.Kx, Kxp = st.Kxp;
+    const int rows = 3 * nz * ny;
+    (void)Px; (void)Pz;
+    if constexpr (PASS == 0) {
+        XIn<float> a;
+        a.in = st.M; a.in_rs = nx; a.wcell = nullptr; a.wscalar = 1.f; a.rows_per_comp = nz * ny;
+        if constexpr (L <= 32) k_x_fwd_tile<float, L, false>(a, rows, nx, st.S1, Kxp, st.tw[0], tile, sm);
+        else k_x_fwd2_tile<float, L, true, false>(a, rows, nx, st.S1, Kxp, st.tw[0], tile, sm);
+    } else if constexpr (PASS == 1 || PASS == 3) {
+        constexpr bool inv = PASS == 3;
+        const float2 *in = inv ? st.S2 : st.S1;
+        float2 *out = inv ? st.S1 : st.S2;
+        const int64_t iss = inv ? (int64_t)Py * Kxp : (int64_t)ny * Kxp, oss = inv ? (int64_t)ny * Kxp : (int64_t)Py * Kxp;
+        const int nin = inv ? Py : ny, nout = inv ? ny : Py;
+        const int ncols = 3 * nz * Kx;
+        if constexpr (L <= 16) {
+            k_col1_tile<float, L, inv, true>(in, out, ncols, Kx, iss, Kxp, nin, oss, Kxp, nout, tile, sm);
+        } else if constexpr (inv) {
+            k_col2_tile<float, L, true, false, true, true>(in, out, ncols, Kx, iss, Kxp, nin, oss, Kxp, nout, st.tw[1], 1,
+                                                           tile, sm);
+        } else {
+            k_col2_tile<float, L, false, true, false, true>(in, out, ncols, Kx, iss, Kxp, nin, oss, Kxp, nout, st.tw[1],
+                                                            1, tile, sm);
+        }
+    } else if constexpr (PASS == 2) {
+        const int ncols = Py * Kx;
+        const int64_t ss = Kxp, rs = (int64_t)Py * Kxp, cs = (int64_t)nz * Py * Kxp;
+        if constexpr (L <= 16) k_z_conv1_tile<float, L, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, tile, sm);
+        else k_z_conv2_tile<float, L, 0, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm);
+    } else if constexpr (PASS == 4) {
+        XOut<float> o;
+        o.out = st.H; o.out_rs = nx; o.scale = 1.f / ((float)Px * Py * Pz); o.oscale = 1.f; o.wcell = nullptr;
+        o.gdev = nullptr; o.Mref = st.M; o.mscale = 1.f; o.partials = st.partials; o.rows_per_comp = nz * ny;
+        if constexpr (L <= 32) k_x_inv_tile<float, L, true>(st.S1, Kxp, rows, nx, o, st.tw[0], tile, sm);
+        else k_x_inv2_tile<float, L, true>(st.S1, Kxp, rows, nx, o, st.tw[0], tile, sm);
+    } else {
+        energy_tile(st);
+    }
+}
+
+// Pass-batched mode: one launch of pass PASS per transform length L covers
+// that pass's tiles of every state with that length (CTA b: item b of the
+// group; its state by binary search of the group's prefix sums gstart over
+// its m states gstate). The launches follow one another on the stream, so no
+// dependency waits are needed, and each launch carries one tile function.
+template <int PASS, int L>
+__global__ void __launch_bounds__(kThreads) k_batch_pass(BatchDesc d, const int *__restrict__ gstate,
+                                                         const int *__restrict__ gstart, int m)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int item = blockIdx.x;
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {  // last group entry with start <= item
+        const int mid = (lo + hi + 1) >> 1;
+        if (gstart[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    run_item_L<PASS, L>(d.states[gstate[lo]], item - gstart[lo], smraw);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_batch(BatchDesc d)
@@ -308,6 +394,22 @@ struct demag_batch {
     long long timeout_cycles;
     bool states_dirty;
     cudaGraphExec_t pexec;
+    // pass-batched (one launch per pass and transform length over all states)
+    struct Group {
+        int pass, L, m, items;
+        size_t smem;
+        int off;  // into dgroups: m state indices, then m + 1 prefix sums
+    };
+    std::vector<Group> groups;
+    int *dgroups;
+    int pass_total[6];
+    double tuned_ms[3];  // last autotune: persistent, branches, pass-batched (1e30: not run)
+    size_t pass_smem[6];
+    cudaGraphExec_t qexec;
+    bool timing;
+    cudaEvent_t tev[7];
+    double pass_ms[6];
+    long pass_n;
     // branches
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
@@ -350,7 +452,10 @@ size_t field_bytes(const demag_plan_t p) { return 3 * (size_t)p->nx * p->ny * p-
 void free_batch(demag_batch *b)
 {
     if (b->pexec) cudaGraphExecDestroy(b->pexec);
+    if (b->qexec) cudaGraphExecDestroy(b->qexec);
     if (b->bexec) cudaGraphExecDestroy(b->bexec);
+    for (auto e : b->tev)
+        if (e) cudaEventDestroy(e);
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto e : b->events) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -361,6 +466,7 @@ void free_batch(demag_batch *b)
     cudaFree(b->derror);
     cudaFree(b->dE);
     cudaFree(b->dpartials);
+    cudaFree(b->dgroups);
     for (auto p : b->plans) demag_plan_destroy(p);
     delete b;
 }
@@ -419,6 +525,51 @@ demag_status build_persistent(demag_batch *b)
         b->hstart[k * (n + 1) + n] = acc;
     }
     b->total = acc;
+    for (int k = 0; k < demag::kPasses; ++k) {
+        b->pass_total[k] = b->hstart[k * (n + 1) + n] - b->hstart[k * (n + 1)];
+        b->pass_smem[k] = 0;
+        for (int i = 0; i < n; ++i)
+            if (geo[i].tiles[k] > 0 && geo[i].smem[k] > b->pass_smem[k]) b->pass_smem[k] = geo[i].smem[k];
+    }
+    // pass-batched groups: per pass, the states of one transform length
+    {
+        std::vector<int> host;
+        b->groups.clear();
+        for (int k = 0; k < demag::kPasses; ++k) {
+            std::vector<int> lens;
+            for (int i = 0; i < n; ++i) {
+                if (geo[i].tiles[k] <= 0) continue;
+                const demag_plan_t pl = b->plans[i];
+                const int L = (k == 0 || k == 4) ? pl->Px / 2 : (k == 1 || k == 3) ? pl->Py : (k == 2 ? pl->Pz : 0);
+                if (std::find(lens.begin(), lens.end(), L) == lens.end()) lens.push_back(L);
+            }
+            std::sort(lens.begin(), lens.end());
+            for (int L : lens) {
+                demag_batch::Group g;
+                g.pass = k; g.L = L; g.m = 0; g.items = 0; g.smem = 0;
+                g.off = (int)host.size();
+                std::vector<int> st, pre;
+                pre.push_back(0);
+                for (int i = 0; i < n; ++i) {
+                    if (geo[i].tiles[k] <= 0) continue;
+                    const demag_plan_t pl = b->plans[i];
+                    const int Li = (k == 0 || k == 4) ? pl->Px / 2 : (k == 1 || k == 3) ? pl->Py : (k == 2 ? pl->Pz : 0);
+                    if (Li != L) continue;
+                    st.push_back(i);
+                    pre.push_back(pre.back() + geo[i].tiles[k]);
+                    if (geo[i].smem[k] > g.smem) g.smem = geo[i].smem[k];
+                }
+                g.m = (int)st.size();
+                g.items = pre.back();
+                host.insert(host.end(), st.begin(), st.end());
+                host.insert(host.end(), pre.begin(), pre.end());
+                b->groups.push_back(g);
+            }
+        }
+        if (cudaMalloc(&b->dgroups, sizeof(int) * (host.size() + 1)) != cudaSuccess)
+            return bfail(DEMAG_ERR_OOM, "batch groups");
+        cudaMemcpy(b->dgroups, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice);
+    }
     if (cudaMalloc(&b->ds, sizeof(BatchState) * n) != cudaSuccess) return bfail(DEMAG_ERR_OOM, "batch states");
     if (cudaMalloc(&b->dstart, sizeof(int) * b->hstart.size()) != cudaSuccess) return bfail(DEMAG_ERR_OOM, "batch table");
     if (cudaMalloc(&b->dcounter, sizeof(int)) != cudaSuccess) return bfail(DEMAG_ERR_OOM, "batch counter");
@@ -493,6 +644,131 @@ demag_status launch_persistent(demag_batch *b, cudaStream_t st)
         }
     }
     cudaError_t e = cudaGraphLaunch(b->pexec, st);
+    if (e != cudaSuccess) return bfail(DEMAG_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+    b->launches += 1;
+    return DEMAG_OK;
+}
+
+template <int PASS, int L>
+cudaError_t group_launch(demag_batch *b, const BatchDesc &d, const demag_batch::Group &g, cudaStream_t st)
+{
+    static int done_for = -1;  // opt in to the per-block shared memory once per device
+    if (done_for != b->device) {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, demag::k_batch_pass<PASS, L>);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(demag::k_batch_pass<PASS, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+        done_for = b->device;
+    }
+    demag::k_batch_pass<PASS, L><<<g.items, demag::kThreads, g.smem, st>>>(d, b->dgroups + g.off,
+                                                                           b->dgroups + g.off + g.m, g.m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group(demag_batch *b, const BatchDesc &d, const demag_batch::Group &g, cudaStream_t st)
+{
+    if (g.items <= 0) return cudaSuccess;
+#define DEMAG_G(P, LL) \
+    case LL: return group_launch<P, LL>(b, d, g, st);
+    switch (g.pass) {
+    case 0:
+        switch (g.L) { DEMAG_G(0, 16) DEMAG_G(0, 32) DEMAG_G(0, 64) DEMAG_G(0, 128) DEMAG_G(0, 256) DEMAG_G(0, 512) }
+        break;
+    case 1:
+        switch (g.L) { DEMAG_G(1, 8) DEMAG_G(1, 16) DEMAG_G(1, 32) DEMAG_G(1, 64) DEMAG_G(1, 128) DEMAG_G(1, 256) DEMAG_G(1, 512) }
+        break;
+    case 2:
+        switch (g.L) { DEMAG_G(2, 4) DEMAG_G(2, 8) DEMAG_G(2, 16) DEMAG_G(2, 32) DEMAG_G(2, 64) DEMAG_G(2, 128) DEMAG_G(2, 256) }
+        break;
+    case 3:
+        switch (g.L) { DEMAG_G(3, 8) DEMAG_G(3, 16) DEMAG_G(3, 32) DEMAG_G(3, 64) DEMAG_G(3, 128) DEMAG_G(3, 256) DEMAG_G(3, 512) }
+        break;
+    case 4:
+        switch (g.L) { DEMAG_G(4, 16) DEMAG_G(4, 32) DEMAG_G(4, 64) DEMAG_G(4, 128) DEMAG_G(4, 256) DEMAG_G(4, 512) }
+        break;
+    case 5:
+        return group_launch<5, 0>(b, d, g, st);
+    }
+#undef DEMAG_G
+    return cudaErrorInvalidValue;
+}
+
+// The pass-batched launches on st, pass by pass (each pass's length groups
+// one after another); with timing, an event before each pass and after the
+// last (tev[0..6]).
+cudaError_t pass_launches(demag_batch *b, cudaStream_t st, bool events)
+{
+    BatchDesc d;
+    memset(&d, 0, sizeof d);
+    d.states = b->ds; d.n = b->n; d.start = b->dstart; d.total = b->total;
+    cudaError_t e = cudaSuccess;
+    size_t gi = 0;
+    for (int k = 0; k < demag::kPasses && e == cudaSuccess; ++k) {
+        if (events) cudaEventRecord(b->tev[k], st);
+        for (; gi < b->groups.size() && b->groups[gi].pass == k && e == cudaSuccess; ++gi)
+            e = launch_group(b, d, b->groups[gi], st);
+    }
+    if (events && e == cudaSuccess) cudaEventRecord(b->tev[6], st);
+    return e;
+}
+
+demag_status launch_passes(demag_batch *b, cudaStream_t st)
+{
+    const int n = b->n;
+    if (b->states_dirty) {
+        for (int i = 0; i < n; ++i) {
+            b->hs[i].M = (const float *)b->curM[i];
+            b->hs[i].H = (float *)b->curH[i];
+        }
+        cudaError_t e = cudaMemcpyAsync(b->ds, b->hs.data(), sizeof(BatchState) * n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return bfail(DEMAG_ERR_CUDA, std::string("batch states upload: ") + cudaGetErrorString(e));
+        b->states_dirty = false;
+    }
+    if (b->timing) {
+        // direct launches with an event around each pass, read at the next call
+        if (!b->tev[0])
+            for (auto &ev : b->tev)
+                if (cudaEventCreate(&ev) != cudaSuccess) return bfail(DEMAG_ERR_CUDA, "batch timing events");
+        cudaError_t e = pass_launches(b, st, true);
+        if (e != cudaSuccess) return bfail(DEMAG_ERR_CUDA, std::string("batch pass launch: ") + cudaGetErrorString(e));
+        cudaEventSynchronize(b->tev[6]);
+        for (int k = 0; k < demag::kPasses; ++k) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, b->tev[k], b->tev[k + 1]) == cudaSuccess) b->pass_ms[k] += ms;
+        }
+        b->pass_n += 1;
+        b->launches += (long)b->groups.size();
+        return DEMAG_OK;
+    }
+    if (!b->qexec) {
+        // a first run outside the capture (kernel attributes, lazy loading)
+        cudaError_t e = pass_launches(b, st, false);
+        if (e != cudaSuccess) return bfail(DEMAG_ERR_CUDA, std::string("batch pass launch: ") + cudaGetErrorString(e));
+        b->launches += (long)b->groups.size();
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return bfail(DEMAG_ERR_CUDA, "capture stream");
+        cudaStreamSynchronize(st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = pass_launches(b, cs, false);
+            e = cudaStreamEndCapture(cs, &g);
+            if (el != cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->qexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            b->qexec = nullptr;
+            return bfail(DEMAG_ERR_CUDA, std::string("batch pass graph: ") + cudaGetErrorString(e));
+        }
+        return DEMAG_OK;
+    }
+    cudaError_t e = cudaGraphLaunch(b->qexec, st);
     if (e != cudaSuccess) return bfail(DEMAG_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
     b->launches += 1;
     return DEMAG_OK;
@@ -602,7 +878,7 @@ demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, 
         free_batch(b);
         return s;
     }
-    b->mode = b->persistent_ok ? 0 : 1;
+    b->mode = b->persistent_ok ? 2 : 1;
     b->curM.assign(n, nullptr);
     b->curH.assign(n, nullptr);
     *out = b;
@@ -611,8 +887,8 @@ demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, 
 
 demag_status demag_batch_set_mode(demag_batch_t b, int mode)
 {
-    if (!b || (mode != 0 && mode != 1)) return bfail(DEMAG_ERR_INVALID_ARG, "bad batch or mode");
-    if (mode == 0 && !b->persistent_ok) return bfail(DEMAG_ERR_UNSUPPORTED, b->why_not_persistent);
+    if (!b || mode < 0 || mode > 2) return bfail(DEMAG_ERR_INVALID_ARG, "bad batch or mode");
+    if (mode != 1 && !b->persistent_ok) return bfail(DEMAG_ERR_UNSUPPORTED, b->why_not_persistent);
     b->mode = mode;
     return DEMAG_OK;
 }
@@ -669,7 +945,7 @@ demag_status demag_batch_field(demag_batch_t b, const void *const *M, void *cons
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (!b->dE && cudaMalloc(&b->dE, sizeof(double) * b->n) != cudaSuccess) return bfail(DEMAG_ERR_OOM, "batch energies");
-    demag_status s = b->mode == 0 ? launch_persistent(b, st) : launch_branches(b, st);
+    demag_status s = b->mode == 0 ? launch_persistent(b, st) : (b->mode == 2 ? launch_passes(b, st) : launch_branches(b, st));
     if (s != DEMAG_OK) return s;
     if (E_dev) {
         cudaError_t e = cudaMemcpyAsync(E_dev, b->dE, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, st);
@@ -708,6 +984,23 @@ demag_status demag_batch_info(demag_batch_t b, int *mode, int *persistent_ok, in
 
 long demag_batch_launch_count(demag_batch_t b) { return b ? b->launches : 0; }
 
+demag_status demag_batch_set_timing(demag_batch_t b, int enable)
+{
+    if (!b) return bfail(DEMAG_ERR_INVALID_ARG, "batch is NULL");
+    b->timing = enable != 0;
+    for (int k = 0; k < 6; ++k) b->pass_ms[k] = 0;
+    b->pass_n = 0;
+    return DEMAG_OK;
+}
+
+demag_status demag_batch_get_timing(demag_batch_t b, double *ms, long *calls)
+{
+    if (!b || !ms) return bfail(DEMAG_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 6; ++k) ms[k] = b->pass_ms[k];
+    if (calls) *calls = b->pass_n;
+    return DEMAG_OK;
+}
+
 demag_status demag_batch_autotune(demag_batch_t b, int use_cache, double *ms_persistent, double *ms_branches,
                                   void *stream)
 {
@@ -736,10 +1029,12 @@ demag_status demag_batch_autotune(demag_batch_t b, int use_cache, double *ms_per
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    double t[2] = {1e30, 1e30};
+    double t[3] = {1e30, 1e30, 1e30};
     demag_status rs = DEMAG_OK;
-    for (int mode = 0; mode < 2 && rs == DEMAG_OK; ++mode) {
-        if (mode == 0 && !b->persistent_ok) continue;
+    const bool timing = b->timing;
+    b->timing = false;
+    for (int mode = 0; mode < 3 && rs == DEMAG_OK; ++mode) {
+        if (mode != 1 && !b->persistent_ok) continue;
         b->mode = mode;
         for (int w = 0; w < 2 && rs == DEMAG_OK; ++w) rs = demag_batch_field(b, M.data(), H.data(), nullptr, stream);
         cudaEventRecord(e0, st);
@@ -752,9 +1047,14 @@ demag_status demag_batch_autotune(demag_batch_t b, int use_cache, double *ms_per
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    b->timing = timing;
     release();
     if (rs != DEMAG_OK) return rs;
-    b->mode = (b->persistent_ok && t[0] <= t[1]) ? 0 : 1;
+    int best = 1;
+    for (int m = 0; m < 3; ++m)
+        if (t[m] < t[best]) best = m;
+    b->mode = best;
+    b->tuned_ms[0] = t[0]; b->tuned_ms[1] = t[1]; b->tuned_ms[2] = t[2];
     if (ms_persistent) *ms_persistent = b->persistent_ok ? t[0] : -1.0;
     if (ms_branches) *ms_branches = t[1];
     return demag_batch_status(b, stream);
@@ -769,7 +1069,7 @@ demag_status demag_batch_autotune_padding(demag_batch_t b, int use_cache, double
     double tp = 0, tb = 0;
     demag_status s = demag_batch_autotune(b, use_cache, &tp, &tb, stream);
     if (s != DEMAG_OK) return s;
-    const double t_this = tp >= 0 && tp < tb ? tp : tb;
+    const double t_this = std::min(b->tuned_ms[0], std::min(b->tuned_ms[1], b->tuned_ms[2]));
     demag_options o;
     memset(&o, 0, sizeof o);
     o.pad_mode = b->pad_mode == DEMAG_PAD_POW2 ? DEMAG_PAD_SMOOTH : DEMAG_PAD_POW2;
@@ -781,7 +1081,7 @@ demag_status demag_batch_autotune_padding(demag_batch_t b, int use_cache, double
         free_batch(nb);
         return s;
     }
-    const double t_other = tp >= 0 && tp < tb ? tp : tb;
+    const double t_other = std::min(nb->tuned_ms[0], std::min(nb->tuned_ms[1], nb->tuned_ms[2]));
     const bool was_pow2 = b->pad_mode == DEMAG_PAD_POW2;
     if (ms_pow2) *ms_pow2 = was_pow2 ? t_this : t_other;
     if (ms_smooth) *ms_smooth = was_pow2 ? t_other : t_this;

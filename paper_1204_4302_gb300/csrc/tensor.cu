@@ -397,6 +397,21 @@ __global__ void k_wrap(const double *__restrict__ oct, int comp, int nx, int ny,
     }
 }
 
+// Largest |imaginary residue| of a block (256 threads) into *imag_max with
+// one atomic per block (non-negative doubles order like their bit patterns).
+__device__ __forceinline__ void block_max_to(double local, unsigned long long *imag_max)
+{
+    __shared__ double red[8];
+    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        atomicMax(imag_max, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 __global__ void k_extract(const double2 *__restrict__ S, int comp, int Kx, int Py, int Pz, int Kxp,
                           double *__restrict__ nhat64, float *__restrict__ nhat32,
                           unsigned long long *__restrict__ imag_max)
@@ -412,8 +427,7 @@ __global__ void k_extract(const double2 *__restrict__ S, int comp, int Kx, int P
         if (nhat32) nhat32[comp * plane + idx] = (float)v.x;
         local = fmax(local, fabs(v.y));
     }
-    // non-negative doubles order like their bit patterns
-    atomicMax(imag_max, (unsigned long long)__double_as_longlong(local));
+    block_max_to(local, imag_max);
 }
 
 constexpr int kFinalizeThreads = 1024;  // FP64 adds are slow: many independent chains per SM
@@ -639,7 +653,7 @@ __global__ void k_sp_extract(const double2 *__restrict__ S, int comp, int Px, in
         if (t32) t32[comp * plane + idx] = (float)re;
         local = fmax(local, fabs(im));
     }
-    atomicMax(imag_max, (unsigned long long)__double_as_longlong(local));
+    block_max_to(local, imag_max);
 }
 
 int grid_for(int64_t n, int block)

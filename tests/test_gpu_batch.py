@@ -1,5 +1,6 @@
-"""Batched states of uneven grid sizes: the persistent kernel and the graph of
-branches against the per-state plans and against the oracle; the bounded
+"""Batched states of uneven grid sizes: the persistent kernel, the
+pass-batched launches and the graph of branches against the per-state plans
+and against the oracle; the bounded
 dependency wait of the persistent kernel made to run out on purpose (a
 dependency that never completes), after which the GPU context keeps working."""
 import numpy as np
@@ -62,7 +63,7 @@ def test_persistent_matches_per_state_plans(small_batch):
 
 def test_batch_matches_oracle(small_batch):
     b, dims, cells, ms = small_batch
-    for mode in (b.PERSISTENT, b.BRANCHES):
+    for mode in (b.PERSISTENT, b.BRANCHES, b.PASSES):
         b.set_mode(mode)
         Hs, E = b.field(ms, energies=True)
         torch.cuda.synchronize()
@@ -83,11 +84,35 @@ def test_modes_agree_and_replay_is_stable(small_batch):
     H0b, _ = b.field(ms, energies=True)           # graph replay, new outputs
     b.set_mode(b.BRANCHES)
     H1, E1 = b.field(ms, energies=True)
+    H1 = [h.clone() for h in H1]
+    b.set_mode(b.PASSES)
+    H2, E2 = b.field(ms, energies=True)            # first call: direct launches, then captured
+    H2 = [h.clone() for h in H2]
+    H2b, E2b = b.field(ms, energies=True)          # graph replay
     torch.cuda.synchronize()
-    for a, c, e in zip(H0, H0b, H1):
+    for a, c, e, f, g in zip(H0, H0b, H1, H2, H2b):
         assert torch.equal(a, c)
         assert float((a - e).abs().max() / e.abs().max()) <= 1e-6
+        assert torch.equal(a, f)                    # the same tile functions: identical fields
+        assert torch.equal(f, g)
     assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
+    assert torch.equal(E0, E2) and torch.equal(E2, E2b)
+    b.set_mode(b.PERSISTENT)
+
+
+def test_pass_batched_timing_records_each_pass(small_batch):
+    b, dims, cells, ms = small_batch
+    b.set_mode(b.PASSES)
+    ref, _ = b.field(ms)
+    ref = [h.clone() for h in ref]
+    b.set_timing(True)
+    for _ in range(3):
+        Hs, _ = b.field(ms)
+    t, calls = b.get_timing()
+    b.set_timing(False)
+    assert calls == 3 and all(v > 0 for v in t)
+    for a, c in zip(ref, Hs):
+        assert torch.equal(a, c)
     b.set_mode(b.PERSISTENT)
 
 
@@ -123,9 +148,13 @@ def test_config_sized_batch_runs_persistent():
     H0 = [h.clone() for h in H0]
     b.set_mode(b.BRANCHES)
     H1, E1 = b.field(ms, energies=True)
+    H1 = [h.clone() for h in H1]
+    b.set_mode(b.PASSES)
+    H2, E2 = b.field(ms, energies=True)
     torch.cuda.synchronize()
-    for a, c in zip(H0, H1):
+    for a, c, e in zip(H0, H1, H2):
         assert float((a - c).abs().max() / c.abs().max()) <= 1e-6
+        assert torch.equal(a, e)
     assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
     b.close()
 
@@ -137,7 +166,12 @@ def test_batch_autotune_chooses_a_mode(tmp_path, monkeypatch):
     b = Batch(dims, cells)
     tp, tb = b.autotune()
     assert tb > 0 and (tp > 0 or tp == -1)
-    assert b.info()["mode"] == (0 if (tp > 0 and tp <= tb) else 1)
+    mode = b.info()["mode"]          # the fastest of persistent, branches, pass-batched
+    assert mode in (0, 1, 2)
+    if mode == 1 and tp > 0:
+        assert tb <= tp
+    if mode == 0:
+        assert tp <= tb
     Hs, _ = b.field(ms)
     torch.cuda.synchronize()
     for i in (0, 3):
