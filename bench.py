@@ -218,6 +218,19 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def load_tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 burst rate scaled by the
+    nominal GB300 TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s), or the fallback
+    bf16 figure scaled the same way."""
+    try:
+        with open(PEAKS) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        src = "measured bf16 burst x 1.1/2.25 (nominal TF32/bf16 ratio)"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1900.0, "fallback bf16 1.9 PF/s x 1.1/2.25 (nominal TF32/bf16 ratio)"
+    return bf16 * 1.1 / 2.25, src
+
+
 def load_traffic(kernel: str, n, src_hash: str):
     """DRAM bytes per launch of a kernel from a committed ncu summary, scaled to
     this workload, or None if absent or taken on an older kernel source."""
@@ -633,8 +646,10 @@ def run_sp(args, dev, M, H_dm, peak):
 def run_tg(args, dev, peak):
     """The tensor-grid method (paper Sec. 3.2) on the same grid for CP
     magnetizations of rank 1 (a uniform body, exact) and rank 8 (seeded random
-    factors): field + energy per step, and the FP32 error of the rank-8 field
-    against the FP64 TG path."""
+    factors): field + energy per step with the dense contraction on the tensor
+    cores (the FP32 default) and on the CUDA cores, the per-stage times, the
+    contraction's tensor-pipe rate against the TF32 peak, and the FP32 error
+    of the rank-8 field against the FP64 TG path."""
     import numpy as np
     import torch
 
@@ -644,6 +659,7 @@ def run_tg(args, dev, peak):
     n = N_GRID
     cells = n[0] * n[1] * n[2]
     st = torch.cuda.current_stream(dev)
+    tf32_peak, tf32_src = load_tf32_peak()
     out = {}
     rng = np.random.default_rng(SEED)
     for r in (1, 8):
@@ -657,41 +673,75 @@ def run_tg(args, dev, peak):
         plan = TGPlan(n, CELL, r, prec="f32", device=dev)
         H = torch.empty((3, n[2], n[1], n[0]), dtype=torch.float32, device=dev)
         E = torch.empty((), dtype=torch.float64, device=dev)
+        R = plan.info()["sinc_terms"]
+        K = 3 * R * r
+        # the dense block-CP contraction Phi[k][j][i] = sum_K Z[K][k] Y[K][j] X[K][i]
+        # over K = 3 R r terms: 2 cells K flops (the step's dominant arithmetic)
+        fl = 2.0 * cells * K
 
         def step():
             B.demag_tg_field_cp(plan.handle, *(t.data_ptr() for t in f32), H.data_ptr(), E.data_ptr(),
                                 st.cuda_stream)
 
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        k = max(5, args.steps)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(k):
-            step()
-        e1.record(st)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / k
-        R = plan.info()["sinc_terms"]
-        # the dense block-CP contraction Phi[k][j][i] = sum_K Z[K][k] Y[K][j] X[K][i]
-        # over K = 3 R r terms: 2 cells K flops (the step's dominant arithmetic)
-        fl = 2.0 * cells * 3 * R * r
-        ent = {"rank": r, "ms_per_step": round(ms, 4), "cells_per_s": cells / (ms / 1e3),
-               "sinc_terms": R, "energy_J": float(E.item()),
-               "alu": {"bound": "alu", "flops_contraction": fl, "tflops": round(fl / (ms * 1e-3) / 1e12, 2),
-                       "peak_tflops": round(FP32_TFLOPS, 1),
-                       "frac": round(fl / (ms * 1e-3) / 1e12 / FP32_TFLOPS, 3),
-                       "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)",
-                       "time": "whole TG step (factor transforms, contraction, differences, energy)"}}
-        plan.close()
+        def timed():
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            k = max(5, args.steps)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(k):
+                step()
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        def stages():
+            plan.set_timing(True)
+            for _ in range(3):
+                step()
+            ms, calls = plan.get_timing()
+            plan.set_timing(False)
+            return [v / calls for v in ms]
+
+        ent = {"rank": r, "sinc_terms": R, "terms_K": K, "flops_contraction": fl}
+        for name, c in (("tensor_cores", TGPlan.TENSOR_CORES), ("cuda_cores", TGPlan.CUDA_CORES)):
+            plan.set_contraction(c)
+            ms = timed()
+            sg = stages()
+            sub = {"ms_per_step": round(ms, 4), "cells_per_s": cells / (ms / 1e3),
+                   "stage_ms": {"factor_transforms": round(sg[0], 4), "operand_prep": round(sg[1], 4),
+                                "contraction": round(sg[2], 4), "differences_energy": round(sg[3], 4)}}
+            if c == TGPlan.TENSOR_CORES:
+                plan.status()
+                t = 3 * fl / (sg[2] * 1e-3) / 1e12
+                sub["roofline"] = {"bound": "tensor", "kernel": "k_tg_mma", "achieved": round(t, 1),
+                                   "peak": round(tf32_peak, 1), "unit": "TFLOP/s", "frac": round(t / tf32_peak, 3),
+                                   "peak_source": tf32_src,
+                                   "flops": "3 TF32 products per term (hi hi, hi lo, lo hi): 3 x 2 cells K",
+                                   "fp32_equivalent_tflops": round(fl / (sg[2] * 1e-3) / 1e12, 1)}
+                ent["energy_J"] = float(E.item())
+            else:
+                t = fl / (sg[2] * 1e-3) / 1e12
+                sub["alu"] = {"bound": "alu", "kernel": "k_tg_dense", "achieved": round(t, 2),
+                              "peak": round(FP32_TFLOPS, 1), "unit": "TFLOP/s", "frac": round(t / FP32_TFLOPS, 3),
+                              "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
+            ent[name] = sub
+        plan.set_contraction(TGPlan.TENSOR_CORES)
+        ent["ms_per_step"] = ent["tensor_cores"]["ms_per_step"]
+        ent["cells_per_s"] = ent["tensor_cores"]["cells_per_s"]
         if r == 8 and not args.skip_f64:
+            step()
             p64 = TGPlan(n, CELL, r, prec="f64", device=dev)
             H64 = p64.field(*[torch.tensor(a, dtype=torch.float64, device=dev) for a in [lam] + U])
             ent["f32_rel_max_err_vs_f64"] = float((H.double() - H64).abs().max() / H64.abs().max())
+            plan.set_contraction(TGPlan.CUDA_CORES)
+            step()
+            ent["f32_cuda_cores_rel_max_err_vs_f64"] = float((H.double() - H64).abs().max() / H64.abs().max())
             p64.close()
             del H64
+        plan.close()
         out[f"rank{r}"] = ent
         del H, f32
         torch.cuda.empty_cache()

@@ -511,6 +511,35 @@ demag_status demag_tg_field_cp(demag_tg_plan_t plan, const void *lam, const void
 demag_status demag_tg_potential_cp(demag_tg_plan_t plan, const void *lam, const void *Ux, const void *Uy,
                                    const void *Uz, void *phi, void *stream);
 
+/* The dense contraction Phi[k][j][i] = sum_K Z[K][k] Y[K][j] X[K][i] over the
+ * K = 3 R rank terms (the transformed factors of Eq. "sumpot"), a GEMM of
+ * nz ny rows by nx columns whose first operand is formed on the fly.
+ * contraction 1 (the default of FP32 plans): on the tensor cores (tcgen05,
+ * TF32 operands in shared memory, FP32 accumulators in tensor memory), each
+ * product a b taken as a_hi b_hi + a_hi b_lo + a_lo b_hi with a = a_hi + a_lo
+ * split into TF32 parts, which keeps FP32 accuracy. contraction 0: FP32 or
+ * FP64 on the CUDA cores (the only form of FP64 plans;
+ * DEMAG_ERR_UNSUPPORTED when 1 is asked of one). */
+demag_status demag_tg_set_contraction(demag_tg_plan_t plan, int contraction);
+demag_status demag_tg_get_contraction(demag_tg_plan_t plan, int *contraction);
+
+/* Per-stage timing of TG calls: with enable != 0 each call records CUDA
+ * events on its stream around (0) the factor transforms, (1) the operand
+ * preparation of the tensor-core contraction (transposes, TF32 split; empty
+ * for contraction 0), (2) the contraction, (3) the differences and energy,
+ * and waits for them; demag_tg_get_timing adds up ms[0..3] over *calls
+ * calls since the last demag_tg_set_timing. */
+demag_status demag_tg_set_timing(demag_tg_plan_t plan, int enable);
+demag_status demag_tg_get_timing(demag_tg_plan_t plan, double *ms, long *calls);
+
+/* The tensor-core contraction waits for its operand copies and MMAs with a
+ * bound (about two seconds); if a wait gives up, the kernel drains what it
+ * has in flight (bounded), frees its tensor memory and returns, leaving
+ * that call's potential incomplete. Synchronises the stream and returns
+ * DEMAG_ERR_TIMEOUT if that happened since the last call (then clears it),
+ * else DEMAG_OK. */
+demag_status demag_tg_status(demag_tg_plan_t plan, void *stream);
+
 /* Sinc terms R, device memory held, kernels launched so far (any may be NULL). */
 demag_status demag_tg_plan_info(demag_tg_plan_t plan, int *sinc_terms, size_t *device_bytes, long *launches);
 

@@ -52,7 +52,8 @@ EXPORTS = [
     "demag_plan_create_sp", "demag_sp_potential",
     "demag_get_x_variant", "demag_set_x_variant", "demag_check_pipeline",
     "demag_tg_plan_create", "demag_tg_field_cp", "demag_tg_potential_cp", "demag_tg_plan_info",
-    "demag_tg_plan_destroy",
+    "demag_tg_plan_destroy", "demag_tg_set_contraction", "demag_tg_get_contraction", "demag_tg_status",
+    "demag_tg_set_timing", "demag_tg_get_timing",
 ]
 
 
@@ -154,6 +155,11 @@ def load(path: str | Path | None = None):
         "demag_tg_potential_cp": (S, [P, P, P, P, P, P, P]),
         "demag_tg_plan_info": (S, [P, POINTER(c_int), POINTER(c_size_t), POINTER(c_long)]),
         "demag_tg_plan_destroy": (None, [P]),
+        "demag_tg_set_contraction": (S, [P, I]),
+        "demag_tg_get_contraction": (S, [P, POINTER(c_int)]),
+        "demag_tg_status": (S, [P, P]),
+        "demag_tg_set_timing": (S, [P, I]),
+        "demag_tg_get_timing": (S, [P, POINTER(c_double), POINTER(c_long)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +248,31 @@ def demag_tg_plan_info(plan) -> dict:
     _check(load().demag_tg_plan_info(_p(plan), ctypes.byref(r), ctypes.byref(b), ctypes.byref(n)),
            "demag_tg_plan_info")
     return {"sinc_terms": r.value, "device_bytes": b.value, "launches": n.value}
+
+
+def demag_tg_set_contraction(plan, contraction):
+    _check(load().demag_tg_set_contraction(_p(plan), int(contraction)), "demag_tg_set_contraction")
+
+
+def demag_tg_get_contraction(plan) -> int:
+    c = ctypes.c_int(0)
+    _check(load().demag_tg_get_contraction(_p(plan), ctypes.byref(c)), "demag_tg_get_contraction")
+    return c.value
+
+
+def demag_tg_set_timing(plan, enable):
+    _check(load().demag_tg_set_timing(_p(plan), int(bool(enable))), "demag_tg_set_timing")
+
+
+def demag_tg_get_timing(plan):
+    ms = (c_double * 4)()
+    calls = c_long()
+    _check(load().demag_tg_get_timing(_p(plan), ms, ctypes.byref(calls)), "demag_tg_get_timing")
+    return list(ms), calls.value
+
+
+def demag_tg_status(plan, stream=0):
+    _check(load().demag_tg_status(_p(plan), _p(stream)), "demag_tg_status")
 
 
 def demag_tg_plan_destroy(plan):

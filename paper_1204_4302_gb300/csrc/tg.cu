@@ -18,8 +18,10 @@
 // so per call the library
 //   1. transforms every factor vector by its Toeplitz matrix (k_tg_apply),
 //   2. sums the K = 3 R r rank-one terms densely: Phi[k][j][i] =
-//      sum_K Z[K][k] Y[K][j] X[K][i] (k_tg_dense, a tiled contraction whose
-//      first operand is formed on the fly as the products Z Y),
+//      sum_K Z[K][k] Y[K][j] X[K][i], a GEMM whose first operand is formed on
+//      the fly as the products Z Y: on the tensor cores for FP32 plans
+//      (k_tg_mma in tg_mma.cuh, three TF32 products per term), as a tiled
+//      FP32 / FP64 CUDA-core contraction otherwise (k_tg_dense),
 //   3. differences Phi (k_tg_field) and forms the energy with M rebuilt from
 //      its factors.
 #include <math.h>
@@ -28,8 +30,13 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "demag.h"
+#include "launch_util.cuh"
 #include "plan.h"
+#include "tg_mma.cuh"
 
 namespace demag {
 namespace {
@@ -167,49 +174,71 @@ k_tg_dense(const T *__restrict__ X, const T *__restrict__ Y, const T *__restrict
 // Second-order differences of the cell-centre potential (central inside,
 // one-sided at the ends; n >= 3 per axis), H = -grad Phi, and optionally the
 // energy partials sum over the block of M . H with M rebuilt from its factors.
+constexpr int kTgFieldThreads = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kTgFieldThreads)
 k_tg_field(const T *__restrict__ phi, int nx, int ny, int nz, T hx, T hy, T hz, T *__restrict__ H,
            const T *__restrict__ lam, const T *__restrict__ Ux, const T *__restrict__ Uy, const T *__restrict__ Uz, int r,
            double *__restrict__ partials)
 {
-    const int64_t ncell = (int64_t)nx * ny * nz;
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double acc = 0.0;
-    if (c < ncell) {
-        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
-        const int64_t sy = nx, sz = (int64_t)nx * ny;
-        auto deriv = [&](int idx, int n, int64_t st, T h) -> T {
-            const T *f = phi + c;
-            if (idx == 0) return ((T)-3 * f[0] + (T)4 * f[st] - f[2 * st]) / ((T)2 * h);
-            if (idx == n - 1) return ((T)3 * f[0] - (T)4 * f[-st] + f[-2 * st]) / ((T)2 * h);
-            return (f[st] - f[-st]) / ((T)2 * h);
-        };
-        const T h0 = -deriv(i, nx, 1, hx), h1 = -deriv(j, ny, sy, hy), h2 = -deriv(k, nz, sz, hz);
-        if (H) {
-            H[c] = h0;
-            H[ncell + c] = h1;
-            H[2 * ncell + c] = h2;
-        }
+    // One block per x row (j, k) at a time (grid-stride over rows), threads
+    // over i. The energy's M^(p)[k][j][i] = sum_m lam Ux Uy Uz takes the
+    // row-constant part w[p r + m] = lam Uy[j] Uz[k] from shared memory, so a
+    // cell costs 3 r coalesced factor loads and no index divisions; the
+    // energy leaves one FP64 partial per block.
+    __shared__ T w[3 * 64];
+    __shared__ double ws[kTgFieldThreads / 32];
+    const int64_t sy = nx, sz = (int64_t)nx * ny, ncell = sz * nz;
+    const T ix = (T)0.5 / hx, iy = (T)0.5 / hy, iz = (T)0.5 / hz;
+    const int nrows = ny * nz;
+    T acc = 0;
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int j = row % ny, k = row / ny;
         if (partials) {
-            const T hv[3] = {h0, h1, h2};
-            for (int p = 0; p < 3; ++p) {
-                T mp = 0;
-                for (int m = 0; m < r; ++m)
-                    mp += lam[p * r + m] * Ux[((int64_t)p * r + m) * nx + i] * Uy[((int64_t)p * r + m) * ny + j] *
-                          Uz[((int64_t)p * r + m) * nz + k];
-                acc += (double)(mp * hv[p]);
+            __syncthreads();  // the previous row's w is read
+            for (int v = threadIdx.x; v < 3 * r; v += blockDim.x) w[v] = lam[v] * Uy[v * ny + j] * Uz[v * nz + k];
+            __syncthreads();
+        }
+        const T *prow = phi + (int64_t)row * nx;
+        // y and z differences: central inside, one-sided at the ends
+        const int64_t jm = j == 0 ? 0 : (j == ny - 1 ? -2 * sy : -sy), jp = j == 0 ? 2 * sy : (j == ny - 1 ? 0 : sy);
+        const int64_t km = k == 0 ? 0 : (k == nz - 1 ? -2 * sz : -sz), kp = k == 0 ? 2 * sz : (k == nz - 1 ? 0 : sz);
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const T *f = prow + i;
+            T d0, d1, d2;
+            if (i == 0) d0 = ((T)-3 * f[0] + (T)4 * f[1] - f[2]) * ix;
+            else if (i == nx - 1) d0 = ((T)3 * f[0] - (T)4 * f[-1] + f[-2]) * ix;
+            else d0 = (f[1] - f[-1]) * ix;
+            if (j == 0) d1 = ((T)-3 * f[0] + (T)4 * f[sy] - f[jp]) * iy;
+            else if (j == ny - 1) d1 = ((T)3 * f[0] - (T)4 * f[-sy] + f[jm]) * iy;
+            else d1 = (f[jp] - f[jm]) * iy;
+            if (k == 0) d2 = ((T)-3 * f[0] + (T)4 * f[sz] - f[kp]) * iz;
+            else if (k == nz - 1) d2 = ((T)3 * f[0] - (T)4 * f[-sz] + f[km]) * iz;
+            else d2 = (f[kp] - f[km]) * iz;
+            const int64_t c = (int64_t)row * nx + i;
+            if (H) {
+                H[c] = -d0;
+                H[ncell + c] = -d1;
+                H[2 * ncell + c] = -d2;
+            }
+            if (partials) {
+                const T hv[3] = {-d0, -d1, -d2};
+                for (int p = 0; p < 3; ++p) {
+                    T mp = 0;
+                    for (int m = 0; m < r; ++m) mp += w[p * r + m] * Ux[(p * r + m) * nx + i];
+                    acc += mp * hv[p];
+                }
             }
         }
     }
     if (partials) {
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        __shared__ double ws[8];
-        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)acc;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0;
-            for (int w = 0; w < 8; ++w) t += ws[w];
+            for (int q = 0; q < kTgFieldThreads / 32; ++q) t += ws[q];
             partials[blockIdx.x] = t;
         }
     }
@@ -233,6 +262,18 @@ struct demag_tg_plan {
     int npartials;
     size_t device_bytes;
     long launches;
+    // tensor-core contraction (FP32 plans): transposed factors, the B operand
+    // in stage order, its tiling, the timeout word
+    int contraction;        // 0 CUDA cores, 1 tensor cores
+    int Kp, BN, ntn, nkc;
+    float *Yt, *Zt, *Bsw;
+    int *err;
+    // per-stage event timing (factor transforms, operand preparation,
+    // contraction, differences and energy)
+    bool timing;
+    cudaEvent_t ev[5];
+    double stage_ms[4];
+    long timed_calls;
 };
 
 namespace {
@@ -241,6 +282,39 @@ demag_status tg_fail(demag_status s, const std::string &m)
 {
     demag::set_last_error(m);
     return s;
+}
+
+// The FP32 contraction on the tensor cores: operand preparation (B in stage
+// order with its TF32 split, Y and Z transposed to K-contiguous rows), then
+// the persistent tcgen05 kernel.
+cudaError_t tg_contract_mma(demag_tg_plan *p, float *phi, cudaStream_t st, cudaEvent_t between)
+{
+    using namespace demag;
+    const int K = 3 * p->R * p->rank;
+    const int64_t nb = (int64_t)p->ntn * p->nkc * p->BN * tgm::kBK;
+    const int bb = (int)std::min<int64_t>((nb + 255) / 256, 4096);
+    tgm::k_tg_prep_b<<<bb, 256, 0, st>>>(static_cast<const float *>(p->X), K, p->nx, p->BN, p->ntn, p->nkc, p->Bsw);
+    const int by = (int)std::min<int64_t>(((int64_t)p->ny * p->Kp + 255) / 256, 4096);
+    tgm::k_tg_transpose<<<by, 256, 0, st>>>(static_cast<const float *>(p->Y), K, p->ny, p->Kp, p->Yt);
+    const int bz = (int)std::min<int64_t>(((int64_t)p->nz * p->Kp + 255) / 256, 4096);
+    tgm::k_tg_transpose<<<bz, 256, 0, st>>>(static_cast<const float *>(p->Z), K, p->nz, p->Kp, p->Zt);
+    p->launches += 3;
+    if (between) cudaEventRecord(between, st);
+    const size_t sm = tgm::smem_bytes(p->BN);
+    cudaError_t e = allow_smem<tgm::k_tg_mma>(sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tgm::k_tg_mma, tgm::kThreads, sm)) != cudaSuccess)
+        return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int64_t M = (int64_t)p->nz * p->ny;
+    const int ntiles = (int)((M + tgm::kBM - 1) / tgm::kBM) * p->ntn;
+    const int cap = sm_count() * occ;
+    const int grid = ntiles < cap ? ntiles : cap;
+    tgm::k_tg_mma<<<grid, tgm::kThreads, sm, st>>>(p->Yt, p->Zt, p->Bsw, p->Kp, p->nx, p->ny, p->nz, p->BN, p->ntn,
+                                                   ntiles, phi, p->err);
+    p->launches++;
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -252,6 +326,7 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
     const int n[3] = {p->nx, p->ny, p->nz};
     const void *U[3] = {Ux, Uy, Uz};
     void *out[3] = {p->X, p->Y, p->Z};
+    if (p->timing) cudaEventRecord(p->ev[0], st);
     for (int q = 0; q < 3; ++q) {
         const size_t sm = (size_t)(3 * n[q]) * sizeof(T);
         k_tg_apply<T><<<K, n[q] >= 512 ? 512 : ((n[q] + 31) / 32) * 32, sm, st>>>(
@@ -259,15 +334,35 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
             p->wnode, p->R, p->rank, q, n[q], static_cast<T *>(out[q]));
         p->launches++;
     }
+    if (p->timing) cudaEventRecord(p->ev[1], st);
     T *phi = phi_out ? static_cast<T *>(phi_out) : static_cast<T *>(p->phi);
-    const dim3 grid((p->nx + kTgCols - 1) / kTgCols, ((p->ny + 15) / 16) * ((p->nz + 7) / 8));
-    k_tg_dense<T><<<grid, 256, 0, st>>>(static_cast<const T *>(p->X), static_cast<const T *>(p->Y),
-                                        static_cast<const T *>(p->Z), K, p->nx, p->ny, p->nz, phi);
-    p->launches++;
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->contraction == 1) {
+            cudaError_t e = tg_contract_mma(p, phi, st, p->timing ? p->ev[2] : nullptr);
+            if (e != cudaSuccess) return tg_fail(DEMAG_ERR_CUDA, std::string("TG tensor-core contraction: ") +
+                                                                     cudaGetErrorString(e));
+            done = true;
+        }
+    }
+    if (!done) {
+        if (p->timing) cudaEventRecord(p->ev[2], st);
+        const dim3 grid((p->nx + kTgCols - 1) / kTgCols, ((p->ny + 15) / 16) * ((p->nz + 7) / 8));
+        k_tg_dense<T><<<grid, 256, 0, st>>>(static_cast<const T *>(p->X), static_cast<const T *>(p->Y),
+                                            static_cast<const T *>(p->Z), K, p->nx, p->ny, p->nz, phi);
+        p->launches++;
+    }
+    if (p->timing) cudaEventRecord(p->ev[3], st);
     if (want_field || E_dev) {
-        const int64_t ncell = (int64_t)p->nx * p->ny * p->nz;
-        const int blocks = (int)((ncell + 255) / 256);
-        k_tg_field<T><<<blocks, 256, 0, st>>>(phi, p->nx, p->ny, p->nz, (T)p->dx, (T)p->dy, (T)p->dz,
+        // a grid-stride kernel: no more blocks than are resident at once
+        const int64_t nrows = (int64_t)p->ny * p->nz;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tg_field<T>, kTgFieldThreads, 0) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        const int blocks =
+            (int)std::min<int64_t>(std::min<int64_t>(nrows, (int64_t)sm_count() * occ), p->npartials);
+        k_tg_field<T><<<blocks, kTgFieldThreads, 0, st>>>(phi, p->nx, p->ny, p->nz, (T)p->dx, (T)p->dy, (T)p->dz,
                                               static_cast<T *>(H), static_cast<const T *>(lam),
                                               static_cast<const T *>(Ux), static_cast<const T *>(Uy),
                                               static_cast<const T *>(Uz), p->rank, E_dev ? p->partials : nullptr);
@@ -281,6 +376,17 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tg_fail(DEMAG_ERR_CUDA, std::string("TG pass: ") + cudaGetErrorString(e));
+    if (p->timing) {
+        cudaEventRecord(p->ev[4], st);
+        if ((e = cudaEventSynchronize(p->ev[4])) != cudaSuccess)
+            return tg_fail(DEMAG_ERR_CUDA, std::string("TG timing: ") + cudaGetErrorString(e));
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]);
+            p->stage_ms[k] += ms;
+        }
+        p->timed_calls++;
+    }
     return DEMAG_OK;
 }
 
@@ -373,6 +479,12 @@ void demag_tg_plan_destroy(demag_tg_plan_t p)
     cudaFree(p->Z);
     cudaFree(p->phi);
     cudaFree(p->partials);
+    cudaFree(p->Yt);
+    cudaFree(p->Zt);
+    cudaFree(p->Bsw);
+    cudaFree(p->err);
+    for (int k = 0; k < 5; ++k)
+        if (p->ev[k]) cudaEventDestroy(p->ev[k]);
     delete p;
 }
 
@@ -419,7 +531,7 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     const size_t es = prec == DEMAG_F32 ? 4 : 8;
     const int K = 3 * R * rank;
     const int64_t ncell = (int64_t)nx * ny * nz;
-    p->npartials = (int)((ncell + 255) / 256);
+    p->npartials = (int)std::min<int64_t>((int64_t)ny * nz, 4096);  // one per block of the field kernel
     auto cleanup = [&](cudaError_t e, const char *what) {
         demag_tg_plan_destroy(p);
         return tg_fail(e == cudaErrorMemoryAllocation ? DEMAG_ERR_OOM : DEMAG_ERR_CUDA,
@@ -435,6 +547,24 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     if ((e = cudaMalloc(&p->Z, (size_t)K * nz * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
     if ((e = cudaMalloc(&p->phi, (size_t)ncell * es)) != cudaSuccess) return cleanup(e, "cudaMalloc potential");
     if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup(e, "cudaMalloc partials");
+    size_t mma_bytes = 0;
+    if (prec == DEMAG_F32) {
+        // tensor-core contraction: K padded to the 16-term stage, the columns
+        // split into ceil(nx / 256) tiles of BN (a multiple of 32) columns
+        p->contraction = 1;
+        p->Kp = (K + demag::tgm::kBK - 1) / demag::tgm::kBK * demag::tgm::kBK;
+        p->nkc = p->Kp / demag::tgm::kBK;
+        p->ntn = (nx + 255) / 256;
+        p->BN = ((nx + p->ntn - 1) / p->ntn + 31) / 32 * 32;
+        const size_t yb = (size_t)ny * p->Kp * 4, zb = (size_t)nz * p->Kp * 4;
+        const size_t bb = (size_t)p->ntn * p->nkc * p->BN * 2 * demag::tgm::kBK * 4;
+        if ((e = cudaMalloc(&p->Yt, yb)) != cudaSuccess) return cleanup(e, "cudaMalloc transposed factors");
+        if ((e = cudaMalloc(&p->Zt, zb)) != cudaSuccess) return cleanup(e, "cudaMalloc transposed factors");
+        if ((e = cudaMalloc(&p->Bsw, bb)) != cudaSuccess) return cleanup(e, "cudaMalloc tensor-core operand");
+        if ((e = cudaMalloc(&p->err, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMalloc status word");
+        if ((e = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess) return cleanup(e, "clear status word");
+        mma_bytes = yb + zb + bb + sizeof(int);
+    }
     if ((e = cudaMemcpy(p->snode, s.data(), sizeof(double) * R, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(e, "upload sinc nodes");
     if ((e = cudaMemcpy(p->wnode, w.data(), sizeof(double) * R, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -451,7 +581,7 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(e, "TG tables");
     p->launches = 1;
     p->device_bytes = 2 * sizeof(double) * R + tab_bytes + (size_t)K * (nx + ny + nz) * es + (size_t)ncell * es +
-                      sizeof(double) * p->npartials;
+                      sizeof(double) * p->npartials + mma_bytes;
     *out = p;
     demag::set_last_error("");
     return DEMAG_OK;
@@ -469,6 +599,69 @@ demag_status demag_tg_potential_cp(demag_tg_plan_t p, const void *lam, const voi
 {
     if (!phi) return tg_fail(DEMAG_ERR_INVALID_ARG, "phi is NULL");
     return tg_job(p, lam, Ux, Uy, Uz, nullptr, nullptr, phi, stream);
+}
+
+demag_status demag_tg_set_contraction(demag_tg_plan_t p, int contraction)
+{
+    if (!p) return tg_fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (contraction != 0 && contraction != 1) return tg_fail(DEMAG_ERR_INVALID_ARG, "contraction must be 0 or 1");
+    if (contraction == 1 && p->prec != DEMAG_F32)
+        return tg_fail(DEMAG_ERR_UNSUPPORTED, "the tensor-core contraction is built for FP32 plans");
+    p->contraction = contraction;
+    return DEMAG_OK;
+}
+
+demag_status demag_tg_get_contraction(demag_tg_plan_t p, int *contraction)
+{
+    if (!p || !contraction) return tg_fail(DEMAG_ERR_INVALID_ARG, "plan or output is NULL");
+    *contraction = p->contraction;
+    return DEMAG_OK;
+}
+
+demag_status demag_tg_set_timing(demag_tg_plan_t p, int enable)
+{
+    if (!p) return tg_fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    TgGuard g(p->device);
+    if (!g.ok) return tg_fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    if (enable && !p->ev[0])
+        for (int k = 0; k < 5; ++k)
+            if (cudaEventCreate(&p->ev[k]) != cudaSuccess) {
+                cudaGetLastError();
+                for (int q = 0; q < k; ++q) cudaEventDestroy(p->ev[q]);
+                for (int q = 0; q < 5; ++q) p->ev[q] = nullptr;
+                return tg_fail(DEMAG_ERR_CUDA, "creating timing events");
+            }
+    p->timing = enable != 0;
+    for (int k = 0; k < 4; ++k) p->stage_ms[k] = 0.0;
+    p->timed_calls = 0;
+    return DEMAG_OK;
+}
+
+demag_status demag_tg_get_timing(demag_tg_plan_t p, double *ms, long *calls)
+{
+    if (!p || !ms) return tg_fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 4; ++k) ms[k] = p->stage_ms[k];
+    if (calls) *calls = p->timed_calls;
+    return DEMAG_OK;
+}
+
+demag_status demag_tg_status(demag_tg_plan_t p, void *stream)
+{
+    if (!p) return tg_fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->err) return DEMAG_OK;
+    TgGuard g(p->device);
+    if (!g.ok) return tg_fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
+    int flag = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return tg_fail(DEMAG_ERR_CUDA, "reading the TG status");
+    if (flag) {
+        cudaMemsetAsync(p->err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        return tg_fail(DEMAG_ERR_TIMEOUT, "a bounded wait of the tensor-core contraction ran out of time");
+    }
+    return DEMAG_OK;
 }
 
 demag_status demag_tg_plan_info(demag_tg_plan_t p, int *sinc_terms, size_t *device_bytes, long *launches)

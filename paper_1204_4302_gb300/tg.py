@@ -70,6 +70,31 @@ class TGPlan:
     def info(self) -> dict:
         return B.demag_tg_plan_info(self.handle)
 
+    CUDA_CORES = 0
+    TENSOR_CORES = 1
+
+    def set_contraction(self, contraction: int):
+        """0: the dense contraction on the CUDA cores; 1 (FP32 default): on the
+        tensor cores, three TF32 products per term."""
+        B.demag_tg_set_contraction(self.handle, contraction)
+
+    def contraction(self) -> int:
+        return B.demag_tg_get_contraction(self.handle)
+
+    def set_timing(self, enable: bool = True):
+        """Per-stage event timing (factor transforms, operand preparation,
+        contraction, differences + energy) of the following calls."""
+        B.demag_tg_set_timing(self.handle, enable)
+
+    def get_timing(self):
+        """(ms per stage summed over the timed calls, number of calls)."""
+        return B.demag_tg_get_timing(self.handle)
+
+    def status(self):
+        """Raises (DEMAG_ERR_TIMEOUT) if a bounded wait of the tensor-core
+        contraction ran out since the last check; synchronises the stream."""
+        B.demag_tg_status(self.handle, self._stream())
+
     def close(self):
         if self.handle:
             B.demag_tg_plan_destroy(self.handle)

@@ -151,3 +151,68 @@ def test_tg_full_size_uniform_body(n):
     H64 = Hs["f64"]
     diff = float((Hs["f32"].double() - H64).abs().max() / H64.abs().max())
     assert diff <= 1e-3, diff
+
+
+@pytest.mark.parametrize("n,d,r", [((64, 40, 7), (1e-9, 1e-9, 1e-9), 2),     # M = 280: a ragged last row tile
+                                   ((300, 33, 9), (1e-9, 2e-9, 1e-9), 1),    # nx > 256: two column tiles of 160
+                                   ((37, 11, 5), (2e-9, 1e-9, 1e-9), 3),     # nx not a multiple of 4 (scalar stores)
+                                   ((5, 4, 3), (1e-9, 1e-9, 1e-9), 1)])      # one partial tile
+def test_tg_tensor_core_contraction(n, d, r):
+    """FP32 plans contract on the tensor cores by default (three TF32
+    products per term, FP32 accumulators in tensor memory): the potential
+    against the oracle within the FP32 bound, against the CUDA-core
+    contraction of the same plan, the per-stage timing and the status word."""
+    from paper_1204_4302_gb300.tg import TGPlan
+    lam, Ux, Uy, Uz = _random_cp(n, r, seed=7 * sum(n) + r)
+    M = _dense(lam, Ux, Uy, Uz)
+    phi_ref = tg.cell_potential_fft(M, d, oracle.sp_kernel)
+    p = TGPlan(n, d, r, prec="f32")
+    assert p.contraction() == TGPlan.TENSOR_CORES
+    args = [_torch(a, torch.float32) for a in (lam, Ux, Uy, Uz)]
+    K = 3 * p.info()["sinc_terms"] * r
+    bound = EPS32 * math.sqrt(K) * 16
+    p.set_timing(True)
+    phi_tc = p.potential(*args).double().cpu().numpy()
+    ms, calls = p.get_timing()
+    assert calls == 1 and len(ms) == 4 and all(v >= 0 for v in ms) and ms[2] > 0
+    p.set_timing(False)
+    p.status()
+    p.set_contraction(TGPlan.CUDA_CORES)
+    phi_cc = p.potential(*args).double().cpu().numpy()
+    assert _relmax(phi_tc, phi_ref) <= bound, (_relmax(phi_tc, phi_ref), bound)
+    assert _relmax(phi_cc, phi_ref) <= bound
+    assert _relmax(phi_tc, phi_cc) <= bound
+    p.close()
+
+
+def test_tg_contraction_choice():
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300.tg import TGPlan
+    p = TGPlan((8, 8, 8), (1e-9, 1e-9, 1e-9), 1, prec="f64")
+    assert p.contraction() == TGPlan.CUDA_CORES
+    with pytest.raises(B.DemagError):
+        p.set_contraction(TGPlan.TENSOR_CORES)
+    with pytest.raises(B.DemagError):
+        p.set_contraction(2)
+    p.close()
+
+
+def test_tg_tensor_core_full_size_rank8():
+    """256^3 cells, CP rank 8 (K = 3 R 8 terms, the benchmark's TG case):
+    the tensor-core FP32 potential against the FP64 plan's within the FP32
+    bound, on every cell."""
+    from paper_1204_4302_gb300.tg import TGPlan
+    n, d, r = (256, 256, 256), (2e-9, 2e-9, 2e-9), 8
+    rng = np.random.default_rng(11)
+    lam = 8e5 * rng.standard_normal((3, r)) / r
+    U = [rng.standard_normal((3, r, v)) for v in n]
+    p32 = TGPlan(n, d, r, prec="f32")
+    phi32 = p32.potential(*[_torch(a, torch.float32) for a in [lam] + U])
+    p32.status()
+    K = 3 * p32.info()["sinc_terms"] * r
+    p32.close()
+    p64 = TGPlan(n, d, r, prec="f64")
+    phi64 = p64.potential(*[_torch(a, torch.float64) for a in [lam] + U])
+    p64.close()
+    rel = float((phi32.double() - phi64).abs().max() / phi64.abs().max())
+    assert rel <= EPS32 * math.sqrt(K) * 16, (rel, K)
