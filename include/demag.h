@@ -511,6 +511,23 @@ demag_status demag_tg_field_cp(demag_tg_plan_t plan, const void *lam, const void
 demag_status demag_tg_potential_cp(demag_tg_plan_t plan, const void *lam, const void *Ux, const void *Uy,
                                    const void *Uz, void *phi, void *stream);
 
+/* Tucker input (App. A): M^(p)[k][j][i] = sum_{a,b,c} G[p][c][b][a] A[p][a][i]
+ * B[p][b][j] C[p][c][k]. Mode products pass a Tucker tensor factor by factor,
+ * G x_1 (D_1 A) x_2 (D_2 B) x_3 (D_3 C), so the potential of Eq. "sumpot" is
+ * the same dense contraction with first operand
+ * Q[(k,j)][(l,p,a)] = sum_{b,c} G[p][c][b][a] (D_2 B)[(l,p,b)][j] (D_3 C)[(l,p,c)][k]
+ * (formed once per call, nz ny x 3 R r1 values) and the x factors
+ * (D_1 A)[(l,p,a)][i]. Plans for Tucker ranks r1, r2, r3 (1..16 each);
+ * otherwise as demag_tg_plan_create. G: device [3][r3][r2][r1]; A [3][r1][nx],
+ * B [3][r2][ny], C [3][r3][nz] (plan element type, A/m carried by G). A
+ * Tucker plan takes only the _tucker calls, a CP plan only the _cp calls. */
+demag_status demag_tg_plan_create_tucker(int nx, int ny, int nz, double dx, double dy, double dz, int r1, int r2,
+                                         int r3, demag_prec prec, demag_tg_plan_t *out);
+demag_status demag_tg_field_tucker(demag_tg_plan_t plan, const void *G, const void *A, const void *B, const void *C,
+                                   void *H, double *E_dev, void *stream);
+demag_status demag_tg_potential_tucker(demag_tg_plan_t plan, const void *G, const void *A, const void *B,
+                                       const void *C, void *phi, void *stream);
+
 /* The dense contraction Phi[k][j][i] = sum_K Z[K][k] Y[K][j] X[K][i] over the
  * K = 3 R rank terms (the transformed factors of Eq. "sumpot"), a GEMM of
  * nz ny rows by nx columns whose first operand is formed on the fly.
@@ -539,6 +556,39 @@ demag_status demag_tg_get_timing(demag_tg_plan_t plan, double *ms, long *calls);
  * DEMAG_ERR_TIMEOUT if that happened since the last call (then clears it),
  * else DEMAG_OK. */
 demag_status demag_tg_status(demag_tg_plan_t plan, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Low-rank magnetization (paper Sec. 3.2, "Low-Rank Magnetization"): each
+ * component M^(p) [nz][ny][nx] approximated in CP or Tucker format by
+ * alternating least squares (the ALS algorithms of Kolda and Bader's tensor
+ * survey, which the paper uses for both), FP64, with the relative error of
+ * Eq. "relr" (Frobenius norms over the three components). The initial
+ * guesses are the caller's (the paper starts from random ones). Both calls
+ * allocate their workspace, run on stream and synchronise it.
+ *
+ * CP-ALS: per component, `iters` sweeps of the mode updates x, y, z:
+ *   A <- X_(x) (C kr B) V^+, V = (C^T C) * (B^T B) (Hadamard product),
+ *   lambda <- the column 2-norms, A <- A / lambda (likewise B, then C),
+ * V^+ the pseudo-inverse of the symmetric V (eigenvalues at or below 1e-12 of
+ * the largest dropped, so ranks beyond what the tensor holds stay defined).
+ * M: device double [3][nz][ny][nx]; Ux [3][rank][nx], Uy [3][rank][ny],
+ * Uz [3][rank][nz]: device double, the initial factors on entry (only Uy and
+ * Uz are read) and the normalised factors on return; lam: device double
+ * [3][rank] out; relerr: device double or NULL. These are the CP factors the
+ * TG entry points take. Grids 1..512 per axis, rank 1..64. */
+demag_status demag_cp_als(int nx, int ny, int nz, const double *M, int rank, int iters, double *lam, double *Ux,
+                          double *Uy, double *Uz, double *relerr, void *stream);
+
+/* Tucker-ALS (higher-order orthogonal iteration): per component, `iters`
+ * sweeps of A <- the r1 leading left singular vectors of
+ * (X x_y B^T x_z C^T)_(x), then B and C likewise, and the core
+ * G = X x_x A^T x_y B^T x_z C^T. A [3][r1][nx], B [3][r2][ny], C [3][r3][nz]:
+ * device double, the initial factors on entry (only B and C are read) and
+ * orthonormal factors on return (a direction the tensor does not hold comes
+ * back as zeros); G: device double [3][r3][r2][r1] out. Ranks 1..16, at most
+ * the axis length; iters >= 1. */
+demag_status demag_tucker_als(int nx, int ny, int nz, const double *M, int r1, int r2, int r3, int iters,
+                              double *G, double *A, double *B, double *C, double *relerr, void *stream);
 
 /* Sinc terms R, device memory held, kernels launched so far (any may be NULL). */
 demag_status demag_tg_plan_info(demag_tg_plan_t plan, int *sinc_terms, size_t *device_bytes, long *launches);

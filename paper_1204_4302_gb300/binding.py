@@ -53,7 +53,8 @@ EXPORTS = [
     "demag_get_x_variant", "demag_set_x_variant", "demag_check_pipeline",
     "demag_tg_plan_create", "demag_tg_field_cp", "demag_tg_potential_cp", "demag_tg_plan_info",
     "demag_tg_plan_destroy", "demag_tg_set_contraction", "demag_tg_get_contraction", "demag_tg_status",
-    "demag_tg_set_timing", "demag_tg_get_timing",
+    "demag_tg_set_timing", "demag_tg_get_timing", "demag_cp_als", "demag_tucker_als",
+    "demag_tg_plan_create_tucker", "demag_tg_field_tucker", "demag_tg_potential_tucker",
 ]
 
 
@@ -159,6 +160,11 @@ def load(path: str | Path | None = None):
         "demag_tg_get_contraction": (S, [P, POINTER(c_int)]),
         "demag_tg_status": (S, [P, P]),
         "demag_tg_set_timing": (S, [P, I]),
+        "demag_cp_als": (S, [I, I, I, P, I, I, P, P, P, P, P, P]),
+        "demag_tg_plan_create_tucker": (S, [I, I, I, D, D, D, I, I, I, I, POINTER(c_void_p)]),
+        "demag_tg_field_tucker": (S, [P, P, P, P, P, P, P, P]),
+        "demag_tg_potential_tucker": (S, [P, P, P, P, P, P, P]),
+        "demag_tucker_als": (S, [I, I, I, P, I, I, I, I, P, P, P, P, P, P]),
         "demag_tg_get_timing": (S, [P, POINTER(c_double), POINTER(c_long)]),
     }
     for name, (res, args) in sig.items():
@@ -231,6 +237,24 @@ def demag_tg_plan_create(nx, ny, nz, dx, dy, dz, rank, prec=DEMAG_F32):
     return h.value
 
 
+def demag_tg_plan_create_tucker(nx, ny, nz, dx, dy, dz, r1, r2, r3, prec=DEMAG_F32):
+    h = c_void_p()
+    _check(load().demag_tg_plan_create_tucker(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), int(r1),
+                                              int(r2), int(r3), int(prec), ctypes.byref(h)),
+           "demag_tg_plan_create_tucker")
+    return h.value
+
+
+def demag_tg_field_tucker(plan, G, A, B_, C, H, E_dev, stream=0):
+    _check(load().demag_tg_field_tucker(_p(plan), _p(G), _p(A), _p(B_), _p(C), _p(H), _p(E_dev), _p(stream)),
+           "demag_tg_field_tucker")
+
+
+def demag_tg_potential_tucker(plan, G, A, B_, C, phi, stream=0):
+    _check(load().demag_tg_potential_tucker(_p(plan), _p(G), _p(A), _p(B_), _p(C), _p(phi), _p(stream)),
+           "demag_tg_potential_tucker")
+
+
 def demag_tg_field_cp(plan, lam, Ux, Uy, Uz, H, E_dev, stream=0):
     _check(load().demag_tg_field_cp(_p(plan), _p(lam), _p(Ux), _p(Uy), _p(Uz), _p(H), _p(E_dev), _p(stream)),
            "demag_tg_field_cp")
@@ -269,6 +293,16 @@ def demag_tg_get_timing(plan):
     calls = c_long()
     _check(load().demag_tg_get_timing(_p(plan), ms, ctypes.byref(calls)), "demag_tg_get_timing")
     return list(ms), calls.value
+
+
+def demag_cp_als(nx, ny, nz, M, rank, iters, lam, Ux, Uy, Uz, relerr, stream=0):
+    _check(load().demag_cp_als(int(nx), int(ny), int(nz), _p(M), int(rank), int(iters), _p(lam), _p(Ux), _p(Uy),
+                               _p(Uz), _p(relerr), _p(stream)), "demag_cp_als")
+
+
+def demag_tucker_als(nx, ny, nz, M, r1, r2, r3, iters, G, A, B, C, relerr, stream=0):
+    _check(load().demag_tucker_als(int(nx), int(ny), int(nz), _p(M), int(r1), int(r2), int(r3), int(iters), _p(G),
+                                   _p(A), _p(B), _p(C), _p(relerr), _p(stream)), "demag_tucker_als")
 
 
 def demag_tg_status(plan, stream=0):

@@ -19,7 +19,7 @@ BUILD = PKG / "_build"
 LIB = BUILD / "libdemag.so"
 
 SOURCES = ["api.cu", "tensor.cu", "passes_f32.cu", "passes_f64.cu", "mixed_f32.cu", "mixed_f64.cu", "noalloc.cu",
-           "batch.cu", "tg.cu"]
+           "batch.cu", "tg.cu", "lowrank.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

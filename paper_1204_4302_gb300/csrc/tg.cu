@@ -180,13 +180,14 @@ template <typename T>
 __global__ void __launch_bounds__(kTgFieldThreads)
 k_tg_field(const T *__restrict__ phi, int nx, int ny, int nz, T hx, T hy, T hz, T *__restrict__ H,
            const T *__restrict__ lam, const T *__restrict__ Ux, const T *__restrict__ Uy, const T *__restrict__ Uz, int r,
-           double *__restrict__ partials)
+           double *__restrict__ partials, const T *__restrict__ G = nullptr, int r2 = 0, int r3 = 0)
 {
     // One block per x row (j, k) at a time (grid-stride over rows), threads
-    // over i. The energy's M^(p)[k][j][i] = sum_m lam Ux Uy Uz takes the
-    // row-constant part w[p r + m] = lam Uy[j] Uz[k] from shared memory, so a
-    // cell costs 3 r coalesced factor loads and no index divisions; the
-    // energy leaves one FP64 partial per block.
+    // over i. The energy's M^(p)[k][j][i] = sum_m w[p r + m] Ux[p r + m][i]
+    // takes the row-constant part from shared memory (CP: w = lam Uy[j]
+    // Uz[k]; Tucker, G given: w[p r + a] = sum_{b,c} G B[b][j] C[c][k] with
+    // r = r1), so a cell costs 3 r coalesced factor loads and no index
+    // divisions; the energy leaves one FP64 partial per block.
     __shared__ T w[3 * 64];
     __shared__ double ws[kTgFieldThreads / 32];
     const int64_t sy = nx, sz = (int64_t)nx * ny, ncell = sz * nz;
@@ -197,7 +198,22 @@ k_tg_field(const T *__restrict__ phi, int nx, int ny, int nz, T hx, T hy, T hz, 
         const int j = row % ny, k = row / ny;
         if (partials) {
             __syncthreads();  // the previous row's w is read
-            for (int v = threadIdx.x; v < 3 * r; v += blockDim.x) w[v] = lam[v] * Uy[v * ny + j] * Uz[v * nz + k];
+            if (G) {
+                // Tucker: w[p r + a] = sum_{b,c} G^(p)[c][b][a] B^(p)[b][j] C^(p)[c][k]
+                for (int v = threadIdx.x; v < 3 * r; v += blockDim.x) {
+                    const int p = v / r, a = v % r;
+                    const T *Gp = G + (int64_t)p * r3 * r2 * r;
+                    T acc = 0;
+                    for (int c = 0; c < r3; ++c) {
+                        T t = 0;
+                        for (int b = 0; b < r2; ++b) t += Gp[(c * r2 + b) * r + a] * Uy[(p * r2 + b) * ny + j];
+                        acc += t * Uz[(p * r3 + c) * nz + k];
+                    }
+                    w[v] = acc;
+                }
+            } else {
+                for (int v = threadIdx.x; v < 3 * r; v += blockDim.x) w[v] = lam[v] * Uy[v * ny + j] * Uz[v * nz + k];
+            }
             __syncthreads();
         }
         const T *prow = phi + (int64_t)row * nx;
@@ -244,6 +260,47 @@ k_tg_field(const T *__restrict__ phi, int nx, int ny, int nz, T hx, T hy, T hz, 
     }
 }
 
+// Tucker input: the contraction's first operand Q[g][K], g = k ny + j,
+// K = (l 3 + p) r1 + a, of the potential's block sum
+//   Phi[k][j][i] = sum_{l,p,a} Q[g][(l,p,a)] X[(l,p,a)][i],
+//   Q = sum_{b,c} G^(p)[c][b][a] Y[(l,p,b)][j] Z[(l,p,c)][k]
+// (the core times the transformed y and z factors). One block per ((l,p), k):
+// U[a][b] = sum_c G[c][b][a] Z[(l,p,c)][k] in shared memory, then
+// Q = sum_b U[a][b] Y[(l,p,b)][j] over the block's threads. KMAJOR: Q stored
+// [g][Kp] (rows of the tensor-core operand), else [K][g] (the CUDA-core form).
+template <typename T, bool KMAJOR>
+__global__ void __launch_bounds__(256)
+k_tg_tucker_q(const T *__restrict__ G, const T *__restrict__ Y, const T *__restrict__ Z, int r1, int r2, int r3,
+              int ny, int nz, int Kp, int64_t M, T *__restrict__ Q)
+{
+    __shared__ T U[16 * 16];
+    const int lp = blockIdx.x, k = blockIdx.y;  // lp = l 3 + p
+    const int p = lp % 3;
+    const T *Gp = G + (int64_t)p * r3 * r2 * r1;
+    for (int e = threadIdx.x; e < r1 * r2; e += blockDim.x) {
+        const int a = e / r2, b = e % r2;
+        T acc = 0;
+        for (int c = 0; c < r3; ++c) acc += Gp[(c * r2 + b) * r1 + a] * Z[((int64_t)lp * r3 + c) * nz + k];
+        U[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ny * r1; e += blockDim.x) {
+        const int j = KMAJOR ? e / r1 : e % ny, a = KMAJOR ? e % r1 : e / ny;
+        T acc = 0;
+        for (int b = 0; b < r2; ++b) acc += U[a * r2 + b] * Y[((int64_t)lp * r2 + b) * ny + j];
+        const int64_t g = (int64_t)k * ny + j, K = (int64_t)lp * r1 + a;
+        if (KMAJOR) Q[g * Kp + K] = acc;
+        else Q[K * M + g] = acc;
+    }
+    if (KMAJOR && lp == (int)gridDim.x - 1) {
+        // the padding terms K .. Kp - 1 of this k's rows are zero (the K-major
+        // and term-major forms share the buffer)
+        const int K = (int)gridDim.x * r1, pad = Kp - K;
+        for (int e = threadIdx.x; e < ny * pad; e += blockDim.x)
+            Q[((int64_t)k * ny + e / pad) * Kp + K + e % pad] = (T)0;
+    }
+}
+
 }  // namespace
 }  // namespace demag
 
@@ -265,6 +322,11 @@ struct demag_tg_plan {
     // tensor-core contraction (FP32 plans): transposed factors, the B operand
     // in stage order, its tiling, the timeout word
     int contraction;        // 0 CUDA cores, 1 tensor cores
+    // Tucker input (ranks r1, r2, r3; rank == r1): the first operand of the
+    // contraction, Q, and a row of ones (the unit z operand / CP weights)
+    bool tucker;
+    int r1, r2, r3;
+    void *Q, *ones;
     int Kp, BN, ntn, nkc;
     float *Yt, *Zt, *Bsw;
     int *err;
@@ -287,18 +349,30 @@ demag_status tg_fail(demag_status s, const std::string &m)
 // The FP32 contraction on the tensor cores: operand preparation (B in stage
 // order with its TF32 split, Y and Z transposed to K-contiguous rows), then
 // the persistent tcgen05 kernel.
+// Tucker plans pass their operand Q [nz ny][Kp] as the y factor of ny_eff =
+// nz ny rows and a row of ones as the z factor (nz_eff = 1): A = Q * 1.
 cudaError_t tg_contract_mma(demag_tg_plan *p, float *phi, cudaStream_t st, cudaEvent_t between)
 {
     using namespace demag;
-    const int K = 3 * p->R * p->rank;
+    const int K = 3 * p->R * p->r1;
     const int64_t nb = (int64_t)p->ntn * p->nkc * p->BN * tgm::kBK;
     const int bb = (int)std::min<int64_t>((nb + 255) / 256, 4096);
     tgm::k_tg_prep_b<<<bb, 256, 0, st>>>(static_cast<const float *>(p->X), K, p->nx, p->BN, p->ntn, p->nkc, p->Bsw);
-    const int by = (int)std::min<int64_t>(((int64_t)p->ny * p->Kp + 255) / 256, 4096);
-    tgm::k_tg_transpose<<<by, 256, 0, st>>>(static_cast<const float *>(p->Y), K, p->ny, p->Kp, p->Yt);
-    const int bz = (int)std::min<int64_t>(((int64_t)p->nz * p->Kp + 255) / 256, 4096);
-    tgm::k_tg_transpose<<<bz, 256, 0, st>>>(static_cast<const float *>(p->Z), K, p->nz, p->Kp, p->Zt);
-    p->launches += 3;
+    p->launches++;
+    const float *Yt = p->Yt, *Zt = p->Zt;
+    int ny = p->ny, nz = p->nz;
+    if (p->tucker) {
+        Yt = static_cast<const float *>(p->Q);
+        Zt = static_cast<const float *>(p->ones);
+        ny = p->ny * p->nz;
+        nz = 1;
+    } else {
+        const int by = (int)std::min<int64_t>(((int64_t)p->ny * p->Kp + 255) / 256, 4096);
+        tgm::k_tg_transpose<<<by, 256, 0, st>>>(static_cast<const float *>(p->Y), K, p->ny, p->Kp, p->Yt);
+        const int bz = (int)std::min<int64_t>(((int64_t)p->nz * p->Kp + 255) / 256, 4096);
+        tgm::k_tg_transpose<<<bz, 256, 0, st>>>(static_cast<const float *>(p->Z), K, p->nz, p->Kp, p->Zt);
+        p->launches += 2;
+    }
     if (between) cudaEventRecord(between, st);
     const size_t sm = tgm::smem_bytes(p->BN);
     cudaError_t e = allow_smem<tgm::k_tg_mma>(sm);
@@ -311,27 +385,45 @@ cudaError_t tg_contract_mma(demag_tg_plan *p, float *phi, cudaStream_t st, cudaE
     const int ntiles = (int)((M + tgm::kBM - 1) / tgm::kBM) * p->ntn;
     const int cap = sm_count() * occ;
     const int grid = ntiles < cap ? ntiles : cap;
-    tgm::k_tg_mma<<<grid, tgm::kThreads, sm, st>>>(p->Yt, p->Zt, p->Bsw, p->Kp, p->nx, p->ny, p->nz, p->BN, p->ntn,
-                                                   ntiles, phi, p->err);
+    tgm::k_tg_mma<<<grid, tgm::kThreads, sm, st>>>(Yt, Zt, p->Bsw, p->Kp, p->nx, ny, nz, p->BN, p->ntn, ntiles, phi,
+                                                   p->err);
     p->launches++;
     return cudaGetLastError();
 }
 
+// One TG call. CP plans: lam [3][r], factors [3][r][n]. Tucker plans: G
+// [3][r3][r2][r1] in place of lam, factors [3][r_q][n_q].
 template <typename T>
 demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const void *Uy, const void *Uz, void *H,
                     double *E_dev, bool want_field, void *phi_out, cudaStream_t st)
 {
     using namespace demag;
-    const int K = 3 * p->R * p->rank;
-    const int n[3] = {p->nx, p->ny, p->nz};
+    const int K = 3 * p->R * p->r1;
+    const int n[3] = {p->nx, p->ny, p->nz}, rq[3] = {p->r1, p->r2, p->r3};
     const void *U[3] = {Ux, Uy, Uz};
     void *out[3] = {p->X, p->Y, p->Z};
+    const T *G = p->tucker ? static_cast<const T *>(lam) : nullptr;
+    const T *weights = p->tucker ? static_cast<const T *>(p->ones) : static_cast<const T *>(lam);
     if (p->timing) cudaEventRecord(p->ev[0], st);
     for (int q = 0; q < 3; ++q) {
         const size_t sm = (size_t)(3 * n[q]) * sizeof(T);
-        k_tg_apply<T><<<K, n[q] >= 512 ? 512 : ((n[q] + 31) / 32) * 32, sm, st>>>(
-            static_cast<const T *>(p->tab), p->tstride, static_cast<const T *>(U[q]), static_cast<const T *>(lam),
-            p->wnode, p->R, p->rank, q, n[q], static_cast<T *>(out[q]));
+        k_tg_apply<T><<<3 * p->R * rq[q], n[q] >= 512 ? 512 : ((n[q] + 31) / 32) * 32, sm, st>>>(
+            static_cast<const T *>(p->tab), p->tstride, static_cast<const T *>(U[q]), weights, p->wnode, p->R, rq[q],
+            q, n[q], static_cast<T *>(out[q]));
+        p->launches++;
+    }
+    const bool mma = std::is_same<T, float>::value && p->contraction == 1;
+    if (p->tucker) {
+        const dim3 grid(3 * p->R, p->nz);
+        const int64_t M = (int64_t)p->ny * p->nz;
+        if (mma)
+            k_tg_tucker_q<T, true><<<grid, 256, 0, st>>>(G, static_cast<const T *>(p->Y), static_cast<const T *>(p->Z),
+                                                        p->r1, p->r2, p->r3, p->ny, p->nz, p->Kp, M,
+                                                        static_cast<T *>(p->Q));
+        else
+            k_tg_tucker_q<T, false><<<grid, 256, 0, st>>>(G, static_cast<const T *>(p->Y), static_cast<const T *>(p->Z),
+                                                         p->r1, p->r2, p->r3, p->ny, p->nz, p->Kp, M,
+                                                         static_cast<T *>(p->Q));
         p->launches++;
     }
     if (p->timing) cudaEventRecord(p->ev[1], st);
@@ -347,9 +439,13 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
     }
     if (!done) {
         if (p->timing) cudaEventRecord(p->ev[2], st);
-        const dim3 grid((p->nx + kTgCols - 1) / kTgCols, ((p->ny + 15) / 16) * ((p->nz + 7) / 8));
-        k_tg_dense<T><<<grid, 256, 0, st>>>(static_cast<const T *>(p->X), static_cast<const T *>(p->Y),
-                                            static_cast<const T *>(p->Z), K, p->nx, p->ny, p->nz, phi);
+        // Tucker: y operand Q [K][nz ny] over ny_eff = nz ny rows, z operand a
+        // row of ones (nz_eff = 1)
+        const int ny = p->tucker ? p->ny * p->nz : p->ny, nz = p->tucker ? 1 : p->nz;
+        const T *Yop = static_cast<const T *>(p->tucker ? p->Q : p->Y);
+        const T *Zop = static_cast<const T *>(p->tucker ? p->ones : p->Z);
+        const dim3 grid((p->nx + kTgCols - 1) / kTgCols, ((ny + 15) / 16) * ((nz + 7) / 8));
+        k_tg_dense<T><<<grid, 256, 0, st>>>(static_cast<const T *>(p->X), Yop, Zop, K, p->nx, ny, nz, phi);
         p->launches++;
     }
     if (p->timing) cudaEventRecord(p->ev[3], st);
@@ -365,7 +461,8 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
         k_tg_field<T><<<blocks, kTgFieldThreads, 0, st>>>(phi, p->nx, p->ny, p->nz, (T)p->dx, (T)p->dy, (T)p->dz,
                                               static_cast<T *>(H), static_cast<const T *>(lam),
                                               static_cast<const T *>(Ux), static_cast<const T *>(Uy),
-                                              static_cast<const T *>(Uz), p->rank, E_dev ? p->partials : nullptr);
+                                              static_cast<const T *>(Uz), p->r1, E_dev ? p->partials : nullptr, G,
+                                              p->r2, p->r3);
         p->launches++;
         if (E_dev) {
             const double V = p->dx * p->dy * p->dz;
@@ -428,17 +525,20 @@ demag_status tg_job(demag_tg_plan *p, const void *lam, const void *Ux, const voi
     TgGuard g(p->device);
     if (!g.ok) return tg_fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
     demag_status s;
-    if ((s = tg_check_ptr(p, lam, "lam")) != DEMAG_OK || (s = tg_check_ptr(p, Ux, "Ux")) != DEMAG_OK ||
-        (s = tg_check_ptr(p, Uy, "Uy")) != DEMAG_OK || (s = tg_check_ptr(p, Uz, "Uz")) != DEMAG_OK)
+    const char *n0 = p->tucker ? "G" : "lam", *n1 = p->tucker ? "A" : "Ux", *n2 = p->tucker ? "B" : "Uy",
+               *n3 = p->tucker ? "C" : "Uz";
+    if ((s = tg_check_ptr(p, lam, n0)) != DEMAG_OK || (s = tg_check_ptr(p, Ux, n1)) != DEMAG_OK ||
+        (s = tg_check_ptr(p, Uy, n2)) != DEMAG_OK || (s = tg_check_ptr(p, Uz, n3)) != DEMAG_OK)
         return s;
     if (H && (s = tg_check_ptr(p, H, "H")) != DEMAG_OK) return s;
     if (phi && (s = tg_check_ptr(p, phi, "phi")) != DEMAG_OK) return s;
     {
         // outputs must not overlap the factors (the kernels read them throughout)
-        const size_t es = p->prec == DEMAG_F32 ? 4 : 8, r = (size_t)p->rank;
+        const size_t es = p->prec == DEMAG_F32 ? 4 : 8, r1 = p->r1, r2 = p->r2, r3 = p->r3;
         const size_t ncell = (size_t)p->nx * p->ny * p->nz;
         const void *in[4] = {lam, Ux, Uy, Uz};
-        const size_t inb[4] = {3 * r * es, 3 * r * p->nx * es, 3 * r * p->ny * es, 3 * r * p->nz * es};
+        const size_t inb[4] = {(p->tucker ? 3 * r1 * r2 * r3 : 3 * r1) * es, 3 * r1 * p->nx * es, 3 * r2 * p->ny * es,
+                               3 * r3 * p->nz * es};
         auto hits = [&](const void *o, size_t ob) {
             for (int q = 0; q < 4; ++q) {
                 const uintptr_t a = (uintptr_t)o, b = (uintptr_t)in[q];
@@ -483,13 +583,19 @@ void demag_tg_plan_destroy(demag_tg_plan_t p)
     cudaFree(p->Zt);
     cudaFree(p->Bsw);
     cudaFree(p->err);
+    cudaFree(p->Q);
+    cudaFree(p->ones);
     for (int k = 0; k < 5; ++k)
         if (p->ev[k]) cudaEventDestroy(p->ev[k]);
     delete p;
 }
 
-demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, int rank, demag_prec prec,
-                                  demag_tg_plan_t *out)
+}  // extern "C"
+
+namespace {
+
+demag_status tg_create(int nx, int ny, int nz, double dx, double dy, double dz, int rank, int r2, int r3, bool tucker,
+                       demag_prec prec, demag_tg_plan_t *out)
 {
     if (!out) return tg_fail(DEMAG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -498,13 +604,19 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     if (nx > 512 || ny > 512 || nz > 512) return tg_fail(DEMAG_ERR_UNSUPPORTED, "TG grids are built up to 512 per axis");
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz))
         return tg_fail(DEMAG_ERR_INVALID_ARG, "cell edges must be positive and finite");
-    if (rank < 1 || rank > 64) return tg_fail(DEMAG_ERR_INVALID_ARG, "CP rank must be in 1..64");
+    if (!tucker && (rank < 1 || rank > 64)) return tg_fail(DEMAG_ERR_INVALID_ARG, "CP rank must be in 1..64");
+    if (tucker && (rank < 1 || r2 < 1 || r3 < 1 || rank > 16 || r2 > 16 || r3 > 16))
+        return tg_fail(DEMAG_ERR_INVALID_ARG, "Tucker ranks must be in 1..16");
     if (prec != DEMAG_F32 && prec != DEMAG_F64) return tg_fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
     demag_tg_plan *p = new demag_tg_plan;
     memset(p, 0, sizeof(*p));
     p->nx = nx; p->ny = ny; p->nz = nz;
     p->dx = dx; p->dy = dy; p->dz = dz;
     p->rank = rank;
+    p->tucker = tucker;
+    p->r1 = rank;
+    p->r2 = tucker ? r2 : rank;
+    p->r3 = tucker ? r3 : rank;
     p->prec = prec;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
@@ -529,7 +641,7 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     const int nmax = nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz);
     p->tstride = 2 * nmax - 1;
     const size_t es = prec == DEMAG_F32 ? 4 : 8;
-    const int K = 3 * R * rank;
+    const int K = 3 * R * rank, K2 = 3 * R * p->r2, K3 = 3 * R * p->r3;
     const int64_t ncell = (int64_t)nx * ny * nz;
     p->npartials = (int)std::min<int64_t>((int64_t)ny * nz, 4096);  // one per block of the field kernel
     auto cleanup = [&](cudaError_t e, const char *what) {
@@ -543,27 +655,45 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     if ((e = cudaMalloc(&p->wnode, sizeof(double) * R)) != cudaSuccess) return cleanup(e, "cudaMalloc sinc weights");
     if ((e = cudaMalloc(&p->tab, tab_bytes)) != cudaSuccess) return cleanup(e, "cudaMalloc tables");
     if ((e = cudaMalloc(&p->X, (size_t)K * nx * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
-    if ((e = cudaMalloc(&p->Y, (size_t)K * ny * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
-    if ((e = cudaMalloc(&p->Z, (size_t)K * nz * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
+    if ((e = cudaMalloc(&p->Y, (size_t)K2 * ny * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
+    if ((e = cudaMalloc(&p->Z, (size_t)K3 * nz * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
     if ((e = cudaMalloc(&p->phi, (size_t)ncell * es)) != cudaSuccess) return cleanup(e, "cudaMalloc potential");
     if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup(e, "cudaMalloc partials");
     size_t mma_bytes = 0;
+    p->Kp = (K + demag::tgm::kBK - 1) / demag::tgm::kBK * demag::tgm::kBK;
+    if (tucker) {
+        // Q: [nz ny][Kp] (tensor cores) or [K][nz ny] (CUDA cores); ones: the
+        // unit z operand of Kp terms and the unit CP weights of the x factors
+        const size_t qb = (size_t)ncell / nx * p->Kp * es;
+        if ((e = cudaMalloc(&p->Q, qb)) != cudaSuccess) return cleanup(e, "cudaMalloc Tucker operand");
+        if ((e = cudaMemset(p->Q, 0, qb)) != cudaSuccess) return cleanup(e, "clear Tucker operand");
+        const size_t no = std::max<size_t>((size_t)p->Kp, (size_t)3 * rank);
+        if ((e = cudaMalloc(&p->ones, no * es)) != cudaSuccess) return cleanup(e, "cudaMalloc ones");
+        if (prec == DEMAG_F32) {
+            std::vector<float> one(no, 1.0f);
+            e = cudaMemcpy(p->ones, one.data(), no * es, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<double> one(no, 1.0);
+            e = cudaMemcpy(p->ones, one.data(), no * es, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return cleanup(e, "upload ones");
+        mma_bytes += qb + no * es;
+    }
     if (prec == DEMAG_F32) {
         // tensor-core contraction: K padded to the 16-term stage, the columns
         // split into ceil(nx / 256) tiles of BN (a multiple of 32) columns
         p->contraction = 1;
-        p->Kp = (K + demag::tgm::kBK - 1) / demag::tgm::kBK * demag::tgm::kBK;
         p->nkc = p->Kp / demag::tgm::kBK;
         p->ntn = (nx + 255) / 256;
         p->BN = ((nx + p->ntn - 1) / p->ntn + 31) / 32 * 32;
-        const size_t yb = (size_t)ny * p->Kp * 4, zb = (size_t)nz * p->Kp * 4;
+        const size_t yb = tucker ? 0 : (size_t)ny * p->Kp * 4, zb = tucker ? 0 : (size_t)nz * p->Kp * 4;
         const size_t bb = (size_t)p->ntn * p->nkc * p->BN * 2 * demag::tgm::kBK * 4;
-        if ((e = cudaMalloc(&p->Yt, yb)) != cudaSuccess) return cleanup(e, "cudaMalloc transposed factors");
-        if ((e = cudaMalloc(&p->Zt, zb)) != cudaSuccess) return cleanup(e, "cudaMalloc transposed factors");
+        if (!tucker && (e = cudaMalloc(&p->Yt, yb)) != cudaSuccess) return cleanup(e, "cudaMalloc transposed factors");
+        if (!tucker && (e = cudaMalloc(&p->Zt, zb)) != cudaSuccess) return cleanup(e, "cudaMalloc transposed factors");
         if ((e = cudaMalloc(&p->Bsw, bb)) != cudaSuccess) return cleanup(e, "cudaMalloc tensor-core operand");
         if ((e = cudaMalloc(&p->err, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMalloc status word");
         if ((e = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess) return cleanup(e, "clear status word");
-        mma_bytes = yb + zb + bb + sizeof(int);
+        mma_bytes += yb + zb + bb + sizeof(int);
     }
     if ((e = cudaMemcpy(p->snode, s.data(), sizeof(double) * R, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(e, "upload sinc nodes");
@@ -580,16 +710,49 @@ demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, 
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(e, "TG tables");
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(e, "TG tables");
     p->launches = 1;
-    p->device_bytes = 2 * sizeof(double) * R + tab_bytes + (size_t)K * (nx + ny + nz) * es + (size_t)ncell * es +
-                      sizeof(double) * p->npartials + mma_bytes;
+    p->device_bytes = 2 * sizeof(double) * R + tab_bytes + ((size_t)K * nx + (size_t)K2 * ny + (size_t)K3 * nz) * es +
+                      (size_t)ncell * es + sizeof(double) * p->npartials + mma_bytes;
     *out = p;
     demag::set_last_error("");
     return DEMAG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+demag_status demag_tg_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, int rank, demag_prec prec,
+                                  demag_tg_plan_t *out)
+{
+    return tg_create(nx, ny, nz, dx, dy, dz, rank, rank, rank, false, prec, out);
+}
+
+demag_status demag_tg_plan_create_tucker(int nx, int ny, int nz, double dx, double dy, double dz, int r1, int r2,
+                                         int r3, demag_prec prec, demag_tg_plan_t *out)
+{
+    return tg_create(nx, ny, nz, dx, dy, dz, r1, r2, r3, true, prec, out);
+}
+
+demag_status demag_tg_field_tucker(demag_tg_plan_t p, const void *G, const void *A, const void *B, const void *C,
+                                   void *H, double *E_dev, void *stream)
+{
+    if (p && !p->tucker) return tg_fail(DEMAG_ERR_INVALID_ARG, "a CP plan takes demag_tg_field_cp");
+    if (!H && !E_dev) return tg_fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no field, no energy)");
+    return tg_job(p, G, A, B, C, H, E_dev, nullptr, stream);
+}
+
+demag_status demag_tg_potential_tucker(demag_tg_plan_t p, const void *G, const void *A, const void *B, const void *C,
+                                       void *phi, void *stream)
+{
+    if (p && !p->tucker) return tg_fail(DEMAG_ERR_INVALID_ARG, "a CP plan takes demag_tg_potential_cp");
+    if (!phi) return tg_fail(DEMAG_ERR_INVALID_ARG, "phi is NULL");
+    return tg_job(p, G, A, B, C, nullptr, nullptr, phi, stream);
+}
+
 demag_status demag_tg_field_cp(demag_tg_plan_t p, const void *lam, const void *Ux, const void *Uy, const void *Uz,
                                void *H, double *E_dev, void *stream)
 {
+    if (p && p->tucker) return tg_fail(DEMAG_ERR_INVALID_ARG, "a Tucker plan takes demag_tg_field_tucker");
     if (!H && !E_dev) return tg_fail(DEMAG_ERR_INVALID_ARG, "nothing to compute (no field, no energy)");
     return tg_job(p, lam, Ux, Uy, Uz, H, E_dev, nullptr, stream);
 }
@@ -597,6 +760,7 @@ demag_status demag_tg_field_cp(demag_tg_plan_t p, const void *lam, const void *U
 demag_status demag_tg_potential_cp(demag_tg_plan_t p, const void *lam, const void *Ux, const void *Uy, const void *Uz,
                                    void *phi, void *stream)
 {
+    if (p && p->tucker) return tg_fail(DEMAG_ERR_INVALID_ARG, "a Tucker plan takes demag_tg_potential_tucker");
     if (!phi) return tg_fail(DEMAG_ERR_INVALID_ARG, "phi is NULL");
     return tg_job(p, lam, Ux, Uy, Uz, nullptr, nullptr, phi, stream);
 }

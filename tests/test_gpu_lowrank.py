@@ -1,0 +1,199 @@
+"""Low-rank magnetization on the GPU (paper Sec. 3.2, "Low-Rank
+Magnetization"): CP-ALS and Tucker-ALS through the C ABI against the FP64
+oracle from the same initial guesses (factors, reconstructions, Eq. relr),
+the tensor-grid potential of Tucker input against the oracle's dense
+potential, and the paper's TG rows of the flower cube (CP rank 6) and the
+vortex cube (Tucker rank 10) run through the CUDA path end to end: ALS
+compression, TG field, energy to the printed digits."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from oracle import low_rank as lr  # noqa: E402
+from oracle import tensor_grid as tg  # noqa: E402
+from paper_1204_4302_gb300 import inputs  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_4302_gb300 import build
+    build.build()
+
+
+def _cuda(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _init(n, ranks, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((3, r, v)) for r, v in zip(ranks, n)]
+
+
+@pytest.mark.parametrize("n,r,iters", [((9, 7, 6), 3, 6), ((16, 5, 11), 2, 4), ((6, 6, 6), 1, 3)])
+def test_cp_als_matches_oracle(n, r, iters):
+    from paper_1204_4302_gb300 import lowrank
+    rng = np.random.default_rng(sum(n) + r)
+    M = rng.standard_normal((3,) + tuple(reversed(n)))
+    init = _init(n, (r, r, r), seed=7 + r)
+    lam, Ux, Uy, Uz, err = lowrank.cp_als(_cuda(M), r, [_cuda(f) for f in init], iters)
+    L = np.zeros_like(M)
+    for p in range(3):
+        lo, A, B, C = lr.cp_als(M[p], [init[q][p].T for q in range(3)], iters)
+        L[p] = lr.cp_reconstruct(lo, A, B, C)
+        assert np.allclose(lam[p].cpu().numpy(), lo, rtol=1e-9, atol=1e-12)
+        for got, ref in ((Ux, A), (Uy, B), (Uz, C)):
+            assert np.allclose(got[p].cpu().numpy(), ref.T, rtol=1e-8, atol=1e-10)
+    assert abs(err - lr.relerr(M, L)) <= 1e-10 * max(1.0, lr.relerr(M, L))
+
+
+def test_cp_als_recovers_exact_rank_and_handles_excess_rank():
+    from paper_1204_4302_gb300 import lowrank
+    n, r = (10, 9, 8), 3
+    rng = np.random.default_rng(3)
+    fac = [rng.standard_normal((3, r, v)) for v in n]
+    lam0 = rng.uniform(1, 3, (3, r))
+    M = np.stack([lr.cp_reconstruct(lam0[p], *(f[p].T for f in fac)) for p in range(3)])
+    init = [f + 0.1 * rng.standard_normal(f.shape) for f in fac]
+    *_, err = lowrank.cp_als(_cuda(M), r, [_cuda(f) for f in init], 150)
+    assert err < 1e-10, err
+    # rank 6 on a rank-3 tensor: singular normal equations, pseudo-inverse
+    init6 = _init(n, (6, 6, 6), seed=4)
+    *_, err6 = lowrank.cp_als(_cuda(M), 6, [_cuda(f) for f in init6], 40)
+    L = np.zeros_like(M)
+    for p in range(3):
+        lo, A, B, C = lr.cp_als(M[p], [init6[q][p].T for q in range(3)], 40)
+        L[p] = lr.cp_reconstruct(lo, A, B, C)
+    # degenerate (the extra terms cancel slowly), but the same iterates as the oracle
+    assert err6 < 1e-3 and abs(err6 - lr.relerr(M, L)) <= 1e-9 * lr.relerr(M, L), (err6, lr.relerr(M, L))
+
+
+@pytest.mark.parametrize("n,ranks", [((9, 10, 12), (3, 4, 2)),    # Gram of the columns (x, y), of the rows (z)
+                                     ((5, 6, 4), (3, 3, 3)),      # Gram of the rows
+                                     ((20, 3, 7), (4, 3, 5))])    # a rank equal to its axis
+def test_tucker_als_matches_oracle(n, ranks):
+    from paper_1204_4302_gb300 import lowrank
+    rng = np.random.default_rng(sum(n))
+    M = rng.standard_normal((3,) + tuple(reversed(n)))
+    init = _init(n, ranks, seed=11)
+    G, A, B, C, err = lowrank.tucker_als(_cuda(M), ranks, [_cuda(f) for f in init], 3)
+    G, A, B, C = (t.cpu().numpy() for t in (G, A, B, C))
+    L = np.zeros_like(M)
+    for p in range(3):
+        Go, Ao, Bo, Co = lr.tucker_als(M[p], [init[q][p].T for q in range(3)], 3)
+        L[p] = lr.tucker_reconstruct(Go, Ao, Bo, Co)
+        got = lr.tucker_reconstruct(G[p], A[p].T, B[p].T, C[p].T)
+        assert _relmax(got, L[p]) <= 1e-10
+        for F, Fo in ((A[p], Ao), (B[p], Bo), (C[p], Co)):
+            # factors [r][n]: orthonormal rows, the same projector onto the factor subspace
+            assert np.allclose(F @ F.T, np.eye(F.shape[0]), atol=1e-10)
+            assert np.allclose(F.T @ F, Fo @ Fo.T, atol=1e-9)
+        assert abs(np.sum(G[p] ** 2) - np.sum(Go ** 2)) <= 1e-10 * np.sum(Go ** 2)
+    assert abs(err - lr.relerr(M, L)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,d,ranks", [((12, 9, 7), (1e-9, 2e-9, 1e-9), (3, 2, 4)), ((40, 6, 5), (1e-9, 1e-9, 3e-9), (2, 2, 2))])
+def test_tg_tucker_potential_matches_oracle(n, d, ranks, prec):
+    from paper_1204_4302_gb300.tg import TGPlan
+    rng = np.random.default_rng(sum(n))
+    r1, r2, r3 = ranks
+    G = 8e5 * rng.standard_normal((3, r3, r2, r1))
+    A, B, C = (rng.standard_normal((3, r, v)) for r, v in zip(ranks, n))
+    M = np.stack([lr.tucker_reconstruct(G[p], A[p].T, B[p].T, C[p].T) for p in range(3)])
+    phi_ref = tg.cell_potential_fft(M, d, oracle.sp_kernel)
+    H_ref = tg.tg_field_from_potential(phi_ref, d)
+    E_ref = oracle.energy(M, H_ref, d)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    p = TGPlan(n, d, tucker=ranks, prec=prec)
+    args = [torch.tensor(a, dtype=dt, device="cuda") for a in (G, A, B, C)]
+    modes = (TGPlan.TENSOR_CORES, TGPlan.CUDA_CORES) if prec == "f32" else (TGPlan.CUDA_CORES,)
+    K = 3 * p.info()["sinc_terms"] * r1
+    for mode in modes:
+        if prec == "f32":
+            p.set_contraction(mode)
+        phi = p.potential(*args).double().cpu().numpy()
+        H, E = p.field(*args, energy=True)
+        H = H.double().cpu().numpy()
+        if prec == "f64":
+            assert _relmax(phi, phi_ref) <= 1e-12
+            assert _relmax(H, H_ref) <= 1e-12
+            assert abs(E.item() - E_ref) <= 1e-11 * abs(E_ref) + 1e-12 * oracle.MU0 * np.sum(np.abs(M * H_ref))
+        else:
+            A_ = float(np.max(np.abs(phi_ref)) / (np.max(np.abs(H_ref)) * min(d)))
+            tol = EPS32 * math.sqrt(K) * (16 + 8 * A_)
+            assert _relmax(phi, phi_ref) <= EPS32 * math.sqrt(K) * 16, (mode, _relmax(phi, phi_ref))
+            assert _relmax(H, H_ref) <= tol
+            assert abs(E.item() - E_ref) <= tol * np.sum(np.abs(M * H_ref)) * 0.5 * oracle.MU0 * np.prod(d)
+    p.status()
+    p.close()
+
+
+def test_cp_plan_and_tucker_plan_take_their_own_calls():
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300.tg import TGPlan
+    pt = TGPlan((5, 5, 5), (1e-9,) * 3, tucker=(2, 2, 2), prec="f64")
+    pc = TGPlan((5, 5, 5), (1e-9,) * 3, 2, prec="f64")
+    z = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in ((3, 2), (3, 2, 5), (3, 2, 5), (3, 2, 5))]
+    out = torch.empty((5, 5, 5), dtype=torch.float64, device="cuda")
+    with pytest.raises(B.DemagError):
+        B.demag_tg_potential_cp(pt.handle, *(t.data_ptr() for t in z), out.data_ptr(), 0)
+    with pytest.raises(B.DemagError):
+        B.demag_tg_potential_tucker(pc.handle, *(t.data_ptr() for t in z), out.data_ptr(), 0)
+    with pytest.raises(B.DemagError):
+        TGPlan((5, 5, 5), (1e-9,) * 3, tucker=(17, 2, 2), prec="f64")
+    pt.close()
+    pc.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name,fmt,rank", [("cube_flower", "cp", 6), ("cube_vortex", "tucker", 10)])
+def test_paper_tg_rows_through_the_cuda_path(name, fmt, rank, prec):
+    """Flower cube, CP rank 6 (Table cube_flower, TG row 1.529e-1) and vortex
+    cube, Tucker rank 10 (Table cube_vortex, TG row 2.193e-2): the dense state
+    compressed by ALS on the GPU (random initial guesses), its TG field on
+    the GPU, and the reduced energy of the compressed state to the printed
+    four digits."""
+    from paper_1204_4302_gb300 import lowrank
+    from paper_1204_4302_gb300.tg import TGPlan
+    with open(os.path.join(GOLDEN, "paper_tg_energies.json")) as fh:
+        case = {c["name"]: c for c in json.load(fh)["cases"]}[name]
+    n = tuple(case["grid"])
+    ext = tuple(case["extent"])
+    d = tuple(e / k for e, k in zip(ext, n))
+    M = inputs.flower(n, ext) if case["state"] == "flower" else inputs.vortex(n, ext, rc=0.14)
+    init = _init(n, (rank, rank, rank), seed=5)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    if fmt == "cp":
+        lam, Ux, Uy, Uz, err = lowrank.cp_als(_cuda(M), rank, [_cuda(f) for f in init], 60)
+        fac = (lam, Ux, Uy, Uz)
+        p = TGPlan(n, d, rank, prec=prec)
+        L = np.stack([lr.cp_reconstruct(lam[q].cpu().numpy(), Ux[q].cpu().numpy().T, Uy[q].cpu().numpy().T,
+                                        Uz[q].cpu().numpy().T) for q in range(3)])
+    else:
+        G, A, B, C, err = lowrank.tucker_als(_cuda(M), (rank,) * 3, [_cuda(f) for f in init], 10)
+        fac = (G, A, B, C)
+        p = TGPlan(n, d, tucker=(rank,) * 3, prec=prec)
+        L = np.stack([lr.tucker_reconstruct(G[q].cpu().numpy(), A[q].cpu().numpy().T, B[q].cpu().numpy().T,
+                                            C[q].cpu().numpy().T) for q in range(3)])
+    assert err < 1e-4 and abs(err - lr.relerr(M, L)) <= 1e-9
+    H = p.field(*[t.to(dt) for t in fac]).double().cpu().numpy()
+    p.close()
+    e = oracle.energy_reduced(L, H, d)
+    mag = 10 ** (math.floor(math.log10(abs(case["e"]))) - case["digits"] + 1)
+    assert abs(e - case["e"]) <= 0.5 * mag, (name, prec, e)
