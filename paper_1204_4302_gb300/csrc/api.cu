@@ -307,7 +307,8 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
         tm.mark();  // no inverse y pass
         tm.mark();  // no inverse x pass
         const double V = p->dx * p->dy * p->dz;
-        e = demag::energy_finalize(p->partials, nparts, 0.5 * kMu0 * V / ((double)Px * Py * Pz), job.E_dev, st);
+        e = demag::energy_finalize(p->partials, nparts, 0.5 * kMu0 * V / ((double)Px * Py * Pz), job.E_dev,
+                                   p->partials + p->npartials, st);
         if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
         p->launches++;
         tm.mark();
@@ -346,7 +347,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     tm.mark();
     if (job.E_dev) {
         const double V = p->dx * p->dy * p->dz;
-        e = demag::energy_finalize(p->partials, nblocks, -0.5 * kMu0 * V, job.E_dev, st);
+        e = demag::energy_finalize(p->partials, nblocks, -0.5 * kMu0 * V, job.E_dev, p->partials + p->npartials, st);
         if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
         p->launches++;
         tm.mark();
@@ -423,7 +424,8 @@ demag_status run_field_sp(demag_plan *p, const FieldJob &job, cudaStream_t st)
     }
     if (job.E_dev) {
         const double V = p->dx * p->dy * p->dz;
-        e = demag::energy_finalize(p->partials, Passes<T>::sp_grad_blocks(nx, ny, nz), -0.5 * kMu0 * V, job.E_dev, st);
+        e = demag::energy_finalize(p->partials, Passes<T>::sp_grad_blocks(nx, ny, nz), -0.5 * kMu0 * V, job.E_dev,
+                                   p->partials + p->npartials, st);
         if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
         p->launches++;
         tm.mark();
@@ -705,7 +707,10 @@ demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz
     } else {
         if ((e = dmalloc(&p->nhat64, ntab * plane * sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc tensor");
     }
-    if ((e = dmalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc partials");
+    if ((e = dmalloc(&p->partials, sizeof(double) * (p->npartials + demag::kFinalizeScratch))) != cudaSuccess)
+        return cleanup_fail(e, "cudaMalloc partials");
+    if ((e = cudaMemset(p->partials, 0, sizeof(double) * (p->npartials + demag::kFinalizeScratch))) != cudaSuccess)
+        return cleanup_fail(e, "clear partials");
     if ((e = dmalloc(&p->e_dev, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc energy");
     for (int a = 0; a < 3; ++a) {
         const auto t64 = twiddles<double2>(P[a]);
@@ -734,7 +739,7 @@ demag_status create_plan(int nx, int ny, int nz, double dx, double dy, double dz
     if ((e = cudaMemset(p->S1, 0, s1)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
     if (p->S2 != p->S1 && (e = cudaMemset(p->S2, 0, s2)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
     p->device_bytes = s1 + (p->S2 != p->S1 ? s2 : 0) + ntab * plane * (prec == DEMAG_F32 ? 4 : 8) +
-                      sizeof(double) * (p->npartials + 1) +
+                      sizeof(double) * (p->npartials + demag::kFinalizeScratch) +
                       (size_t)(P[0] + P[1] + P[2]) * (sizeof(double2) + (prec == DEMAG_F32 ? sizeof(float2) : 0)) *
                           (sp ? 2 : 1);
     *out = p;

@@ -167,7 +167,12 @@ cudaError_t tensor_extract(const double2 *S, int comp, int Px, int Py, int Pz, i
 // Sets the calling thread's demag_last_error() message (api.cu).
 void set_last_error(const std::string &msg);
 
-cudaError_t energy_finalize(const double *partials, int n, double factor, double *E,
+// Energy from n FP64 partials: *E = factor * sum (deterministic, several
+// CTAs). scratch: kFinalizeScratch doubles of device memory per plan (the
+// CTA results and a counter the kernel leaves at zero; zero-initialised).
+constexpr int kFinalizeBlocks = 64;
+constexpr int kFinalizeScratch = 2 * kFinalizeBlocks + 1;
+cudaError_t energy_finalize(const double *partials, int n, double factor, double *E, double *scratch,
                             cudaStream_t st);
 
 // Scalar-potential kernel setup (tensor.cu): octant of the cell kernel S at

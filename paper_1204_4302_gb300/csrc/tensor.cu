@@ -430,15 +430,25 @@ __global__ void k_extract(const double2 *__restrict__ S, int comp, int Kx, int P
     block_max_to(local, imag_max);
 }
 
-constexpr int kFinalizeThreads = 1024;  // FP64 adds are slow: many independent chains per SM
+constexpr int kFinalizeThreads = 256;
 
+// Sum of n FP64 partials times `factor` into *E. The CUDA cores' FP64 rate
+// per SM is low on this GPU, so the sum is spread over up to kFinalizeBlocks
+// CTAs: CTA b sums the contiguous chunk b (Neumaier-compensated per thread,
+// then a tree of compensated pairs) into scratch[2b], scratch[2b + 1]; the
+// CTA that finishes last (a counter after the scratch) adds the CTA results
+// in index order, writes *E and resets the counter. The result does not
+// depend on which CTA finishes last.
 __global__ void __launch_bounds__(kFinalizeThreads) k_energy_finalize(const double *__restrict__ partials, int n,
-                                                                      double factor, double *__restrict__ E)
+                                                                      double factor, double *__restrict__ E,
+                                                                      double *__restrict__ scratch)
 {
-    // one block; Neumaier-compensated sums per thread, then a tree of pairs
     __shared__ double ss[kFinalizeThreads], sc[kFinalizeThreads];
+    __shared__ bool s_last;
+    const int nb = gridDim.x, chunk = (n + nb - 1) / nb;
+    const int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
     double s = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double v = partials[i];
         const double t = s + v;
         c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
@@ -457,7 +467,27 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_energy_finalize(const doub
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *E = factor * (ss[0] + sc[0]);
+    unsigned int *count = reinterpret_cast<unsigned int *>(scratch + 2 * kFinalizeBlocks);
+    if (threadIdx.x == 0) {
+        scratch[2 * blockIdx.x] = ss[0];
+        scratch[2 * blockIdx.x + 1] = sc[0];
+        __threadfence();
+        s_last = atomicAdd(count, 1u) == (unsigned)(nb - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double *vs = scratch;
+        double S = 0.0, C = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double v = vs[2 * b];
+            const double t = S + v;
+            C += (fabs(S) >= fabs(v) ? (S - t) + v : (v - t) + S) + vs[2 * b + 1];
+            S = t;
+        }
+        *E = factor * (S + C);
+        *count = 0u;
+    }
 }
 
 // ------------------------------------------------------------------ SP kernel
@@ -728,9 +758,10 @@ cudaError_t sp_extract(const double2 *S, int comp, int Px, int Py, int Pz, int K
     return cudaGetLastError();
 }
 
-cudaError_t energy_finalize(const double *partials, int n, double factor, double *E, cudaStream_t st)
+cudaError_t energy_finalize(const double *partials, int n, double factor, double *E, double *scratch, cudaStream_t st)
 {
-    k_energy_finalize<<<1, kFinalizeThreads, 0, st>>>(partials, n, factor, E);
+    const int nb = std::max(1, std::min(kFinalizeBlocks, (n + 127) / 128));
+    k_energy_finalize<<<nb, kFinalizeThreads, 0, st>>>(partials, n, factor, E, scratch);
     return cudaGetLastError();
 }
 

@@ -466,7 +466,8 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
         p->launches++;
         if (E_dev) {
             const double V = p->dx * p->dy * p->dz;
-            cudaError_t e = energy_finalize(p->partials, blocks, -0.5 * 4e-7 * 3.14159265358979323846 * V, E_dev, st);
+            cudaError_t e = energy_finalize(p->partials, blocks, -0.5 * 4e-7 * 3.14159265358979323846 * V, E_dev,
+                                            p->partials + p->npartials, st);
             if (e != cudaSuccess) return tg_fail(DEMAG_ERR_CUDA, std::string("TG energy: ") + cudaGetErrorString(e));
             p->launches++;
         }
@@ -658,7 +659,10 @@ demag_status tg_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     if ((e = cudaMalloc(&p->Y, (size_t)K2 * ny * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
     if ((e = cudaMalloc(&p->Z, (size_t)K3 * nz * es)) != cudaSuccess) return cleanup(e, "cudaMalloc factors");
     if ((e = cudaMalloc(&p->phi, (size_t)ncell * es)) != cudaSuccess) return cleanup(e, "cudaMalloc potential");
-    if ((e = cudaMalloc(&p->partials, sizeof(double) * p->npartials)) != cudaSuccess) return cleanup(e, "cudaMalloc partials");
+    if ((e = cudaMalloc(&p->partials, sizeof(double) * (p->npartials + demag::kFinalizeScratch))) != cudaSuccess)
+        return cleanup(e, "cudaMalloc partials");
+    if ((e = cudaMemset(p->partials, 0, sizeof(double) * (p->npartials + demag::kFinalizeScratch))) != cudaSuccess)
+        return cleanup(e, "clear partials");
     size_t mma_bytes = 0;
     p->Kp = (K + demag::tgm::kBK - 1) / demag::tgm::kBK * demag::tgm::kBK;
     if (tucker) {
@@ -711,7 +715,7 @@ demag_status tg_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(e, "TG tables");
     p->launches = 1;
     p->device_bytes = 2 * sizeof(double) * R + tab_bytes + ((size_t)K * nx + (size_t)K2 * ny + (size_t)K3 * nz) * es +
-                      (size_t)ncell * es + sizeof(double) * p->npartials + mma_bytes;
+                      (size_t)ncell * es + sizeof(double) * (p->npartials + demag::kFinalizeScratch) + mma_bytes;
     *out = p;
     demag::set_last_error("");
     return DEMAG_OK;
