@@ -51,7 +51,8 @@ typedef enum {
     DEMAG_ERR_OOM = 3,         /* device or pinned host allocation failed */
     DEMAG_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has it) */
     DEMAG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    DEMAG_ERR_UNSUPPORTED = 6  /* size or option outside what is built */
+    DEMAG_ERR_UNSUPPORTED = 6, /* size or option outside what is built */
+    DEMAG_ERR_GUARD = 7        /* a guard zone of a debug allocation was overwritten */
 } demag_status;
 
 typedef enum { DEMAG_F32 = 0, DEMAG_F64 = 1 } demag_prec;
@@ -101,6 +102,22 @@ demag_status demag_plan_load(const char *path, demag_plan_t *out);
  * autotuner fails as if the device were out of memory (the call returns
  * DEMAG_ERR_OOM and frees what it had allocated); 0 disarms it. */
 void demag_debug_fail_alloc(long n);
+
+/* Debug allocations: with DEMAG_DEBUG=1 in the environment, every device
+ * buffer that plan creation, tensor setup, the host-buffer entry points or
+ * the autotuner allocate gets a 4 KB guard zone before and after it, filled
+ * with the byte 0xA5 (the buffer itself stays 256-byte aligned). A kernel
+ * that writes past either end of such a buffer overwrites a guard byte;
+ * demag_check_pipeline then scans the guard zones of every live debug
+ * allocation (one kernel per zone) and returns DEMAG_ERR_GUARD naming the
+ * first overwritten one. Reads past the ends are not detected. Without the
+ * variable the allocations are plain. demag_debug_guard_count returns the
+ * number of live debug allocations; demag_debug_poke_guard overwrites one
+ * byte of the trailing guard zone of the most recent one from the host (a
+ * test of the scan itself) and returns DEMAG_ERR_INVALID_ARG when there is
+ * none. */
+long demag_debug_guard_count(void);
+demag_status demag_debug_poke_guard(void);
 
 /* Sizes of a plan, as chosen at creation. */
 typedef struct {
@@ -474,8 +491,10 @@ demag_status demag_set_x_variant(demag_plan_t plan, int x);
  * seconds); if a wait gives up, the kernel waits (bounded) for its copies in
  * flight, records the failure and returns, leaving that call's output
  * incomplete. This call synchronises the device and returns
- * DEMAG_ERR_TIMEOUT if that happened since the last check (and clears it),
- * else DEMAG_OK. */
+ * DEMAG_ERR_TIMEOUT if that happened since the last check (and clears it);
+ * with debug allocations live (DEMAG_DEBUG=1, see demag_debug_guard_count) it
+ * then scans their guard zones and returns DEMAG_ERR_GUARD if one was
+ * overwritten; else DEMAG_OK. */
 demag_status demag_check_pipeline(demag_plan_t plan);
 
 /* ------------------------------------------------------------------------

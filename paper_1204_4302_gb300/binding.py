@@ -31,6 +31,7 @@ STATUS = {
     4: "DEMAG_ERR_CUDA",
     5: "DEMAG_ERR_TIMEOUT",
     6: "DEMAG_ERR_UNSUPPORTED",
+    7: "DEMAG_ERR_GUARD",
 }
 
 # Every symbol include/demag.h declares (the CPU tests check the export list).
@@ -41,7 +42,8 @@ EXPORTS = [
     "demag_launch_count", "demag_plan_destroy", "demag_last_error", "demag_status_string",
     "demag_energy_noalloc",
     "demag_batch_create", "demag_batch_create_ex", "demag_tune_padding", "demag_padded_lengths", "demag_set_graphs",
-    "demag_plan_save", "demag_plan_load", "demag_debug_fail_alloc", "demag_field_energy_host_async",
+    "demag_plan_save", "demag_plan_load", "demag_debug_fail_alloc", "demag_debug_guard_count",
+    "demag_debug_poke_guard", "demag_field_energy_host_async",
     "demag_batch_autotune_padding",
     "demag_batch_field", "demag_batch_set_mode", "demag_batch_set_timeout",
     "demag_batch_set_timing", "demag_batch_get_timing",
@@ -119,6 +121,8 @@ def load(path: str | Path | None = None):
         "demag_batch_autotune_padding": (S, [P, I, POINTER(c_double), POINTER(c_double), P]),
         "demag_field_energy_host_async": (S, [P, P, P, P, P]),
         "demag_debug_fail_alloc": (None, [ctypes.c_long]),
+        "demag_debug_guard_count": (ctypes.c_long, []),
+        "demag_debug_poke_guard": (S, []),
         "demag_plan_save": (S, [P, ctypes.c_char_p]),
         "demag_plan_load": (S, [ctypes.c_char_p, POINTER(c_void_p)]),
         "demag_get_timing": (S, [P, POINTER(c_double), POINTER(c_long), I]),
@@ -420,6 +424,14 @@ def demag_plan_load(path):
     h = c_void_p()
     _check(load().demag_plan_load(os.fsencode(path), ctypes.byref(h)), "demag_plan_load")
     return h.value
+
+
+def demag_debug_guard_count() -> int:
+    return int(load().demag_debug_guard_count())
+
+
+def demag_debug_poke_guard():
+    _check(load().demag_debug_poke_guard(), "demag_debug_poke_guard")
 
 
 def demag_debug_fail_alloc(n):

@@ -17,6 +17,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +33,27 @@ namespace {
 // as if the device were out of memory.
 std::atomic<long> g_fail_alloc{0};
 
+// Debug allocations (DEMAG_DEBUG=1): guard zones of kGuardBytes before and
+// after each buffer, filled with kGuardByte, registered by the buffer's
+// address so dfree releases the whole block and demag_check_pipeline scans
+// the zones.
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+struct GuardBlock {
+    void *base;
+    size_t bytes;
+    long serial;
+};
+std::mutex g_guard_mu;
+std::map<void *, GuardBlock> g_guards;
+long g_guard_serial = 0;
+
+bool debug_allocations()
+{
+    const char *v = getenv("DEMAG_DEBUG");
+    return v && v[0] && strcmp(v, "0") != 0;
+}
+
 template <typename P>
 cudaError_t dmalloc(P **ptr, size_t bytes)
 {
@@ -41,7 +64,50 @@ cudaError_t dmalloc(P **ptr, size_t bytes)
         *ptr = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMalloc(reinterpret_cast<void **>(ptr), bytes);
+    if (!debug_allocations()) return cudaMalloc(reinterpret_cast<void **>(ptr), bytes);
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes + 2 * kGuardBytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return e;
+    }
+    unsigned char *b = static_cast<unsigned char *>(base);
+    if ((e = cudaMemset(b, kGuardByte, kGuardBytes)) != cudaSuccess ||
+        (e = cudaMemset(b + kGuardBytes + bytes, kGuardByte, kGuardBytes)) != cudaSuccess) {
+        cudaFree(base);
+        *ptr = nullptr;
+        return e;
+    }
+    void *user = b + kGuardBytes;
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        g_guards[user] = GuardBlock{base, bytes, ++g_guard_serial};
+    }
+    *ptr = static_cast<P *>(user);
+    return cudaSuccess;
+}
+
+// cudaFree for buffers from dmalloc (the guarded block when it has one).
+void dfree(void *ptr)
+{
+    if (!ptr) return;
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        auto it = g_guards.find(ptr);
+        if (it != g_guards.end()) {
+            void *base = it->second.base;
+            g_guards.erase(it);
+            cudaFree(base);
+            return;
+        }
+    }
+    cudaFree(ptr);
+}
+
+__global__ void k_guard_scan(const unsigned char *__restrict__ z, int n, unsigned int *__restrict__ bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (z[i] != kGuardByte) atomicAdd(bad, 1u);
 }
 
 thread_local std::string g_err;
@@ -832,6 +898,7 @@ const char *demag_status_string(demag_status s)
     case DEMAG_ERR_CUDA: return "DEMAG_ERR_CUDA";
     case DEMAG_ERR_TIMEOUT: return "DEMAG_ERR_TIMEOUT";
     case DEMAG_ERR_UNSUPPORTED: return "DEMAG_ERR_UNSUPPORTED";
+    case DEMAG_ERR_GUARD: return "DEMAG_ERR_GUARD";
     }
     return "DEMAG_ERR_UNKNOWN";
 }
@@ -841,26 +908,26 @@ void demag_plan_destroy(demag_plan_t p)
     if (!p) return;
     DeviceGuard g(p->device);
     graphs_free(p);
-    if (p->S2 && p->S2 != p->S1) cudaFree(p->S2);
-    cudaFree(p->S1);
-    cudaFree(p->nhat32);
-    cudaFree(p->nhat64);
-    cudaFree(p->ntile);
+    if (p->S2 && p->S2 != p->S1) dfree(p->S2);
+    dfree(p->S1);
+    dfree(p->nhat32);
+    dfree(p->nhat64);
+    dfree(p->ntile);
     for (int a = 0; a < 3; ++a) {
-        cudaFree(p->tw64[a]); cudaFree(p->tw32[a]);
-        cudaFree(p->ph64[a]); cudaFree(p->ph32[a]);
+        dfree(p->tw64[a]); dfree(p->tw32[a]);
+        dfree(p->ph64[a]); dfree(p->ph32[a]);
     }
-    cudaFree(p->partials);
-    cudaFree(p->e_dev);
-    cudaFree(p->dM);
-    cudaFree(p->dH);
+    dfree(p->partials);
+    dfree(p->e_dev);
+    dfree(p->dM);
+    dfree(p->dH);
     if (p->async_ready) {
         cudaStreamSynchronize(p->s_in);
         cudaStreamSynchronize(p->s_out);
         for (int k = 0; k < 2; ++k) {
-            cudaFree(p->aM[k]);
-            cudaFree(p->aH[k]);
-            cudaFree(p->aE[k]);
+            dfree(p->aM[k]);
+            dfree(p->aH[k]);
+            dfree(p->aE[k]);
             cudaEventDestroy(p->ev_in[k]);
             cudaEventDestroy(p->ev_done[k]);
             cudaEventDestroy(p->ev_out[k]);
@@ -972,8 +1039,8 @@ demag_status sp_setup(demag_plan *p, cudaStream_t st)
     bool own64 = false;
     demag_status rs = DEMAG_OK;
     auto done = [&](demag_status s) {
-        cudaFree(oct); cudaFree(W); cudaFree(St); cudaFree(imag);
-        if (own64) cudaFree(t64);
+        dfree(oct); dfree(W); dfree(St); dfree(imag);
+        if (own64) dfree(t64);
         return s;
     };
 #define SETUP_CUDA(call)                                                                       \
@@ -1037,8 +1104,8 @@ demag_status demag_tensor_setup(demag_plan_t p, void *stream)
     bool own64 = false;
     demag_status rs = DEMAG_OK;
     auto done = [&](demag_status s) {
-        cudaFree(oct); cudaFree(W); cudaFree(St); cudaFree(imag);
-        if (own64) cudaFree(nh64);
+        dfree(oct); dfree(W); dfree(St); dfree(imag);
+        if (own64) dfree(nh64);
         return s;
     };
 #define SETUP_CUDA(call)                                                                       \
@@ -1431,7 +1498,7 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     void *M = nullptr, *H = nullptr;
     DEMAG_CUDA(dmalloc(&M, bytes));
     if (dmalloc(&H, bytes) != cudaSuccess) {
-        cudaFree(M);
+        dfree(M);
         return fail(DEMAG_ERR_OOM, "autotune buffers");
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -1464,8 +1531,8 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     p->use_graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(M);
-    cudaFree(H);
+    dfree(M);
+    dfree(H);
     if (rs != DEMAG_OK) return rs;
     p->zvariant = bz;
     p->yvariant = by;
@@ -1589,6 +1656,58 @@ demag_status demag_check_pipeline(demag_plan_t p)
     DEMAG_CUDA(cudaDeviceSynchronize());
     const int e = Passes<float>::pipe_error_take() | Passes<double>::pipe_error_take();
     if (e) return fail(DEMAG_ERR_TIMEOUT, "a pipelined x pass gave up waiting for a bulk copy");
+    std::vector<std::pair<void *, GuardBlock>> blocks;
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        blocks.assign(g_guards.begin(), g_guards.end());
+    }
+    if (blocks.empty()) return DEMAG_OK;
+    unsigned int *bad = nullptr;
+    DEMAG_CUDA(cudaMalloc(&bad, sizeof(unsigned int) * 2 * blocks.size()));
+    DEMAG_CUDA(cudaMemset(bad, 0, sizeof(unsigned int) * 2 * blocks.size()));
+    for (size_t q = 0; q < blocks.size(); ++q) {
+        const unsigned char *b = static_cast<const unsigned char *>(blocks[q].second.base);
+        k_guard_scan<<<8, 256>>>(b, (int)kGuardBytes, bad + 2 * q);
+        k_guard_scan<<<8, 256>>>(b + kGuardBytes + blocks[q].second.bytes, (int)kGuardBytes, bad + 2 * q + 1);
+    }
+    std::vector<unsigned int> h(2 * blocks.size());
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpy(h.data(), bad, sizeof(unsigned int) * h.size(), cudaMemcpyDeviceToHost);
+    cudaFree(bad);
+    if (ce != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("guard scan: ") + cudaGetErrorString(ce));
+    for (size_t q = 0; q < blocks.size(); ++q)
+        if (h[2 * q] || h[2 * q + 1]) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "guard zone %s debug allocation #%ld (%zu bytes) overwritten (%u bytes)",
+                     h[2 * q] ? "before" : "after", blocks[q].second.serial, blocks[q].second.bytes,
+                     h[2 * q] ? h[2 * q] : h[2 * q + 1]);
+            return fail(DEMAG_ERR_GUARD, msg);
+        }
+    return DEMAG_OK;
+}
+
+long demag_debug_guard_count(void)
+{
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    return (long)g_guards.size();
+}
+
+demag_status demag_debug_poke_guard(void)
+{
+    void *base = nullptr;
+    size_t bytes = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        long best = -1;
+        for (const auto &kv : g_guards)
+            if (kv.second.serial > best) {
+                best = kv.second.serial;
+                base = kv.second.base;
+                bytes = kv.second.bytes;
+            }
+    }
+    if (!base) return fail(DEMAG_ERR_INVALID_ARG, "no debug allocation is live");
+    DEMAG_CUDA(cudaMemset(static_cast<unsigned char *>(base) + kGuardBytes + bytes, 0x5A, 1));
     return DEMAG_OK;
 }
 
