@@ -29,7 +29,7 @@
  *  - Streams: a cudaStream_t passed as void*; NULL means the legacy default
  *    stream. Calls are asynchronous on that stream unless stated otherwise.
  *  - Errors: every call returns a status and never aborts. On failure a
- *    message is kept per thread, readable with demag_last_error(). A plan is
+ *    message is kept per thread, readable with demag_last_error(NULL). A plan is
  *    not thread safe: use one plan per host thread or serialise calls.
  */
 #ifndef DEMAG_H
@@ -323,7 +323,7 @@ demag_status demag_get_timing(demag_plan_t plan, double *ms, long *counts, int n
  * DEMAG_ERR_UNSUPPORTED beyond the capacity (checked before any product of
  * the sizes is formed) and DEMAG_ERR_CUDA if the set-up or one of its own
  * launches fails; an error left pending by earlier, unrelated work is not
- * reported as this call's failure and is not cleared. demag_last_error() is
+ * reported as this call's failure and is not cleared. demag_last_error(NULL) is
  * not updated by this call. */
 demag_status demag_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
                                   demag_prec prec, const void *M, const void *H, double *E_dev,
@@ -617,8 +617,10 @@ void demag_tg_plan_destroy(demag_tg_plan_t plan);
 /* Destroy a plan and free its device memory (NULL is ignored). */
 void demag_plan_destroy(demag_plan_t plan);
 
-/* Last error message of the calling thread ("" if none). */
-const char *demag_last_error(void);
+/* Error messages: with plan == NULL, the calling thread's latest one (any
+ * entry point, plan-less calls included); with a plan, the latest failed call
+ * on that plan ("" if none). */
+const char *demag_last_error(demag_plan_t plan);
 
 /* Name of a status code. */
 const char *demag_status_string(demag_status s);

@@ -128,7 +128,7 @@ def load(path: str | Path | None = None):
         "demag_get_timing": (S, [P, POINTER(c_double), POINTER(c_long), I]),
         "demag_launch_count": (c_long, [P]),
         "demag_plan_destroy": (None, [P]),
-        "demag_last_error": (ctypes.c_char_p, []),
+        "demag_last_error": (ctypes.c_char_p, [P]),
         "demag_status_string": (ctypes.c_char_p, [I]),
         "demag_energy_noalloc": (S, [I, I, I, D, D, D, I, P, P, P, P]),
         "demag_batch_create": (S, [I, P, P, I, POINTER(c_void_p)]),
@@ -182,7 +182,7 @@ def load(path: str | Path | None = None):
 
 def _check(status: int, where: str):
     if status != 0:
-        msg = load().demag_last_error()
+        msg = load().demag_last_error(None)
         raise DemagError(status, where, msg.decode() if msg else "")
 
 
@@ -387,8 +387,10 @@ def demag_plan_destroy(plan):
         load().demag_plan_destroy(_p(plan))
 
 
-def demag_last_error() -> str:
-    m = load().demag_last_error()
+def demag_last_error(plan=None) -> str:
+    """The calling thread's latest error message (plan None), or the latest
+    failed call's on that plan."""
+    m = load().demag_last_error(_p(plan))
     return m.decode() if m else ""
 
 

@@ -111,10 +111,20 @@ __global__ void k_guard_scan(const unsigned char *__restrict__ z, int n, unsigne
 }
 
 thread_local std::string g_err;
+// The plan whose entry point the calling thread is in (its failures are also
+// kept on the plan, for demag_last_error(plan)).
+thread_local demag_plan *g_err_plan = nullptr;
+
+struct PlanScope {
+    demag_plan *prev;
+    explicit PlanScope(demag_plan *p) : prev(g_err_plan) { g_err_plan = p; }
+    ~PlanScope() { g_err_plan = prev; }
+};
 
 demag_status fail(demag_status s, const std::string &msg)
 {
     g_err = msg;
+    if (g_err_plan) snprintf(g_err_plan->last_err, sizeof g_err_plan->last_err, "%s", msg.c_str());
     return s;
 }
 
@@ -886,7 +896,7 @@ void demag::set_last_error(const std::string &msg) { g_err = msg; }
 
 extern "C" {
 
-const char *demag_last_error(void) { return g_err.c_str(); }
+const char *demag_last_error(demag_plan_t plan) { return plan ? plan->last_err : g_err.c_str(); }
 
 const char *demag_status_string(demag_status s)
 {
@@ -1090,6 +1100,7 @@ demag_status sp_setup(demag_plan *p, cudaStream_t st)
 
 demag_status demag_tensor_setup(demag_plan_t p, void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (p->setup_done) return DEMAG_OK;
     DeviceGuard g(p->device);
@@ -1159,6 +1170,7 @@ demag_status demag_tensor_setup(demag_plan_t p, void *stream)
 
 demag_status demag_sp_potential(demag_plan_t p, const void *M, void *phi, void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (p->method != DEMAG_METHOD_SP) return fail(DEMAG_ERR_INVALID_ARG, "not a scalar-potential plan");
     if (!phi) return fail(DEMAG_ERR_INVALID_ARG, "phi is NULL");
@@ -1169,12 +1181,14 @@ demag_status demag_sp_potential(demag_plan_t p, const void *M, void *phi, void *
 
 demag_status demag_field(demag_plan_t p, const void *M, void *H, void *stream)
 {
+    PlanScope scope_(p);
     if (!H) return fail(DEMAG_ERR_INVALID_ARG, "H is NULL");
     return run_job(p, plain_job(M, H, nullptr), stream);
 }
 
 demag_status demag_field_adjoint(demag_plan_t p, const void *G, void *out, void *stream)
 {
+    PlanScope scope_(p);
     // N_ij = N_ji and N(-r) = N(r): the operator equals its adjoint.
     if (!out) return fail(DEMAG_ERR_INVALID_ARG, "out is NULL");
     if (p && p->method == DEMAG_METHOD_SP)
@@ -1184,6 +1198,7 @@ demag_status demag_field_adjoint(demag_plan_t p, const void *G, void *out, void 
 
 demag_status demag_field_energy(demag_plan_t p, const void *M, void *H, double *E_dev, void *stream)
 {
+    PlanScope scope_(p);
     if (!E_dev) return fail(DEMAG_ERR_INVALID_ARG, "E_dev is NULL");
     if (!H) return fail(DEMAG_ERR_INVALID_ARG, "H is NULL");
     return run_job(p, plain_job(M, H, E_dev), stream);
@@ -1191,6 +1206,7 @@ demag_status demag_field_energy(demag_plan_t p, const void *M, void *H, double *
 
 demag_status demag_energy(demag_plan_t p, const void *M, double *E_out, void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (!E_out) return fail(DEMAG_ERR_INVALID_ARG, "E_out is NULL");
     DeviceGuard g(p->device);
@@ -1205,6 +1221,7 @@ demag_status demag_energy(demag_plan_t p, const void *M, double *E_out, void *st
 
 demag_status demag_field_host(demag_plan_t p, const void *M_host, void *H_host, void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (!M_host || !H_host) return fail(DEMAG_ERR_INVALID_ARG, "host buffers must not be NULL");
     DeviceGuard g(p->device);
@@ -1224,6 +1241,7 @@ demag_status demag_field_host(demag_plan_t p, const void *M_host, void *H_host, 
 demag_status demag_energy_grad(demag_plan_t p, const void *m, const void *w, double Ms, double *E_dev,
                                void *grad, const double *gscale_dev, void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (p->method == DEMAG_METHOD_SP)
         return fail(DEMAG_ERR_UNSUPPORTED, "energy gradients need the adjoint, which scalar-potential plans do not build");
@@ -1240,12 +1258,14 @@ demag_status demag_energy_grad(demag_plan_t p, const void *m, const void *w, dou
 
 demag_status demag_field_host_async(demag_plan_t p, const void *M_host, void *H_host, void *stream)
 {
+    PlanScope scope_(p);
     return demag_field_energy_host_async(p, M_host, H_host, nullptr, stream);
 }
 
 demag_status demag_field_energy_host_async(demag_plan_t p, const void *M_host, void *H_host, double *E_host,
                                            void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (!M_host || !H_host) return fail(DEMAG_ERR_INVALID_ARG, "host buffers must not be NULL");
     if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
@@ -1288,6 +1308,7 @@ demag_status demag_field_energy_host_async(demag_plan_t p, const void *M_host, v
 
 demag_status demag_host_wait(demag_plan_t p)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (!p->async_ready) return DEMAG_OK;
     DeviceGuard g(p->device);
@@ -1300,6 +1321,7 @@ void demag_debug_fail_alloc(long n) { g_fail_alloc.store(n > 0 ? n : 0); }
 
 demag_status demag_plan_save(demag_plan_t p, const char *path)
 {
+    PlanScope scope_(p);
     if (!p || !path) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
     if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
     DeviceGuard g(p->device);
@@ -1396,6 +1418,7 @@ demag_status demag_plan_load(const char *path, demag_plan_t *out)
 
 demag_status demag_plan_info(demag_plan_t p, demag_info *info)
 {
+    PlanScope scope_(p);
     if (!p || !info) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
     info->nx = p->nx; info->ny = p->ny; info->nz = p->nz;
     info->px = p->Px; info->py = p->Py; info->pz = p->Pz;
@@ -1411,6 +1434,7 @@ demag_status demag_plan_info(demag_plan_t p, demag_info *info)
 
 demag_status demag_set_graphs(demag_plan_t p, int enable)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     DeviceGuard g(p->device);
     if (enable) {
@@ -1424,6 +1448,7 @@ demag_status demag_set_graphs(demag_plan_t p, int enable)
 
 demag_status demag_set_timing(demag_plan_t p, int enable)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     DeviceGuard g(p->device);
     if (enable && !p->ring) {
@@ -1445,6 +1470,7 @@ demag_status demag_set_timing(demag_plan_t p, int enable)
 
 demag_status demag_get_timing(demag_plan_t p, double *ms, long *counts, int n)
 {
+    PlanScope scope_(p);
     if (!p || !ms || !counts || n < 0 || n > 8) return fail(DEMAG_ERR_INVALID_ARG, "bad arguments");
     DeviceGuard g(p->device);
     if (p->ring) {
@@ -1460,6 +1486,7 @@ long demag_launch_count(demag_plan_t p) { return p ? p->launches : 0; }
 
 demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void *stream)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (!p->setup_done) return fail(DEMAG_ERR_NOT_SETUP, "demag_tensor_setup() has not run on this plan");
     DeviceGuard g(p->device);
@@ -1613,6 +1640,7 @@ demag_status demag_tune_padding(int nx, int ny, int nz, double dx, double dy, do
 
 demag_status demag_set_spectral_energy(demag_plan_t p, int enable)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     p->spectral_energy = enable != 0;
     return DEMAG_OK;
@@ -1620,6 +1648,7 @@ demag_status demag_set_spectral_energy(demag_plan_t p, int enable)
 
 demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     if (z) *z = p->zvariant;
     if (y) *y = p->yvariant;
@@ -1628,6 +1657,7 @@ demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
 
 demag_status demag_set_variants(demag_plan_t p, int z, int y)
 {
+    PlanScope scope_(p);
     if (!p || z < 0 || z > 7 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->zvariant = z;
     p->yvariant = y;
@@ -1636,6 +1666,7 @@ demag_status demag_set_variants(demag_plan_t p, int z, int y)
 
 demag_status demag_get_x_variant(demag_plan_t p, int *x)
 {
+    PlanScope scope_(p);
     if (!p || !x) return fail(DEMAG_ERR_INVALID_ARG, "NULL argument");
     *x = p->xvariant;
     return DEMAG_OK;
@@ -1643,6 +1674,7 @@ demag_status demag_get_x_variant(demag_plan_t p, int *x)
 
 demag_status demag_set_x_variant(demag_plan_t p, int x)
 {
+    PlanScope scope_(p);
     if (!p || x < 0 || x > 2) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->xvariant = x;
     return DEMAG_OK;
@@ -1650,6 +1682,7 @@ demag_status demag_set_x_variant(demag_plan_t p, int x)
 
 demag_status demag_check_pipeline(demag_plan_t p)
 {
+    PlanScope scope_(p);
     if (!p) return fail(DEMAG_ERR_INVALID_ARG, "plan is NULL");
     DeviceGuard g(p->device);
     if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");

@@ -868,7 +868,7 @@ demag_status demag_batch_create_ex(int n, const int *dims, const double *cells, 
                                               cells[3 * i + 1], cells[3 * i + 2], prec, opt, &b->plans[i]);
         if (s == DEMAG_OK) s = demag_tensor_setup(b->plans[i], nullptr);
         if (s != DEMAG_OK) {
-            demag::set_last_error(std::string("state ") + std::to_string(i) + ": " + demag_last_error());
+            demag::set_last_error(std::string("state ") + std::to_string(i) + ": " + demag_last_error(nullptr));
             free_batch(b);
             return s;
         }

@@ -188,6 +188,7 @@ cudaError_t sp_extract(const double2 *S, int comp, int Px, int Py, int Pz, int K
 
 // The opaque plan.
 struct demag_plan {
+    char last_err[320];  // message of the latest failed call on this plan (plain bytes: the struct is zeroed)
     int method;  // demag_method: DM (tensor) or SP (scalar potential)
     int nx, ny, nz;
     double dx, dy, dz;

@@ -96,3 +96,24 @@ def test_host_entry_allocation_failure():
     ref = p.field(Mh.cuda()).cpu()
     assert torch.equal(ref, Hh)
     p.close()
+
+
+def test_last_error_per_plan_and_per_thread():
+    """demag_last_error(plan) keeps the latest failed call on that plan;
+    demag_last_error(NULL) the calling thread's latest message."""
+    from paper_1204_4302_gb300 import binding as B
+    from paper_1204_4302_gb300.plan import Plan
+    p = Plan((8, 8, 8), (1e-9,) * 3, prec="f32")
+    q = Plan((8, 8, 8), (1e-9,) * 3, prec="f32")
+    assert B.demag_last_error(p.handle) == ""
+    with pytest.raises(B.DemagError) as ei:
+        B.demag_set_variants(p.handle, 99, 0)
+    msg = B.demag_last_error(p.handle)
+    assert msg and msg == B.demag_last_error() and msg in str(ei.value)
+    assert B.demag_last_error(q.handle) == ""
+    with pytest.raises(B.DemagError):
+        B.demag_tg_plan_create(2, 2, 2, 1e-9, 1e-9, 1e-9, 1)   # plan-less failure
+    assert B.demag_last_error() != msg
+    assert B.demag_last_error(p.handle) == msg
+    p.close()
+    q.close()
