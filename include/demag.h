@@ -261,13 +261,13 @@ demag_status demag_field_host(demag_plan_t plan, const void *M_host, void *H_hos
 
 /* Streaming variant of demag_field_host for sequences of host-resident
  * states: returns without synchronising. The upload runs on a copy stream,
- * the field on `stream`, the download on a second copy stream, through two
- * alternating device slots, so consecutive calls overlap one call's download
- * and the next call's upload with the fields. The caller must keep M_host
- * unchanged and must not read H_host until demag_host_wait() returns (or
- * until two further calls have been issued and waited for); page-locked
- * buffers are needed for the copies to overlap. Device buffers (two input
- * and two output fields) are allocated at the first call. */
+ * the field on `stream`, the download on a second copy stream, through three
+ * rotating device slots, so consecutive calls overlap one call's download
+ * and a later call's upload with each other and with the fields. The caller
+ * must keep M_host unchanged and must not read H_host until
+ * demag_host_wait() returns; page-locked buffers are needed for the copies
+ * to overlap. Device buffers (three input and three output fields) are
+ * allocated at the first call. */
 demag_status demag_field_host_async(demag_plan_t plan, const void *M_host, void *H_host, void *stream);
 
 /* Same, with the energy E = -(mu0/2) V sum M.H of each call written to

@@ -934,7 +934,7 @@ void demag_plan_destroy(demag_plan_t p)
     if (p->async_ready) {
         cudaStreamSynchronize(p->s_in);
         cudaStreamSynchronize(p->s_out);
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < demag_plan::kAsyncSlots; ++k) {
             dfree(p->aM[k]);
             dfree(p->aH[k]);
             dfree(p->aE[k]);
@@ -1273,7 +1273,7 @@ demag_status demag_field_energy_host_async(demag_plan_t p, const void *M_host, v
     if (!g.ok) return fail(DEMAG_ERR_CUDA, "cannot select the plan's device");
     const size_t bytes = 3 * (size_t)ncell(p) * elem_size(p);
     if (!p->async_ready) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < demag_plan::kAsyncSlots; ++k) {
             DEMAG_CUDA(dmalloc(&p->aM[k], bytes));
             DEMAG_CUDA(dmalloc(&p->aH[k], bytes));
             DEMAG_CUDA(dmalloc(&p->aE[k], sizeof(double)));
@@ -1289,7 +1289,7 @@ demag_status demag_field_energy_host_async(demag_plan_t p, const void *M_host, v
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int k = p->slot;
-    p->slot ^= 1;
+    p->slot = (p->slot + 1) % demag_plan::kAsyncSlots;
     // the slot's previous download must be done before its buffers are reused
     if (p->out_recorded[k]) DEMAG_CUDA(cudaStreamWaitEvent(p->s_in, p->ev_out[k], 0));
     DEMAG_CUDA(cudaMemcpyAsync(p->aM[k], M_host, bytes, cudaMemcpyHostToDevice, p->s_in));

@@ -217,12 +217,15 @@ struct demag_plan {
     double *e_dev;
     // host-buffer entry point buffers
     void *dM, *dH;
-    // asynchronous host entry point: two device slots, copy streams, events
-    void *aM[2], *aH[2];
-    double *aE[2];  // per-slot energy of the streamed host entry
+    // asynchronous host entry point: kAsyncSlots device slots, copy streams,
+    // events (three slots: the upload of call n + 2 does not wait for the
+    // download of call n, so uploads and downloads run at the same time)
+    static constexpr int kAsyncSlots = 3;
+    void *aM[kAsyncSlots], *aH[kAsyncSlots];
+    double *aE[kAsyncSlots];  // per-slot energy of the streamed host entry
     cudaStream_t s_in, s_out;
-    cudaEvent_t ev_in[2], ev_done[2], ev_out[2];
-    bool out_recorded[2];
+    cudaEvent_t ev_in[kAsyncSlots], ev_done[kAsyncSlots], ev_out[kAsyncSlots];
+    bool out_recorded[kAsyncSlots];
     int slot;
     bool async_ready;
     bool setup_done;

@@ -213,8 +213,8 @@ def test_host_entry_point_matches_device():
     assert torch.equal(Hd, Hh)
     Hh2 = plan.field_host(torch.tensor(M, dtype=torch.float32))  # pageable
     assert torch.equal(Hd, Hh2)
-    # streamed: three states in flight through the two device slots
-    Ms = [torch.tensor(inputs.random_unit(n, seed=50 + i) * 8e5, dtype=torch.float32).pin_memory() for i in range(5)]
+    # streamed: seven states through the three rotating device slots
+    Ms = [torch.tensor(inputs.random_unit(n, seed=50 + i) * 8e5, dtype=torch.float32).pin_memory() for i in range(7)]
     Hs = [torch.empty_like(m).pin_memory() for m in Ms]
     for m, h in zip(Ms, Hs):
         plan.field_host_async(m, h)
