@@ -468,7 +468,9 @@ demag_status demag_tune_padding(int nx, int ny, int nz, double dx, double dy, do
  *    setup, about the size of the spectrum), both one tile ahead; the
  *    length-512 transforms run as 2 x 16 x 16 with packed FP32x2 butterflies
  *    (z length 512, at most 256 input rows), 7 = as 6 with 4-column tiles and
- *    two CTAs per SM.
+ *    two CTAs per SM, 8 = variant 0 with an 8-point second stage (8 complex
+ *    values per component and thread across the product, half the registers
+ *    and shared memory) and two CTAs per SM (z lengths 32..128).
  * y: 0 = two-stage column transform, 1 = swapped radix order (y lengths 32,
  *    128, 512), 2 = three-stage transform with more CTAs per SM (y lengths
  *    512 and 1024), 3 = as 2, with the forward pass by persistent CTAs that

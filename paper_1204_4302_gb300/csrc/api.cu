@@ -392,12 +392,12 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     }
     // z forward . product . z inverse
     e = cudaErrorNotSupported;
-    if (p->zvariant >= 6 && f32 && p->ntile)  // persistent TMA forms, FP32 only
+    if ((p->zvariant == 6 || p->zvariant == 7) && f32 && p->ntile)  // persistent TMA forms, FP32 only
         e = Passes<T>::zconv_ws(Pz, S2, Kx, Py, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz,
                                 (const T *)(const void *)p->ntile, twz, st, p->zvariant == 7 ? 4 : 8);
     if (e == cudaErrorNotSupported)
         e = Passes<T>::zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat, Py, Kx,
-                             twz, 1, st, p->zvariant >= 6 ? 0 : p->zvariant);
+                             twz, 1, st, (p->zvariant == 6 || p->zvariant == 7) ? 0 : p->zvariant);
     if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("z convolution: ") + cudaGetErrorString(e));
     p->launches++;
     tm.mark();
@@ -1513,6 +1513,7 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
     if (z2 && dm && p->Pz == 512) zs.push_back(2);  // 256 threads: the product stage uses every thread
     if (z2 && dm && p->Pz >= 64 && p->Pz <= 512) zs.push_back(3);  // persistent, pipelined
     if (z2 && dm && p->Pz >= 32 && p->Pz <= 512) zs.push_back(4);   // half tile, two CTAs per SM
+    if (z2 && dm && p->Pz >= 32 && p->Pz <= 128) zs.push_back(8);   // 8-point second stage, two CTAs per SM
     if (z2 && p->Pz >= 32 && p->Pz <= 256) zs.push_back(5);   // persistent, TMA-staged input (DM and SP)
     if (dm && p->ntile) {  // persistent, TMA input and tensor tiles, FP32: 8 or 4 columns per tile
         zs.push_back(6);
@@ -1658,7 +1659,7 @@ demag_status demag_get_variants(demag_plan_t p, int *z, int *y)
 demag_status demag_set_variants(demag_plan_t p, int z, int y)
 {
     PlanScope scope_(p);
-    if (!p || z < 0 || z > 7 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
+    if (!p || z < 0 || z > 8 || y < 0 || y > 3) return fail(DEMAG_ERR_INVALID_ARG, "bad plan or variant");
     p->zvariant = z;
     p->yvariant = y;
     return DEMAG_OK;

@@ -85,19 +85,24 @@ bool y_geom(int L, int &cols_per_tile, size_t &sm)
     return false;
 }
 
+// z tiles of the batch kernels: the 8-point second stage (variant 8) for
+// lengths 32..128, the two-stage variant 0 otherwise.
+template <int L> constexpr int kBatchZV = (L >= 32 && L <= 128) ? 8 : 0;
+
 template <int L> constexpr size_t z_smem()
 {
-    return 3 * swsize(L * ZShape<float, L, 0>::TC) * 8 + (size_t)(L / 2 + 1) * 6 * ZShape<float, L, 0>::TC * 4;
+    using Sh = ZShape<float, L, kBatchZV<L>>;
+    return 3 * swsize(L * Sh::TC) * 8 + (size_t)(L / 2 + 1) * 6 * Sh::TC * 4;
 }
 
 bool z_geom(int L, int &cols_per_tile, size_t &sm)
 {
     switch (L) {
     case 4: case 8: case 16: cols_per_tile = kThreads; sm = 0; return true;
-    case 32: cols_per_tile = ZShape<float, 32, 0>::TC; sm = z_smem<32>(); return true;
-    case 64: cols_per_tile = ZShape<float, 64, 0>::TC; sm = z_smem<64>(); return true;
-    case 128: cols_per_tile = ZShape<float, 128, 0>::TC; sm = z_smem<128>(); return true;
-    case 256: cols_per_tile = ZShape<float, 256, 0>::TC; sm = z_smem<256>(); return true;
+    case 32: cols_per_tile = ZShape<float, 32, kBatchZV<32>>::TC; sm = z_smem<32>(); return true;
+    case 64: cols_per_tile = ZShape<float, 64, kBatchZV<64>>::TC; sm = z_smem<64>(); return true;
+    case 128: cols_per_tile = ZShape<float, 128, kBatchZV<128>>::TC; sm = z_smem<128>(); return true;
+    case 256: cols_per_tile = ZShape<float, 256, kBatchZV<256>>::TC; sm = z_smem<256>(); return true;
     }
     return false;
 }
@@ -210,10 +215,10 @@ __device__ __forceinline__ void run_item_t(const BatchState &st, int tile, unsig
         case 4: k_z_conv1_tile<float, 4, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, tile, sm); break;
         case 8: k_z_conv1_tile<float, 8, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, tile, sm); break;
         case 16: k_z_conv1_tile<float, 16, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, tile, sm); break;
-        case 32: k_z_conv2_tile<float, 32, 0, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
-        case 64: k_z_conv2_tile<float, 64, 0, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
-        case 128: k_z_conv2_tile<float, 128, 0, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
-        case 256: k_z_conv2_tile<float, 256, 0, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
+        case 32: k_z_conv2_tile<float, 32, kBatchZV<32>, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
+        case 64: k_z_conv2_tile<float, 64, kBatchZV<64>, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
+        case 128: k_z_conv2_tile<float, 128, kBatchZV<128>, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
+        case 256: k_z_conv2_tile<float, 256, kBatchZV<256>, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm); break;
         }
         break;
     }
@@ -282,7 +287,8 @@ __device__ __forceinline__ void run_item_L(const BatchState &st, int tile, unsig
         const int ncols = Py * Kx;
         const int64_t ss = Kxp, rs = (int64_t)Py * Kxp, cs = (int64_t)nz * Py * Kxp;
         if constexpr (L <= 16) k_z_conv1_tile<float, L, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, tile, sm);
-        else k_z_conv2_tile<float, L, 0, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1, tile, sm);
+        else k_z_conv2_tile<float, L, kBatchZV<L>, true>(st.S2, ncols, Kx, ss, rs, cs, nz, st.nhat, Py, Kx, st.tw[2], 1,
+                                                        tile, sm);
     } else if constexpr (PASS == 4) {
         XOut<float> o;
         o.out = st.H; o.out_rs = nx; o.scale = 1.f / ((float)Px * Py * Pz); o.oscale = 1.f; o.wcell = nullptr;

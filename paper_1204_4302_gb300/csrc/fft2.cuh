@@ -56,11 +56,17 @@ template <typename T, int L, int V = 0> struct ColShape {
 // Variant 1: half the columns.
 // Variant 4: variant 0's thread layout on half the columns, compiled for two
 // resident CTAs per SM (one CTA's loads overlap the other's arithmetic).
+// Variant 8 (lengths 32..128): an 8-point second stage (three components of
+// 8 complex values per thread across the product instead of 16), half-width
+// tiles and two CTAs per SM.
+template <int L, int V> struct ZRadixV {
+    static constexpr int R2 = (V == 8 && L >= 32) ? 8 : ZRadix<L>::R2, R1 = L / R2;
+};
 template <typename T, int L, int V = 0> struct ZShape {
-    static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2;
+    static constexpr int R1 = ZRadixV<L, V>::R1, R2 = ZRadixV<L, V>::R2;
     static constexpr int TC = ((V == 1 || V == 4) ? Tile2<T>::NT / 2 : Tile2<T>::NT) / R1;
     static constexpr int NT = ((V == 0 || V == 4) && R1 == 2 * R2) ? 3 * TC * R2 : TC * R1;
-    static constexpr int MIN_CTAS = V == 4 ? 2 : 1;
+    static constexpr int MIN_CTAS = (V == 4 || V == 8) ? 2 : 1;
 };
 
 // v[r] *= W_L^(r * k) (or its conjugate), table W_L^m at tw[m * twstride]

@@ -748,6 +748,14 @@ cudaError_t Passes<T>::zconv(int L, C *S, int ncols, int width, int64_t ss, int6
              : variant == 2 ? zconv_launch<LL, 2>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
              : variant == 4 ? zconv_launch<LL, 4>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st) \
                             : zconv_launch<LL, 0>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+    if (variant == 8) {  // 8-point second stage, two CTAs per SM (lengths 32..128)
+        switch (L) {
+        case 32: return zconv_launch<32, 8>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        case 64: return zconv_launch<64, 8>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        case 128: return zconv_launch<128, 8>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, twstride, st);
+        default: variant = 0;
+        }
+    }
     switch (L) { DEMAG_CASE(32) DEMAG_CASE(64) DEMAG_CASE(128) DEMAG_CASE(256) DEMAG_CASE(512) default: return cudaErrorInvalidValue; }
 #undef DEMAG_CASE
 }

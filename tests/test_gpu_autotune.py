@@ -21,7 +21,8 @@ def _built():
 
 
 @pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f64", 1e-12)])
-@pytest.mark.parametrize("n", [(20, 256, 40), (9, 17, 100), (30, 64, 16), (12, 40, 256), (7, 33, 60), (6, 400, 5)])
+@pytest.mark.parametrize("n", [(20, 256, 40), (9, 17, 100), (30, 64, 16), (12, 40, 256), (7, 33, 60), (6, 400, 5),
+                               (16, 24, 32)])
 def test_every_variant_matches_oracle(n, prec, tol):
     from paper_1204_4302_gb300.plan import Plan
     d = (2e-9, 2e-9, 2e-9)
@@ -31,7 +32,7 @@ def test_every_variant_matches_oracle(n, prec, tol):
     p = Plan(n, d, prec=prec)
     Mt = torch.tensor(M, dtype=dt, device="cuda")
     for x in (0, 1, 2):
-        for z in (0, 1, 2, 3, 4, 5, 6, 7):
+        for z in (0, 1, 2, 3, 4, 5, 6, 7, 8):
             for y in (0, 1, 2, 3):
                 p.set_variants(z, y, x)
                 H = p.field(Mt).double().cpu().numpy()

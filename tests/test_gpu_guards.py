@@ -99,8 +99,8 @@ def test_mixed_radix_grids_stay_in_bounds(n, pad, prec):
     _exercise(n, (1e-9, 1.1e-9, 0.9e-9), prec, pad=pad)
 
 
-@pytest.mark.parametrize("zv", [0, 1, 2, 3, 4, 5, 6, 7])
-@pytest.mark.parametrize("n", [(33, 17, 5), (40, 6, 100), (9, 17, 129), (24, 24, 24)])
+@pytest.mark.parametrize("zv", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("n", [(33, 17, 5), (40, 6, 100), (9, 17, 129), (24, 24, 24), (20, 30, 16)])
 def test_power_of_two_z_forms_stay_in_bounds(n, zv):
     _exercise(n, (2e-9, 1.5e-9, 1e-9), "f32", zv=zv)
 
