@@ -870,6 +870,19 @@ template <typename T, int L> struct XShape {
     static constexpr int RS = swsize(L);                 // padded row in shared memory
 };
 
+// Position in an x row's exchange of element j R1 + c (written by stage-1
+// thread j as its output c, read by stage-2 thread c as its input j). For
+// R1 = 16 the column is XORed with j: the 16 writers of one column and the 16
+// readers of one group then hit 16 different 8-byte bank pairs (two rows per
+// warp: two wavefronts, the minimum). Otherwise one padding element per 32
+// (j R1 % 32 + c < 32 there).
+template <int R1>
+__device__ __forceinline__ int xex(int j, int c)
+{
+    if constexpr (R1 == 16) return j * 16 + (c ^ (j & 15));
+    else return sw(j * R1) + c;
+}
+
 template <typename C>
 __device__ __forceinline__ C shfl_c(C v, int lane)
 {
@@ -926,7 +939,7 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
         else RegDFT<R1, false, C>::run(u);
         C *s = sm + rr * RS;
 #pragma unroll
-        for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
+        for (int r = 0; r < R1; ++r) s[xex<R1>(j1, r)] = u[r];
     }
     __syncthreads();
     // stage 2 + split: thread (row, j2) computes X[k], k = j2 + r R1
@@ -935,7 +948,7 @@ __device__ __forceinline__ void k_x_fwd2_tile(XIn<T> a, int nrows, int nvalid, t
         const C *s = sm + rr * RS;
         C v[R2];
 #pragma unroll
-        for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
+        for (int r = 0; r < R2; ++r) v[r] = s[xex<R1>(r, j2)];
 #pragma unroll
         for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], __ldg(&twx[2 * r * j2]));
         RegDFT<R2, false, C>::run(v);
@@ -971,6 +984,35 @@ k_x_fwd2(XIn<T> a, int nrows, int nvalid, typename Cplx<T>::type *__restrict__ o
 // energy's reference field rows (o.Mref, nvalid a multiple of 4 and rows
 // 16-byte aligned) are copied to shared memory with cp.async at the start, so
 // their loads overlap the transform instead of following it.
+// Epilogue of an inverse x row: the real outputs x, x + 1 (one complex value
+// of the half-length transform, scaled), stored and, with the energy, dotted
+// with M. Without a cell weight and with even rows, one 8-byte (FP32) or
+// 16-byte (FP64) access per pair; otherwise element by element. mref: the
+// row of M in shared memory (MP) or nullptr (then M from global memory).
+template <typename T>
+__device__ __forceinline__ void x_out_pair(const XOut<T> &o, int row, int x, T h0, T h1, T oscale, int nvalid,
+                                           const T *mref, T &acc)
+{
+    using C = typename Cplx<T>::type;
+    const int64_t idx = (int64_t)row * o.out_rs + x;
+    if (!o.wcell && (o.out_rs & 1) == 0 && x + 1 < nvalid) {
+        if (o.out) *reinterpret_cast<C *>(o.out + idx) = cmk<C>(h0 * oscale, h1 * oscale);
+        if (o.partials) {
+            const C m = mref ? *reinterpret_cast<const C *>(mref + x) : *reinterpret_cast<const C *>(o.Mref + idx);
+            acc += o.mscale * (m.x * h0 + m.y * h1);
+        }
+        return;
+    }
+    const T hv[2] = {h0, h1};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        if (x + u >= nvalid) continue;
+        const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x + u);
+        if (o.out) o.out[idx + u] = hv[u] * oscale * w;
+        if (o.partials) acc += o.mscale * w * (mref ? mref[x + u] : o.Mref[idx + u]) * hv[u];
+    }
+}
+
 template <typename T, int L, bool CG, bool P1 = false, bool MP = false>
 __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__restrict__ in, int64_t in_rs, int nrows, int nvalid, XOut<T> o,
          const typename Cplx<T>::type *__restrict__ twx, int tile, unsigned char *smraw)
@@ -1012,7 +1054,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         RegDFT<R1, true, C>::run(u);
         C *s = sm + rr * RS;
 #pragma unroll
-        for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
+        for (int r = 0; r < R1; ++r) s[xex<R1>(j1, r)] = u[r];
     }
     if constexpr (MP) cp_async_wait_all();
     __syncthreads();
@@ -1022,7 +1064,7 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
         const C *s = sm + rr * RS;
         C v[R2];
 #pragma unroll
-        for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
+        for (int r = 0; r < R2; ++r) v[r] = s[xex<R1>(r, j2)];
 #pragma unroll
         for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
         if constexpr (P1) RegDFTHalfOutP1<R2, true, C>::run(v);
@@ -1033,16 +1075,8 @@ __device__ __forceinline__ void k_x_inv2_tile(const typename Cplx<T>::type *__re
 #pragma unroll
             for (int r = 0; r < (P1 ? R2 / 2 + 1 : R2 / 2); ++r) {  // z[n], n = j2 + r R1 (< L/2 unless P1)
                 const int n = j2 + r * R1;
-                const T hv[2] = {v[r].x * o.scale, v[r].y * o.scale};
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int x = 2 * n + u;
-                    if (x >= nvalid) continue;
-                    const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
-                    const int64_t idx = (int64_t)row * o.out_rs + x;
-                    if (o.out) o.out[idx] = hv[u] * oscale * w;
-                    if (o.partials) acc += o.mscale * w * (MP ? smM[rr * L + x] : o.Mref[idx]) * hv[u];
-                }
+                x_out_pair<T>(o, row, 2 * n, v[r].x * o.scale, v[r].y * o.scale, oscale, nvalid,
+                              MP ? smM + rr * L : nullptr, acc);
             }
         }
     }

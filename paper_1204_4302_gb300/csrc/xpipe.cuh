@@ -191,7 +191,7 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
             RegDFTHalfIn<R1, false, C>::run(u);
             C *s = sm + rr * RS;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
+            for (int r = 0; r < R1; ++r) s[xex<R1>(j1, r)] = u[r];
         }
         __syncthreads();  // buffer b consumed, exchange rows written
         if (threadIdx.x == 0) {
@@ -207,7 +207,7 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
             const C *s = sm + rr * RS;
             C v[R2];
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
+            for (int r = 0; r < R2; ++r) v[r] = s[xex<R1>(r, j2)];
 #pragma unroll
             for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], __ldg(&twx[2 * r * j2]));
             RegDFT<R2, false, C>::run(v);
@@ -303,7 +303,7 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
         if (act1) {
             C *s = sm + rr1 * RS;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) s[sw(j1 * R1) + r] = u[r];  // j1 R1 % 32 + r < 32
+            for (int r = 0; r < R1; ++r) s[xex<R1>(j1, r)] = u[r];
         }
         __syncthreads();
         T acc = 0;
@@ -312,7 +312,7 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
             const C *s = sm + rr * RS;
             C v[R2];
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[r] = s[j2 + r * R1 + (r * R1) / 32];  // = sw(j2 + r R1), j2 < R1
+            for (int r = 0; r < R2; ++r) v[r] = s[xex<R1>(r, j2)];
 #pragma unroll
             for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], __ldg(&twx[2 * r * j2]));
             if constexpr (P1) RegDFTHalfOutP1<R2, true, C>::run(v);
@@ -321,16 +321,7 @@ k_x_inv_tma(const typename Cplx<T>::type *__restrict__ in, int in_rs, int nrows,
 #pragma unroll
                 for (int r = 0; r < (P1 ? R2 / 2 + 1 : R2 / 2); ++r) {
                     const int n = j2 + r * R1;
-                    const T hv[2] = {v[r].x * o.scale, v[r].y * o.scale};
-#pragma unroll
-                    for (int uu = 0; uu < 2; ++uu) {
-                        const int x = 2 * n + uu;
-                        if (x >= nvalid) continue;
-                        const T w = cell_weight(o.wcell, row, o.rows_per_comp, o.out_rs, x);
-                        const int64_t idx = (int64_t)row * o.out_rs + x;
-                        if (o.out) o.out[idx] = hv[uu] * oscale * w;
-                        if (o.partials) acc += o.mscale * w * o.Mref[idx] * hv[uu];
-                    }
+                    x_out_pair<T>(o, row, 2 * n, v[r].x * o.scale, v[r].y * o.scale, oscale, nvalid, nullptr, acc);
                 }
             }
         }

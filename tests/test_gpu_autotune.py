@@ -80,7 +80,7 @@ def test_autotune_picks_and_caches(tmp_path, monkeypatch):
     ms = p.autotune(use_cache=True)
     assert ms > 0
     z, y = p.variants()
-    assert z in (0, 1, 3, 4, 5) and y in (0, 1, 2, 3)
+    assert z in (0, 1, 3, 4, 5, 8) and y in (0, 1, 2, 3)
     text = cache.read_text()
     assert "f32|128x256x128|64x128x64" in text
     p2 = Plan(n, d, prec="f32")
