@@ -1192,6 +1192,48 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+PASS_KERNELS = {"x_fwd": "k_x_fwd_tma", "y_fwd": "k_col3", "z_conv": "k_z_ws", "y_inv": "k_col3", "x_inv": "k_x_inv2"}
+
+
+def write_traffic(logs, command, workload):
+    """profiles/traffic.json from ncu CSV logs (--metrics dram__bytes_read.sum,
+    dram__bytes_write.sum,gpu__time_duration.sum, one or two launches per log
+    of the 256^3 step): per pass its kernel's DRAM bytes per launch and per
+    cell, keyed by the hash of the step-kernel sources. The y passes share a
+    kernel template: the first captured k_col3 launch of a log is the forward
+    pass, the second the inverse one."""
+    import csv as _csv
+    launches = []  # (kernel name, {metric: value}) in capture order
+    for path in logs:
+        with open(path) as fh:
+            rows = [r for r in _csv.reader(line for line in fh if line.startswith('"'))]
+        head, body = rows[0], rows[1:]
+        ki, ii, mi, vi = head.index("Kernel Name"), head.index("ID"), head.index("Metric Name"), head.index("Metric Value")
+        by_id = {}
+        for r in body:
+            ent = by_id.setdefault(r[ii], (r[ki], {}))
+            ent[1][r[mi]] = float(r[vi].replace(",", ""))
+        launches += [by_id[k] for k in sorted(by_id, key=int)]
+    cells = N_GRID[0] * N_GRID[1] * N_GRID[2]
+    out, col3 = {}, [l for l in launches if "k_col3" in l[0]]
+    for name, pat in PASS_KERNELS.items():
+        if pat == "k_col3":
+            pick = col3[0] if name == "y_fwd" and col3 else (col3[1] if len(col3) > 1 else None)
+        else:
+            pick = next((l for l in launches if pat in l[0]), None)
+        if pick is None:
+            continue
+        kname, m = pick
+        rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
+        short = kname.split("(")[0].replace("void ", "").replace("demag::", "").strip()
+        out[name] = {"kernel": short, "source_hash": source_hash(), "dram_read_bytes": rd, "dram_write_bytes": wr,
+                     "bytes_per_cell": (rd + wr) / cells, "ncu_ms": m["gpu__time_duration.sum"] / 1e6,
+                     "workload": workload, "command": command}
+    with open(TRAFFIC, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps({k: v["bytes_per_cell"] for k, v in out.items()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1218,7 +1260,15 @@ def main():
     ap.add_argument("--variants", default="", help="fixed z,y,x kernel variants instead of autotuning")
     ap.add_argument("--grid", default="", help="grid edge n (cubic) or nx,ny,nz (default 256^3, the headline; "
                                                "other grids are for profiling runs)")
+    ap.add_argument("--write-traffic", nargs="+", default=None, metavar="NCU_CSV",
+                    help="write profiles/traffic.json from ncu CSV logs of the step kernels and exit "
+                         "(with --traffic-command, the command that produced them)")
+    ap.add_argument("--traffic-command", default="")
     args = ap.parse_args()
+    if args.write_traffic:
+        write_traffic(args.write_traffic, args.traffic_command,
+                      "256^3 FP32 field + energy, padded 512^3, z variant 6, y 2, x 1")
+        return
     if args.warmup < 3:
         args.warmup = 3
     global N_GRID
