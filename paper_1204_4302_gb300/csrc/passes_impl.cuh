@@ -393,6 +393,10 @@ cudaError_t Passes<T>::zconv_ws_energy(int L, C *S, int Kx, int Py, int64_t ss, 
     }
 }
 
+// Spectral-energy z pass: the 8-point second stage (variant 8) for lengths
+// 32..128, as in the field pipeline's fastest form there.
+template <int L> constexpr int kZEnergyV = (L >= 32 && L <= 128) ? 8 : 0;
+
 template <typename T>
 int Passes<T>::zenergy_blocks(int L, int Py, int Kx)
 {
@@ -404,10 +408,10 @@ int Passes<T>::zenergy_blocks(int L, int Py, int Kx)
     } else {
         int tc;
         switch (L) {
-        case 32: tc = ZShape<T, 32, 0>::TC; break;
-        case 64: tc = ZShape<T, 64, 0>::TC; break;
-        case 128: tc = ZShape<T, 128, 0>::TC; break;
-        case 256: tc = ZShape<T, 256, 0>::TC; break;
+        case 32: tc = ZShape<T, 32, kZEnergyV<32>>::TC; break;
+        case 64: tc = ZShape<T, 64, kZEnergyV<64>>::TC; break;
+        case 128: tc = ZShape<T, 128, kZEnergyV<128>>::TC; break;
+        case 256: tc = ZShape<T, 256, kZEnergyV<256>>::TC; break;
         default: tc = ZShape<T, 512, 0>::TC; break;
         }
         n = (ncols + tc - 1) / tc;
@@ -435,13 +439,14 @@ cudaError_t Passes<T>::zconv_energy(int L, C *S, int ncols, int width, int64_t s
     }
 #define DEMAG_CASE(LL)                                                                                     \
     case LL: {                                                                                             \
-        using Sh = ZShape<T, LL, 0>;                                                                       \
+        constexpr int V = kZEnergyV<LL>;                                                                   \
+        using Sh = ZShape<T, LL, V>;                                                                       \
         const size_t sm = 3 * swsize(LL * Sh::TC) * sizeof(C) + (LL / 2 + 1) * 6 * Sh::TC * sizeof(T);     \
-        cudaError_t e = allow_smem<k_z_energy2<T, LL, 0>>(sm);                                             \
+        cudaError_t e = allow_smem<k_z_energy2<T, LL, V>>(sm);                                             \
         if (e != cudaSuccess) return e;                                                                    \
         const int grid = (ncols + Sh::TC - 1) / Sh::TC;                                                    \
         *nparts = grid;                                                                                    \
-        k_z_energy2<T, LL, 0><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, \
+        k_z_energy2<T, LL, V><<<grid, Sh::NT, sm, st>>>(S, ncols, width, ss, rs, cs, nrows, nhat, Py, Kx, tw, \
                                                         twstride, partials);                              \
         return cudaGetLastError();                                                                         \
     }
