@@ -5,8 +5,9 @@
 // N_ij(R) = (1/V) Int_cell(R) Int_cell(0) G_ij(r - r') dr' dr,
 // G_ij(r) = -(1/4pi) d_i d_j (1/|r|),  positive definite at R = 0 (trace 1).
 //
-// One thread per offset R = (i dx, j dy, k dz), 0 <= i < nx etc. (the other
-// octants follow by parity). Three regimes, all in FP64 with lengths scaled
+// Offsets R = (i dx, j dy, k dz), 0 <= i < nx etc. (the other octants follow
+// by parity): far offsets one thread each, near and separated ones one warp
+// each (k_tensor_octant_warp). Three regimes, all in FP64 with lengths scaled
 // by the largest cell edge (N is scale invariant):
 //   near  (cells touch: |i|,|j|,|k| <= 1): Newell's closed form, the
 //         27-point second-difference stencil of f and g (Newell, Williams
@@ -124,28 +125,6 @@ __device__ double newell_g(double x, double y, double z)
     return sgn * v;
 }
 
-__device__ void near_closed(double X, double Y, double Z, double a, double b, double c, double *out)
-{
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int p = -1; p <= 1; ++p) {
-        const double wp = p == 0 ? 2.0 : -1.0, x = X + p * a;
-        for (int q = -1; q <= 1; ++q) {
-            const double wq = q == 0 ? 2.0 : -1.0, y = Y + q * b;
-            for (int t = -1; t <= 1; ++t) {
-                const double wt = wp * wq * (t == 0 ? 2.0 : -1.0), z = Z + t * c;
-                s[0] += wt * newell_f(x, y, z);
-                s[1] += wt * newell_f(y, x, z);
-                s[2] += wt * newell_f(z, y, x);
-                s[3] += wt * newell_g(x, y, z);
-                s[4] += wt * newell_g(x, z, y);
-                s[5] += wt * newell_g(y, z, x);
-            }
-        }
-    }
-    const double k = 1.0 / (4.0 * 3.14159265358979323846 * a * b * c);
-    for (int i = 0; i < 6; ++i) out[i] = s[i] * k;
-}
-
 __device__ int half_axis_nodes(double gap, double d)
 {
     const double b = gap / d;
@@ -161,44 +140,6 @@ __device__ __forceinline__ void tent_node(int n, int i, double d, double &u, dou
     const double t = 0.5 * d * (1.0 + c_glx[base + g]);
     w = 0.5 * c_glw[base + g] * (1.0 - t / d);
     u = (i & 1) ? -t : t;
-}
-
-__device__ void mid_quadrature(double X, double Y, double Z, double a, double b, double c, double *out)
-{
-    const double gx = fmax(0.0, fabs(X) - a), gy = fmax(0.0, fabs(Y) - b), gz = fmax(0.0, fabs(Z) - c);
-    const double gap = sqrt(gx * gx + gy * gy + gz * gz);
-    const int nx = half_axis_nodes(gap, a), ny = half_axis_nodes(gap, b), nz = half_axis_nodes(gap, c);
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < 2 * nz; ++k) {
-        double uz, wz;
-        tent_node(nz, k, c, uz, wz);
-        const double rz = Z + uz;
-        for (int j = 0; j < 2 * ny; ++j) {
-            double uy, wy;
-            tent_node(ny, j, b, uy, wy);
-            const double ry = Y + uy;
-            double p[6] = {0, 0, 0, 0, 0, 0};
-            for (int i = 0; i < 2 * nx; ++i) {
-                double ux, wx;
-                tent_node(nx, i, a, ux, wx);
-                const double rx = X + ux;
-                const double r2 = rx * rx + ry * ry + rz * rz;
-                const double ir = rsqrt(r2);
-                const double ir2 = ir * ir;
-                const double f = wx * ir2 * ir2 * ir;  // w / r^5
-                p[0] += f * (3.0 * rx * rx - r2);
-                p[1] += f * (3.0 * ry * ry - r2);
-                p[2] += f * (3.0 * rz * rz - r2);
-                p[3] += f * 3.0 * rx * ry;
-                p[4] += f * 3.0 * rx * rz;
-                p[5] += f * 3.0 * ry * rz;
-            }
-            const double w = wy * wz;
-            for (int q = 0; q < 6; ++q) s[q] += w * p[q];
-        }
-    }
-    const double k = -a * b * c / (4.0 * 3.14159265358979323846);
-    for (int q = 0; q < 6; ++q) out[q] = k * s[q];
 }
 
 // Index of the multi-index (b1, b2, n - b1 - b2) among all of order <= n.
@@ -432,61 +373,74 @@ __global__ void k_extract(const double2 *__restrict__ S, int comp, int Kx, int P
 
 constexpr int kFinalizeThreads = 256;
 
+// Compensated pair sum (s, c) + (s2, c2) -> (s, c): Neumaier's two-sum of the
+// leading parts, the error and both compensations in c.
+__device__ __forceinline__ void two_sum_add(double &s, double &c, double s2, double c2)
+{
+    const double t = s + s2;
+    const double e = fabs(s) >= fabs(s2) ? (s - t) + s2 : (s2 - t) + s;
+    c += c2 + e;
+    s = t;
+}
+
+// Warp-wide compensated sum by shuffles (five levels, fixed pairing).
+__device__ __forceinline__ void warp_two_sum(double &s, double &c)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        two_sum_add(s, c, s2, c2);
+    }
+}
+
 // Sum of n FP64 partials times `factor` into *E. The CUDA cores' FP64 rate
 // per SM is low on this GPU, so the sum is spread over up to kFinalizeBlocks
-// CTAs: CTA b sums the contiguous chunk b (Neumaier-compensated per thread,
-// then a tree of compensated pairs) into scratch[2b], scratch[2b + 1]; the
-// CTA that finishes last (a counter after the scratch) adds the CTA results
-// in index order, writes *E and resets the counter. The result does not
-// depend on which CTA finishes last.
+// CTAs and kept shallow: CTA b sums the contiguous chunk b (Neumaier-
+// compensated per thread, then warp shuffles and one shared-memory step over
+// the warps) into scratch[2b], scratch[2b + 1]; the CTA that finishes last (a
+// counter after the scratch) combines the CTA results the same way in its
+// first two warps, writes *E and resets the counter. The pairing is fixed, so
+// the result does not depend on which CTA finishes last.
 __global__ void __launch_bounds__(kFinalizeThreads) k_energy_finalize(const double *__restrict__ partials, int n,
                                                                       double factor, double *__restrict__ E,
                                                                       double *__restrict__ scratch)
 {
-    __shared__ double ss[kFinalizeThreads], sc[kFinalizeThreads];
+    constexpr int NW = kFinalizeThreads / 32;
+    __shared__ double ss[NW], sc[NW];
     __shared__ bool s_last;
     const int nb = gridDim.x, chunk = (n + nb - 1) / nb;
     const int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double s = 0.0, c = 0.0;
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double v = partials[i];
-        const double t = s + v;
-        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-        s = t;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) two_sum_add(s, c, partials[i], 0.0);
+    warp_two_sum(s, c);
+    if (lane == 0) {
+        ss[warp] = s;
+        sc[warp] = c;
     }
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) {
-            const double a = ss[threadIdx.x], b = ss[threadIdx.x + w];
-            const double t = a + b;
-            const double e = fabs(a) >= fabs(b) ? (a - t) + b : (b - t) + a;
-            ss[threadIdx.x] = t;
-            sc[threadIdx.x] += sc[threadIdx.x + w] + e;
-        }
-        __syncthreads();
-    }
     unsigned int *count = reinterpret_cast<unsigned int *>(scratch + 2 * kFinalizeBlocks);
-    if (threadIdx.x == 0) {
-        scratch[2 * blockIdx.x] = ss[0];
-        scratch[2 * blockIdx.x + 1] = sc[0];
-        __threadfence();
-        s_last = atomicAdd(count, 1u) == (unsigned)(nb - 1);
+    if (warp == 0) {
+        s = lane < NW ? ss[lane] : 0.0;
+        c = lane < NW ? sc[lane] : 0.0;
+        warp_two_sum(s, c);
+        if (lane == 0) {
+            scratch[2 * blockIdx.x] = s;
+            scratch[2 * blockIdx.x + 1] = c;
+            __threadfence();
+            s_last = atomicAdd(count, 1u) == (unsigned)(nb - 1);
+        }
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last && warp == 0) {
         __threadfence();
         const volatile double *vs = scratch;
         double S = 0.0, C = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const double v = vs[2 * b];
-            const double t = S + v;
-            C += (fabs(S) >= fabs(v) ? (S - t) + v : (v - t) + S) + vs[2 * b + 1];
-            S = t;
+        for (int b = lane; b < nb; b += 32) two_sum_add(S, C, vs[2 * b], vs[2 * b + 1]);
+        warp_two_sum(S, C);
+        if (lane == 0) {
+            *E = factor * (S + C);
+            *count = 0u;
         }
-        *E = factor * (S + C);
-        *count = 0u;
     }
 }
 
