@@ -349,24 +349,45 @@ k_eig_leading(double *__restrict__ W, double *__restrict__ Q, int m, int r, doub
     if (threadIdx.x < r) val[threadIdx.x] = W[order[threadIdx.x] * m + order[threadIdx.x]];
 }
 
-// Left singular vectors from right ones: F[a][row] = (Y v_a)[row] / |Y v_a|
-// (zero when the direction is null); one CTA per a.
+// Left singular vectors from right ones, by one CTA: u_a = Y v_a for a = 0 ..
+// r - 1 (eigenvalues descending), each orthogonalised against u_0 .. u_{a-1}
+// (two Gram-Schmidt passes: Y v_a loses orthogonality as sigma_a / sigma_0
+// falls, the Gram matrix squaring the condition) and normalised into
+// F[a][.]. A direction whose eigenvalue is at or below 1e-20 of the largest
+// (sigma below 1e-10 of sigma_0: rounding noise of the Gram matrix), or
+// whose norm after orthogonalisation falls below 1e-8 of its norm before,
+// is a direction the tensor does not hold: zero.
 __global__ void __launch_bounds__(kLrThreads)
 k_left_from_right(Unfold u, const double *__restrict__ V, const double *__restrict__ val, int r, double *__restrict__ F)
 {
     __shared__ double red[kLrThreads / 32];
-    const int a = blockIdx.x, q = u.qhi * u.qlo;
-    double acc = 0.0;
-    for (int row = threadIdx.x; row < u.n; row += blockDim.x) {
-        double v = 0.0;
-        for (int c = 0; c < q; ++c) v += u.at(row, c) * V[(int64_t)a * q + c];
-        F[(int64_t)a * u.n + row] = v;
-        acc += v * v;
+    const int q = u.qhi * u.qlo, n = u.n;
+    const double top = val[0] > 0.0 ? val[0] : 0.0;
+    for (int a = 0; a < r; ++a) {
+        double *fa = F + (int64_t)a * n;
+        double acc = 0.0;
+        for (int row = threadIdx.x; row < n; row += blockDim.x) {
+            double v = 0.0;
+            for (int c = 0; c < q; ++c) v += u.at(row, c) * V[(int64_t)a * q + c];
+            fa[row] = v;
+            acc += v * v;
+        }
+        const double n0 = sqrt(block_sum(acc, red));
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b = 0; b < a; ++b) {
+                const double *fb = F + (int64_t)b * n;
+                double d = 0.0;
+                for (int row = threadIdx.x; row < n; row += blockDim.x) d += fb[row] * fa[row];
+                d = block_sum(d, red);
+                for (int row = threadIdx.x; row < n; row += blockDim.x) fa[row] -= d * fb[row];
+            }
+        acc = 0.0;
+        for (int row = threadIdx.x; row < n; row += blockDim.x) acc += fa[row] * fa[row];
+        const double n1 = sqrt(block_sum(acc, red));
+        const bool null_dir = !(val[a] > 1e-20 * top) || !(n0 > 0.0) || !(n1 > 1e-8 * n0);
+        for (int row = threadIdx.x; row < n; row += blockDim.x) fa[row] = null_dir ? 0.0 : fa[row] / n1;
+        __syncthreads();
     }
-    const double nrm = sqrt(block_sum(acc, red));
-    const bool null_dir = !(val[a] > 0.0) || !(nrm > 0.0);
-    for (int row = threadIdx.x; row < u.n; row += blockDim.x)
-        F[(int64_t)a * u.n + row] = null_dir ? 0.0 : F[(int64_t)a * u.n + row] / nrm;
 }
 
 // Relative error of Eq. "relr" for all three components: one CTA per x row
@@ -515,7 +536,7 @@ void leading_vectors(const Unfold &u, int r, double *F, double *W, double *Q, do
     const int m = by_rows ? u.n : q;
     k_unfold_gram<<<m * m, kLrThreads, 0, st>>>(u, by_rows, W);
     k_eig_leading<<<1, kEigThreads, 0, st>>>(W, Q, m, r, by_rows ? F : sel, val);
-    if (!by_rows) k_left_from_right<<<r, kLrThreads, 0, st>>>(u, sel, val, r, F);
+    if (!by_rows) k_left_from_right<<<1, kLrThreads, 0, st>>>(u, sel, val, r, F);
 }
 
 demag_status relerr_run(const double *M, int nx, int ny, int nz, const double *lam, const double *G, const double *A,
