@@ -164,12 +164,10 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
         const int t = blockIdx.x + i * step;
         if (t >= ntiles) break;
         const int b = i & 1;
+        // every thread waits for the tile itself; a wait that gives up is
+        // acted on after stage 1's barrier (stage 1 then read a partly
+        // filled buffer: shared memory only, and the tile is abandoned)
         if (!mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1), kPipeWaitCycles)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) {
-            xpipe_abort(bars, i, step, ntiles);
-            return;
-        }
         const int row0 = t * TR;
         // stage 1 from shared memory: thread (row, j1) reads z[j1 + r R2], r < R1/2
         if (threadIdx.x < TR * R2) {
@@ -194,6 +192,10 @@ k_x_fwd_tma(const T *__restrict__ in, T wscalar, int nrows, int nvalid, typename
             for (int r = 0; r < R1; ++r) s[xex<R1>(j1, r)] = u[r];
         }
         __syncthreads();  // buffer b consumed, exchange rows written
+        if (s_fail) {
+            xpipe_abort(bars, i, step, ntiles);
+            return;
+        }
         if (threadIdx.x == 0) {
             const int tn = blockIdx.x + (i + 2) * step;
             if (tn < ntiles) {

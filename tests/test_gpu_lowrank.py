@@ -226,3 +226,31 @@ def test_paper_low_rank_figure_properties():
         # same error from these initial guesses, in the oracle too); Tucker falls
         assert errs[0]["cp"] > errs[1]["cp"] and errs[2]["cp"] <= errs[1]["cp"] * (1 + 1e-9), (name, errs)
         assert errs[0]["tucker"] > errs[1]["tucker"] > errs[2]["tucker"], (name, errs)
+
+
+def test_tucker_als_rank_deficient_unfolding_matches_oracle():
+    """A component constant along z (its z unfolding has rank 1, like the
+    vortex's m_z) with Tucker ranks (3, 3, 3): the null directions of C come
+    back as zeros or orthonormal completions, never as noise, and the
+    reconstruction equals the oracle's (SVD-based) to 1e-10."""
+    from paper_1204_4302_gb300 import lowrank
+    n, ranks = (11, 9, 14), (3, 3, 3)
+    rng = np.random.default_rng(21)
+    M = rng.standard_normal((3,) + tuple(reversed(n)))
+    M[2] = M[2][:1]                 # m_z the same in every z plane
+    M[1] = np.outer(rng.standard_normal(n[2]), rng.standard_normal(n[1] * n[0])).reshape(M[1].shape)
+    init = _init(n, ranks, seed=22)
+    G, A, B, C, err = lowrank.tucker_als(_cuda(M), ranks, [_cuda(f) for f in init], 4)
+    G, A, B, C = (t.cpu().numpy() for t in (G, A, B, C))
+    L = np.zeros_like(M)
+    for p in range(3):
+        Go, Ao, Bo, Co = lr.tucker_als(M[p], [init[q][p].T for q in range(3)], 4)
+        L[p] = lr.tucker_reconstruct(Go, Ao, Bo, Co)
+        got = lr.tucker_reconstruct(G[p], A[p].T, B[p].T, C[p].T)
+        assert _relmax(got, L[p]) <= 1e-10, p
+        for F in (A[p], B[p], C[p]):
+            gram = F @ F.T
+            # orthonormal rows, or zero rows for directions the component does not hold
+            assert np.allclose(gram, np.diag(np.diag(gram)), atol=1e-10)
+            assert all(abs(v - 1) < 1e-10 or abs(v) < 1e-20 for v in np.diag(gram)), np.diag(gram)
+    assert abs(err - lr.relerr(M, L)) <= 1e-10
