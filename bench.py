@@ -556,7 +556,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches,
             "setup_ms": round(setup_ms, 1),
             "autotune": {"z_variant": variants[0], "y_variant": variants[1], "x_variant": plan.x_variant(),
-                         "ms_per_field": None if tuned_ms is None else round(tuned_ms, 4)},
+                         "ms_per_field_energy": None if tuned_ms is None else round(tuned_ms, 4)},
             "batch": batch,
             "scalar_potential": sp,
             "tensor_grid": tgr,

@@ -430,14 +430,14 @@ long demag_launch_count(demag_plan_t plan);
 demag_status demag_set_graphs(demag_plan_t plan, int enable);
 
 /* Autotuner: times the kernel variants that exist for this plan's sizes (the
- * z-pass tile width and the y-pass radix order of the two-stage transforms)
- * with CUDA events on the plan's own sizes (five timed calls after two
- * warm-up calls each, on stream) and keeps the fastest. With use_cache != 0 a
- * previous result for the same GPU, precision and sizes is reused from the
- * cache file (DEMAG_TUNE_CACHE, default $HOME/.cache/demag_tune.txt) and a new
- * result is appended to it. best_ms (may be NULL) receives the time of one
- * field call with the chosen variants. Allocates and frees two temporary
- * fields; synchronises. */
+ * z-, y- and x-pass forms, demag_set_variants) with CUDA events on the plan's
+ * own sizes (five timed field + energy calls after two warm-up calls each, on
+ * stream: the x-inverse forms differ most in the energy's epilogue) and keeps
+ * the fastest. With use_cache != 0 a previous result for the same GPU,
+ * precision and sizes is reused from the cache file (DEMAG_TUNE_CACHE,
+ * default $HOME/.cache/demag_tune.txt) and a new result is appended to it.
+ * best_ms (may be NULL) receives the time of one field + energy call with the
+ * chosen variants. Allocates and frees two temporary fields; synchronises. */
 demag_status demag_autotune(demag_plan_t plan, int use_cache, double *best_ms, void *stream);
 
 /* Padding autotuner for DM plans of an nx x ny x nz grid. Every axis can be

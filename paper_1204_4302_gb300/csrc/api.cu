@@ -1546,9 +1546,10 @@ demag_status demag_autotune(demag_plan_t p, int use_cache, double *best_ms, void
             p->zvariant = z;
             p->yvariant = y;
             p->xvariant = x;
-            for (int w = 0; w < 2 && rs == DEMAG_OK; ++w) rs = run_job(p, plain_job(M, H, nullptr), stream);
+            // field + energy: the x-inverse forms differ most in the energy's epilogue
+            for (int w = 0; w < 2 && rs == DEMAG_OK; ++w) rs = run_job(p, plain_job(M, H, p->e_dev), stream);
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 5 && rs == DEMAG_OK; ++r) rs = run_job(p, plain_job(M, H, nullptr), stream);
+            for (int r = 0; r < 5 && rs == DEMAG_OK; ++r) rs = run_job(p, plain_job(M, H, p->e_dev), stream);
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
             float ms = 0;
