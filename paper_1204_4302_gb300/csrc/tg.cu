@@ -83,29 +83,71 @@ __global__ void k_tg_tables(const double *__restrict__ snode, int R, int nx, int
 // Factor transform on axis q: out[v][i] = sum_j D[i - j] u[v][j] for the
 // vectors v = (l, p, m) (K = 3 R r of them), D the plain table (p != q) or
 // the odd one (p = q) of node l. On axis x the weight W_l lam_m^(p) / (4 pi)
-// is folded in. One block per vector; the factor and the table sit in
-// shared memory.
-template <typename T>
+// is folded in. One block per (l, p): its r vectors share the table, so a
+// thread (output i) takes each table entry once for VC vectors at a time
+// (VC = 8, 4, 2 or 1 by the rank), whose factors sit in shared memory as
+// [j][VC] (read two at a time).
+template <typename T, int VC>
 __global__ void __launch_bounds__(512)
 k_tg_apply(const T *__restrict__ tab, int tstride, const T *__restrict__ U, const T *__restrict__ lam,
            const double *__restrict__ wnode, int R, int r, int q, int n, T *__restrict__ out)
 {
+    using V2 = typename CplxOf<T>::type;  // two values (float2 / double2)
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *su = reinterpret_cast<T *>(smraw);   // [n]
-    T *st = su + n;                          // [2n - 1]
-    const int v = blockIdx.x;                // (l * 3 + p) * r + m
-    const int m = v % r, p = (v / r) % 3, l = v / (3 * r);
-    const T *u = U + ((int64_t)p * r + m) * n;
+    T *su = reinterpret_cast<T *>(smraw);   // [n][VC]
+    T *st = su + (size_t)n * VC;             // [2n - 1]
+    const int lp = blockIdx.x;               // l * 3 + p
+    const int p = lp % 3, l = lp / 3;
     const T *tb = tab + ((int64_t)(l * 3 + q) * 2 + (p == q ? 1 : 0)) * tstride;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) su[j] = u[j];
     for (int t = threadIdx.x; t < 2 * n - 1; t += blockDim.x) st[t] = tb[t];
-    __syncthreads();
-    T scale = (T)1;
-    if (q == 0) scale = (T)(wnode[l] * (double)lam[p * r + m] * (1.0 / (4.0 * 3.14159265358979323846)));
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        T acc = 0;
-        for (int j = 0; j < n; ++j) acc += st[i - j + n - 1] * su[j];
-        out[(int64_t)v * n + i] = acc * scale;
+    for (int m0 = 0; m0 < r; m0 += VC) {
+        const int mc = min(VC, r - m0);
+        __syncthreads();  // the previous chunk's factors are read
+        for (int e = threadIdx.x; e < n * VC; e += blockDim.x) {
+            const int j = e / VC, mm = e % VC;
+            su[e] = mm < mc ? U[((int64_t)p * r + m0 + mm) * n + j] : (T)0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            T acc[VC];
+#pragma unroll
+            for (int mm = 0; mm < VC; ++mm) acc[mm] = 0;
+            for (int j = 0; j < n; ++j) {
+                const T d = st[i - j + n - 1];
+                if constexpr (VC == 1) {
+                    acc[0] += d * su[j];
+                } else {
+                    const V2 *f = reinterpret_cast<const V2 *>(su + (size_t)j * VC);
+#pragma unroll
+                    for (int h = 0; h < VC / 2; ++h) {
+                        const V2 w = f[h];
+                        acc[2 * h] += d * w.x;
+                        acc[2 * h + 1] += d * w.y;
+                    }
+                }
+            }
+            for (int mm = 0; mm < mc; ++mm) {
+                const int m = m0 + mm, v = lp * r + m;
+                T scale = (T)1;
+                if (q == 0) scale = (T)(wnode[l] * (double)lam[p * r + m] * (1.0 / (4.0 * 3.14159265358979323846)));
+                out[(int64_t)v * n + i] = acc[mm] * scale;
+            }
+        }
+    }
+}
+
+template <typename T>
+void tg_apply(const T *tab, int tstride, const T *U, const T *lam, const double *wnode, int R, int r, int q, int n,
+              T *out, cudaStream_t st)
+{
+    const int threads = n >= 512 ? 512 : ((n + 31) / 32) * 32;
+    const int vc = r >= 8 ? 8 : (r >= 4 ? 4 : (r >= 2 ? 2 : 1));
+    const size_t sm = (size_t)(vc * n + 2 * n) * sizeof(T);
+    switch (vc) {
+    case 8: k_tg_apply<T, 8><<<3 * R, threads, sm, st>>>(tab, tstride, U, lam, wnode, R, r, q, n, out); break;
+    case 4: k_tg_apply<T, 4><<<3 * R, threads, sm, st>>>(tab, tstride, U, lam, wnode, R, r, q, n, out); break;
+    case 2: k_tg_apply<T, 2><<<3 * R, threads, sm, st>>>(tab, tstride, U, lam, wnode, R, r, q, n, out); break;
+    default: k_tg_apply<T, 1><<<3 * R, threads, sm, st>>>(tab, tstride, U, lam, wnode, R, r, q, n, out); break;
     }
 }
 
@@ -406,10 +448,8 @@ demag_status tg_run(demag_tg_plan *p, const void *lam, const void *Ux, const voi
     const T *weights = p->tucker ? static_cast<const T *>(p->ones) : static_cast<const T *>(lam);
     if (p->timing) cudaEventRecord(p->ev[0], st);
     for (int q = 0; q < 3; ++q) {
-        const size_t sm = (size_t)(3 * n[q]) * sizeof(T);
-        k_tg_apply<T><<<3 * p->R * rq[q], n[q] >= 512 ? 512 : ((n[q] + 31) / 32) * 32, sm, st>>>(
-            static_cast<const T *>(p->tab), p->tstride, static_cast<const T *>(U[q]), weights, p->wnode, p->R, rq[q],
-            q, n[q], static_cast<T *>(out[q]));
+        tg_apply<T>(static_cast<const T *>(p->tab), p->tstride, static_cast<const T *>(U[q]), weights, p->wnode, p->R,
+                    rq[q], q, n[q], static_cast<T *>(out[q]), st);
         p->launches++;
     }
     const bool mma = std::is_same<T, float>::value && p->contraction == 1;
