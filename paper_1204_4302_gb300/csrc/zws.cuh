@@ -264,11 +264,15 @@ template <bool SYNEG>
 __device__ __forceinline__ void product(float2 &mx, float2 &my, float2 &mz, float txx, float tyy, float tzz,
                                         float txy, float txz, float tyz)
 {
-    const float nxy = SYNEG ? -txy : txy, nyz = SYNEG ? -tyz : tyz;
+    // each product term as one packed FP32x2 multiply-add with the negated
+    // tensor value in both halves
+    const float nxy = SYNEG ? txy : -txy, nyz = SYNEG ? tyz : -tyz;
     const float2 x = mx, y = my, z = mz;
-    mx = make_float2(-(txx * x.x + nxy * y.x + txz * z.x), -(txx * x.y + nxy * y.y + txz * z.y));
-    my = make_float2(-(nxy * x.x + tyy * y.x + nyz * z.x), -(nxy * x.y + tyy * y.y + nyz * z.y));
-    mz = make_float2(-(txz * x.x + nyz * y.x + tzz * z.x), -(txz * x.y + nyz * y.y + tzz * z.y));
+    const float2 pxx = make_float2(-txx, -txx), pyy = make_float2(-tyy, -tyy), pzz = make_float2(-tzz, -tzz);
+    const float2 pxy = make_float2(nxy, nxy), pxz = make_float2(-txz, -txz), pyz = make_float2(nyz, nyz);
+    mx = __ffma2_rn(pxz, z, __ffma2_rn(pxy, y, __fmul2_rn(pxx, x)));
+    my = __ffma2_rn(pyz, z, __ffma2_rn(pyy, y, __fmul2_rn(pxy, x)));
+    mz = __ffma2_rn(pzz, z, __ffma2_rn(pyz, y, __fmul2_rn(pxz, x)));
 }
 
 }  // namespace zw
