@@ -51,7 +51,8 @@ FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 def pass_bytes(n, P, elem=4, energy=True):
     """Algorithmic HBM bytes of each kernel per launch (the data each pass must
     read and write once): spectra are complex (2 elem), the tensor spectrum is
-    6 real octant arrays; with the energy the last pass also reads M."""
+    6 real octant arrays; energy: the last pass also reads M (false where the
+    energy is taken in the z pass, demag_info.energy_in_z)."""
     nx, ny, nz = n
     Px, Py, Pz = P
     Kx = Px // 2 + 1
@@ -346,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---------------------------------------------------------------- roofline
     peak, peak_kind = load_peaks()
-    pb = pass_bytes(n, P, 4)
+    pb = pass_bytes(n, P, 4, energy=not plan.info()["energy_in_z"])
     avg = {nm: (pass_ms[i] / pass_n[i] if pass_n[i] else None) for i, nm in enumerate(PASS_NAMES[:5])}
     per_pass = {}
     for nm in PASS_NAMES[:5]:
@@ -1038,7 +1039,7 @@ def run_configs(args, dev, peak):
                 plan.set_timing(False)
                 pinfo = plan.info()
                 Pp = (pinfo["px"], pinfo["py"], pinfo["pz"])
-                pbytes = pass_bytes(n, Pp, 4, energy=kind != "fwdadj")
+                pbytes = pass_bytes(n, Pp, 4, energy=kind != "fwdadj" and not pinfo["energy_in_z"])
                 work = sum(pbytes.values()) * (2 if kind == "fwdadj" else 1)
                 passes = {}
                 for i, nm in enumerate(PASS_NAMES[:5]):

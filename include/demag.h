@@ -134,6 +134,11 @@ typedef struct {
                                 half-cell phase) */
     int method;              /* demag_method */
     double dx, dy, dz;       /* cell edges */
+    int energy_in_z;         /* 1: a field call with the energy takes the
+                                energy's spectral sum in its z pass (FP32
+                                plan, persistent z form, z length 256 or 512,
+                                spectral route on), so its last pass does not
+                                read M; 0: the last pass sums M.H */
 } demag_info;
 
 /* Create a plan for an nx x ny x nz grid with cell edges dx, dy, dz.
@@ -217,8 +222,10 @@ demag_status demag_field_adjoint(demag_plan_t plan, const void *G, void *out, vo
 /* Field and energy E = -(mu0/2) V sum_cells M.H (paper Sec. 2, the stray-
  * field energy, in SI units; V = dx dy dz). H: device output as above.
  * E_dev: device pointer to one double receiving E. The per-block partial sums
- * are formed in the field's last pass and summed in FP64 with compensation.
- * Asynchronous. */
+ * are formed in the field's last pass (sum of M.H), or, where
+ * demag_info.energy_in_z says so, in its z pass as the spectral sum of
+ * demag_energy (equal up to rounding: Parseval's identity), and summed in
+ * FP64 with compensation. Asynchronous. */
 demag_status demag_field_energy(demag_plan_t plan, const void *M, void *H, double *E_dev,
                                 void *stream);
 
@@ -236,8 +243,10 @@ demag_status demag_energy(demag_plan_t plan, const void *M, double *E_out, void 
  * demag_energy_grad with G = NULL): enable != 0 (the default) takes the
  * spectral sum where the plan allows it, 0 always runs the field pipeline.
  * Both give E within rounding; the spectral route skips the y and x inverse
- * passes. Tensor-method plans only (scalar-potential plans always run their
- * own pipeline). */
+ * passes. The same switch decides whether field calls with the energy take
+ * the spectral sum in the persistent z pass (demag_info.energy_in_z) or the
+ * sum of M.H in their last pass. Tensor-method plans only (scalar-potential
+ * plans always run their own pipeline). */
 demag_status demag_set_spectral_energy(demag_plan_t plan, int enable);
 
 /* Energy and its gradient for a magnetization given as M = Ms * w * m, with m

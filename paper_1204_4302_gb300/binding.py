@@ -81,6 +81,7 @@ class demag_info(ctypes.Structure):
         ("tensor_imag_max", c_double),
         ("method", c_int),
         ("dx", c_double), ("dy", c_double), ("dz", c_double),
+        ("energy_in_z", c_int),
     ]
 
 

@@ -316,6 +316,15 @@ struct FieldJob {
     double *E_dev;        // optional energy -(mu0/2) V sum input . H
 };
 
+// Field calls with the energy take its spectral sum in the persistent z pass
+// (FP32 plans of the tensor method whose z form is 6 or 7 at length 256 or
+// 512, spectral route on); the last pass then does not read M.
+bool energy_in_z(const demag_plan *p)
+{
+    return p->method == DEMAG_METHOD_DM && p->prec == DEMAG_F32 && p->spectral_energy && p->ntile &&
+           (p->zvariant == 6 || p->zvariant == 7) && (p->Pz == 256 || p->Pz == 512);
+}
+
 template <typename T>
 demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
 {
@@ -367,7 +376,7 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     }
     tm.mark();
     if (spectral) {
-        int nparts = 0;
+        int nparts = p->npartials;
         e = cudaErrorNotSupported;
         if ((p->zvariant == 6 || p->zvariant == 7) && f32 && p->ntile)
             e = Passes<T>::zconv_ws_energy(Pz, S2, Kx, Py, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz,
@@ -390,11 +399,21 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
         tm.mark();
         return DEMAG_OK;
     }
-    // z forward . product . z inverse
+    // z forward . product . z inverse; with the energy and the persistent
+    // form, the energy's spectral sum is taken there (so the x inverse pass
+    // does not read M)
     e = cudaErrorNotSupported;
+    int zparts = p->npartials;
+    const bool zenergy = job.E_dev && energy_in_z(p);
     if ((p->zvariant == 6 || p->zvariant == 7) && f32 && p->ntile)  // persistent TMA forms, FP32 only
         e = Passes<T>::zconv_ws(Pz, S2, Kx, Py, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz,
-                                (const T *)(const void *)p->ntile, twz, st, p->zvariant == 7 ? 4 : 8);
+                                (const T *)(const void *)p->ntile, twz, st, p->zvariant == 7 ? 4 : 8,
+                                zenergy ? p->partials : nullptr, zenergy ? &zparts : nullptr);
+    if (!(e == cudaSuccess && zenergy)) zparts = 0;
+    if (zparts > 0) {
+        xo.Mref = nullptr;
+        xo.partials = nullptr;
+    }
     if (e == cudaErrorNotSupported)
         e = Passes<T>::zconv(Pz, S2, Py * Kx, Kx, Kxp, (int64_t)Py * Kxp, (int64_t)nz * Py * Kxp, nz, nhat, Py, Kx,
                              twz, 1, st, (p->zvariant == 6 || p->zvariant == 7) ? 0 : p->zvariant);
@@ -423,7 +442,12 @@ demag_status run_field(demag_plan *p, const FieldJob &job, cudaStream_t st)
     tm.mark();
     if (job.E_dev) {
         const double V = p->dx * p->dy * p->dz;
-        e = demag::energy_finalize(p->partials, nblocks, -0.5 * kMu0 * V, job.E_dev, p->partials + p->npartials, st);
+        if (zparts > 0)  // spectral sum of the z pass
+            e = demag::energy_finalize(p->partials, zparts, 0.5 * kMu0 * V / ((double)Px * Py * Pz), job.E_dev,
+                                       p->partials + p->npartials, st);
+        else
+            e = demag::energy_finalize(p->partials, nblocks, -0.5 * kMu0 * V, job.E_dev, p->partials + p->npartials,
+                                       st);
         if (e != cudaSuccess) return fail(DEMAG_ERR_CUDA, std::string("energy: ") + cudaGetErrorString(e));
         p->launches++;
         tm.mark();
@@ -1429,6 +1453,7 @@ demag_status demag_plan_info(demag_plan_t p, demag_info *info)
     info->tensor_imag_max = p->imag_max;
     info->method = p->method;
     info->dx = p->dx; info->dy = p->dy; info->dz = p->dz;
+    info->energy_in_z = energy_in_z(p) ? 1 : 0;
     return DEMAG_OK;
 }
 

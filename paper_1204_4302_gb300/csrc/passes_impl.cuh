@@ -313,7 +313,7 @@ bool zws_input_map(CUtensorMap *out, const float2 *S, int Kx, int Py, int nz, in
     return true;
 }
 
-template <int L, int TC, bool EONLY = false>
+template <int L, int TC, bool EONLY = false, bool FE = false>
 cudaError_t zws_launch(float2 *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows, const float *ntile,
                        const float2 *tw, cudaStream_t st, double *partials = nullptr, int *nparts = nullptr)
 {
@@ -322,15 +322,18 @@ cudaError_t zws_launch(float2 *S, int Kx, int Py, int64_t ss, int64_t rs, int64_
     if (!zws_input_map<L, TC>(&map, S, Kx, Py, nrows, ss, rs, cs)) return cudaErrorNotSupported;
     const size_t sm = zws_smem_bytes<L, TC>(nrows);
     if (sm > 227 * 1024) return cudaErrorNotSupported;
-    cudaError_t e = allow_smem<k_z_ws<L, TC, EONLY>>(sm);
+    cudaError_t e = allow_smem<k_z_ws<L, TC, EONLY, FE>>(sm);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + TC - 1) / TC;
     const int ntiles = ntx * Py;
-    const int cap = sm_count() * resident_ctas<k_z_ws<L, TC, EONLY>>(Sh::NT, sm);
-    const int grid = ntiles < cap ? ntiles : cap;
-    if (nparts) *nparts = grid;
-    k_z_ws<L, TC, EONLY><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx, ntiles,
-                                                   partials);
+    const int cap = sm_count() * resident_ctas<k_z_ws<L, TC, EONLY, FE>>(Sh::NT, sm);
+    int grid = ntiles < cap ? ntiles : cap;
+    if (nparts) {  // in: room for per-CTA sums (the persistent loop takes any grid); out: sums written
+        if (*nparts > 0 && grid > *nparts) grid = *nparts;
+        *nparts = grid;
+    }
+    k_z_ws<L, TC, EONLY, FE><<<grid, Sh::NT, sm, st>>>(map, S, Kx, Py, ss, rs, cs, nrows, ntile, tw, ntx, ntiles,
+                                                       partials);
     return cudaGetLastError();
 }
 
@@ -362,12 +365,19 @@ cudaError_t Passes<T>::tile_tensor(int L, const T *nhat, T *ntile, int Py, int K
 
 template <typename T>
 cudaError_t Passes<T>::zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
-                                const T *ntile, const C *tw, cudaStream_t st, int tc)
+                                const T *ntile, const C *tw, cudaStream_t st, int tc, double *partials, int *nparts)
 {
     if constexpr (sizeof(T) != 4) {
         return cudaErrorNotSupported;
     } else {
         if (!zws_ok(L, S, ntile, nrows, ss, rs, cs, sizeof(C))) return cudaErrorNotSupported;
+        if (partials) {  // field and spectral energy
+            if (L == 256)
+                return tc == 4 ? zws_launch<256, 4, false, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts)
+                               : zws_launch<256, 8, false, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts);
+            return tc == 4 ? zws_launch<512, 4, false, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts)
+                           : zws_launch<512, 8, false, true>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st, partials, nparts);
+        }
         if (L == 256)
             return tc == 4 ? zws_launch<256, 4>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st)
                            : zws_launch<256, 8>(S, Kx, Py, ss, rs, cs, nrows, ntile, tw, st);

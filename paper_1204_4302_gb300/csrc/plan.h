@@ -90,13 +90,18 @@ template <typename T> struct Passes {
                              cudaStream_t st, int variant = 0);
     // persistent z pass streaming column tiles by TMA (FP32, L = 256 or 512, at
     // most L/2 input rows); ntile: the tile-ordered tensor copy (tile_tensor); tc:
-    // columns per tile, 8 (one CTA per SM) or 4 (two CTAs per SM).
+    // columns per tile, 8 (one CTA per SM) or 4 (two CTAs per SM). With
+    // partials: also the spectral energy's per-CTA sums of w(kx) m^H N^ m,
+    // taken at the product; *nparts holds the room in partials on entry (the
+    // grid is capped to it) and the number of sums written on return.
     // cudaErrorNotSupported when the arguments do not allow it.
     static cudaError_t zconv_ws(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,
-                                const T *ntile, const C *tw, cudaStream_t st, int tc = 8);
+                                const T *ntile, const C *tw, cudaStream_t st, int tc = 8,
+                                double *partials = nullptr, int *nparts = nullptr);
     // spectral energy (the Parseval form of E, no inverse passes): forward z
     // transforms and the per-CTA sums of w(kx) m^H N^ m into partials
-    // (*nparts of them). zconv_ws_energy: the persistent TMA form (as
+    // (*nparts of them; for zconv_ws_energy *nparts also holds the room in
+    // partials on entry, as for zconv_ws). zconv_ws_energy: the persistent TMA form (as
     // zconv_ws); zconv_energy: the two-stage / one-thread forms (power-of-two
     // L <= 512). cudaErrorNotSupported where the form does not exist.
     static cudaError_t zconv_ws_energy(int L, C *S, int Kx, int Py, int64_t ss, int64_t rs, int64_t cs, int nrows,

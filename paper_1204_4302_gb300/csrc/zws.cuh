@@ -340,7 +340,9 @@ __host__ __device__ inline size_t zws_smem_bytes(int nrows)
 // forward transforms each thread sums w(kx) m^H N^ m over its frequencies,
 // nothing is transformed back or written; partials[blockIdx.x] receives the
 // CTA's sum over all its tiles (NaN if a wait gave up).
-template <int L, int TC, bool EONLY = false>
+// FE: the field and the same energy sum, taken at the product as
+// -Re(m^H h) with h = -N^ m (both in registers there).
+template <int L, int TC, bool EONLY = false, bool FE = false>
 __global__ void __launch_bounds__(ZwsShape<L, TC>::NT, ZwsShape<L, TC>::MIN_CTAS)
 k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, int Py, int64_t ss, int64_t rs,
        int64_t cs, int nrows, const float *__restrict__ ntile, const float2 *__restrict__ twg, int ntx, int ntiles,
@@ -390,9 +392,10 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
         for (int h = 0; h < NSUB; ++h) bulk_g2s(tz + h * TZS, src + h * TZB, TZB * (unsigned)sizeof(float), &bar[1]);
     };
 
-    double eacc = 0.0;  // EONLY: this thread's sum over its tiles
+    static_assert(!(EONLY && FE), "one energy form at a time");
+    double eacc = 0.0;  // EONLY / FE: this thread's sum over its tiles
     auto fail_exit_partial = [&]() {
-        if constexpr (EONLY) {
+        if constexpr (EONLY || FE) {
             if (tid == 0) partials[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
         }
     };
@@ -501,6 +504,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 else quad_all(std::false_type{});
                 eacc += (double)(e * kx_weight<float>(kx0 + c, Kx));
             } else {
+            float e = 0.f;  // FE: sum of -Re(m^H h) over this thread's frequencies
             auto prod_all = [&](auto syneg) {
                 constexpr bool SN = decltype(syneg)::value;
 #pragma unroll
@@ -515,11 +519,20 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                         txz = -txz;
                         tyz = -tyz;
                     }
-                    zw::product<SN>(a[m], b[m], d[m], q[0], q[HZ * 4], q[2 * HZ * 4], q[3 * HZ * 4], txz, tyz);
+                    if constexpr (FE) {
+                        const float2 mx = a[m], my = b[m], mz = d[m];
+                        zw::product<SN>(a[m], b[m], d[m], q[0], q[HZ * 4], q[2 * HZ * 4], q[3 * HZ * 4], txz, tyz);
+                        e -= mx.x * a[m].x + mx.y * a[m].y;
+                        e -= my.x * b[m].x + my.y * b[m].y;
+                        e -= mz.x * d[m].x + mz.y * d[m].y;
+                    } else {
+                        zw::product<SN>(a[m], b[m], d[m], q[0], q[HZ * 4], q[2 * HZ * 4], q[3 * HZ * 4], txz, tyz);
+                    }
                 }
             };
             if (ky > Py / 2) prod_all(std::true_type{});
             else prod_all(std::false_type{});
+            if constexpr (FE) eacc += (double)(e * kx_weight<float>(kx0 + c, Kx));
             zw::dft16<true>(a);
             zw::dft16<true>(b);
             zw::dft16<true>(d);
@@ -600,7 +613,7 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
         }
         __syncthreads();  // exchange read before the next tile's stage 1 writes it
     }
-    if constexpr (EONLY) block_partial<NT>(eacc, partials, blockIdx.x);
+    if constexpr (EONLY || FE) block_partial<NT>(eacc, partials, blockIdx.x);
 }
 
 }  // namespace demag
