@@ -504,7 +504,9 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                 else quad_all(std::false_type{});
                 eacc += (double)(e * kx_weight<float>(kx0 + c, Kx));
             } else {
-            float e = 0.f;  // FE: sum of -Re(m^H h) over this thread's frequencies
+            // FE: Re(m^H h) over this thread's frequencies, one packed
+            // accumulator per component
+            float2 ex2 = make_float2(0.f, 0.f), ey2 = ex2, ez2 = ex2;
             auto prod_all = [&](auto syneg) {
                 constexpr bool SN = decltype(syneg)::value;
 #pragma unroll
@@ -522,9 +524,9 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
                     if constexpr (FE) {
                         const float2 mx = a[m], my = b[m], mz = d[m];
                         zw::product<SN>(a[m], b[m], d[m], q[0], q[HZ * 4], q[2 * HZ * 4], q[3 * HZ * 4], txz, tyz);
-                        e -= mx.x * a[m].x + mx.y * a[m].y;
-                        e -= my.x * b[m].x + my.y * b[m].y;
-                        e -= mz.x * d[m].x + mz.y * d[m].y;
+                        ex2 = __ffma2_rn(mx, a[m], ex2);
+                        ey2 = __ffma2_rn(my, b[m], ey2);
+                        ez2 = __ffma2_rn(mz, d[m], ez2);
                     } else {
                         zw::product<SN>(a[m], b[m], d[m], q[0], q[HZ * 4], q[2 * HZ * 4], q[3 * HZ * 4], txz, tyz);
                     }
@@ -532,7 +534,8 @@ k_z_ws(const __grid_constant__ CUtensorMap map, float2 *__restrict__ S, int Kx, 
             };
             if (ky > Py / 2) prod_all(std::true_type{});
             else prod_all(std::false_type{});
-            if constexpr (FE) eacc += (double)(e * kx_weight<float>(kx0 + c, Kx));
+            if constexpr (FE)
+                eacc -= (double)(((ex2.x + ex2.y) + (ey2.x + ey2.y) + (ez2.x + ez2.y)) * kx_weight<float>(kx0 + c, Kx));
             zw::dft16<true>(a);
             zw::dft16<true>(b);
             zw::dft16<true>(d);
