@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library builds, loads,
-exports every entry point include/demag.h declares, and fails cleanly (a
-status, not a crash) when no CUDA device is present."""
+exports every entry point include/demag.h declares, fails cleanly (a status,
+not a crash) when no CUDA device is present, and the Python mirrors of its
+structs have the C layout."""
 import os
 import re
 
@@ -279,3 +280,34 @@ def test_noalloc_capacity_is_checked_before_the_sizes_are_multiplied(lib):
         with pytest.raises(binding.DemagError) as e:
             binding.demag_energy_noalloc(*dims, 1.0, 1.0, 1.0, binding.DEMAG_F32, None, None, None)
         assert e.value.name == "DEMAG_ERR_UNSUPPORTED", dims
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of demag_options and demag_info have the C layout
+    (size and every field offset), checked with a C program compiled against
+    include/demag.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1204_4302_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "demag.h"', "int main(void) {"]
+    for st in (B.demag_options, B.demag_info):
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in (B.demag_options, B.demag_info):
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
